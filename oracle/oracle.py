@@ -1,0 +1,192 @@
+"""Python access to the FP64 CPU oracle (``lbnr_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` may import this module; the product library does
+not, and it shares no code with the CUDA path.
+
+The oracle follows the lattice Boltzmann model of Ilseven & Mendoza
+(arXiv:1505.02037): Eq. (numlb) with the equilibria and source distributions
+of Eqs. (alfa)-(ekstsor), the moment rule rho = sum f + dt S / 2, the
+Bona-Masso right-hand sides of Sec. "Bona-Masso evolution equations" and the
+ADM constraints of Sec. "3+1 ADM formalism". The C file lists every reading
+of a passage the paper leaves open.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lbnr_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liblbnr_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+NF = 16
+Q_OF = {1: 3, 2: 9, 3: 19}
+VSET_NAMES = {"D1Q3": 1, "D2Q9": 2, "D3Q19": 3}
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("vset", ctypes.c_int32),
+        ("slicing", ctypes.c_int32),
+        ("sources_on", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
+        ("nx", ctypes.c_int64),
+        ("ny", ctypes.c_int64),
+        ("nz", ctypes.c_int64),
+        ("dx", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("tau", ctypes.c_double),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compiles the oracle with gcc (no FMA contraction, optional OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = ctypes.CDLL(path)
+            dp = ctypes.POINTER(ctypes.c_double)
+            pp = ctypes.POINTER(Params)
+            L.orc_vset.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp]
+            L.orc_vset.restype = ctypes.c_int
+            L.orc_bm_point.argtypes = [ctypes.c_double, dp, dp, dp, dp, dp, ctypes.c_int,
+                                       dp, dp, dp, dp]
+            L.orc_bm_point.restype = None
+            for name in ("orc_init", "orc_step", "orc_moments"):
+                getattr(L, name).argtypes = [pp, dp, dp]
+                getattr(L, name).restype = ctypes.c_int
+            L.orc_run.argtypes = [pp, dp, dp, ctypes.c_int64]
+            L.orc_run.restype = ctypes.c_int
+            L.orc_step_cells.argtypes = [pp, dp, ctypes.c_int64,
+                                         ctypes.POINTER(ctypes.c_int64), dp]
+            L.orc_step_cells.restype = ctypes.c_int
+            L.orc_constraint_fields.argtypes = [pp, dp, dp]
+            L.orc_constraint_fields.restype = ctypes.c_int
+            L.orc_constraints.argtypes = [pp, dp, dp]
+            L.orc_constraints.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _check(rc: int, what: str):
+    if rc == -4:
+        raise FloatingPointError(f"oracle {what}: non-finite value")
+    if rc != 0:
+        raise OracleError(f"oracle {what} failed with code {rc}")
+
+
+def velocity_set(vset: int):
+    """(c[Q,3] int, w[Q] float) as tabulated in the oracle."""
+    c = (ctypes.c_int * 57)()
+    w = np.zeros(19)
+    Q = lib().orc_vset(vset, c, _dp(w))
+    if Q < 0:
+        raise OracleError("unknown velocity set")
+    return np.array(c[: 3 * Q]).reshape(Q, 3), w[:Q].copy()
+
+
+def bm_point(alpha, g6, K6, V3, A3, D18, slicing=1):
+    """Pointwise lambda^k_ij [3,6], S_ij [6], Omega_k [3], lapse source."""
+    g6, K6, V3, A3, D18 = (np.ascontiguousarray(np.asarray(v, dtype=np.float64))
+                           for v in (g6, K6, V3, A3, D18))
+    lam = np.zeros(18)
+    S = np.zeros(6)
+    Om = np.zeros(3)
+    Sa = ctypes.c_double(0)
+    lib().orc_bm_point(float(alpha), _dp(g6), _dp(K6), _dp(V3), _dp(A3), _dp(D18.reshape(-1)),
+                       int(slicing), _dp(lam), _dp(S), _dp(Om), ctypes.byref(Sa))
+    return lam.reshape(3, 6), S, Om, Sa.value
+
+
+class Oracle:
+    """One lattice configuration: vset 1/2/3, grid (nx, ny, nz), tau (the
+    dimensionless tau/dt), dx = dt, slicing 0/1/2, sources on/off."""
+
+    def __init__(self, vset, shape, tau, dx, dt=None, slicing=1, sources_on=True):
+        nx, ny, nz = shape
+        self.vset = int(vset)
+        self.Q = Q_OF[self.vset]
+        self.shape = (int(nx), int(ny), int(nz))
+        self.cells = nx * ny * nz
+        self.p = Params(self.vset, int(slicing), int(bool(sources_on)), 0, nx, ny, nz,
+                        float(dx), float(dx if dt is None else dt), float(tau))
+
+    def _f_shape(self):
+        return (NF, self.Q, self.cells)
+
+    def init(self, fields: np.ndarray) -> np.ndarray:
+        fields = np.ascontiguousarray(fields, dtype=np.float64).reshape(NF, self.cells)
+        f = np.zeros(self._f_shape())
+        _check(lib().orc_init(ctypes.byref(self.p), _dp(fields), _dp(f)), "init")
+        return f
+
+    def step(self, f: np.ndarray) -> np.ndarray:
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        out = np.zeros(self._f_shape())
+        _check(lib().orc_step(ctypes.byref(self.p), _dp(f), _dp(out)), "step")
+        return out
+
+    def run(self, f: np.ndarray, n: int) -> np.ndarray:
+        f = np.array(f, dtype=np.float64, order="C", copy=True)
+        scratch = np.zeros_like(f)
+        _check(lib().orc_run(ctypes.byref(self.p), _dp(f), _dp(scratch), int(n)), "run")
+        return f
+
+    def moments(self, f: np.ndarray) -> np.ndarray:
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        out = np.zeros((NF, self.cells))
+        _check(lib().orc_moments(ctypes.byref(self.p), _dp(f), _dp(out)), "moments")
+        return out
+
+    def step_cells(self, f: np.ndarray, cells) -> np.ndarray:
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        idx = np.ascontiguousarray(np.asarray(cells, dtype=np.int64))
+        out = np.zeros((len(idx), NF, self.Q))
+        _check(lib().orc_step_cells(ctypes.byref(self.p), _dp(f), len(idx),
+                                    idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                    _dp(out)), "step_cells")
+        return out
+
+    def constraint_fields(self, rho: np.ndarray) -> np.ndarray:
+        rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(NF, self.cells)
+        out = np.zeros((self.cells, 7))
+        _check(lib().orc_constraint_fields(ctypes.byref(self.p), _dp(rho), _dp(out)),
+               "constraint_fields")
+        return out
+
+    def constraints(self, f: np.ndarray) -> np.ndarray:
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        out = np.zeros(22)
+        _check(lib().orc_constraints(ctypes.byref(self.p), _dp(f), _dp(out)), "constraints")
+        return out

@@ -1,0 +1,171 @@
+"""Seeded synthetic inputs: the closed-form test spacetimes of Ilseven &
+Mendoza (arXiv:1505.02037, Sec. "Tests and Results") sampled on a periodic
+cell-centred lattice, plus seeded random distribution states.
+
+This module holds no lattice Boltzmann arithmetic. Both the CUDA library's
+tests and the CPU oracle take their inputs from here.
+
+Field order (16 values per cell): alpha; gamma_xx, gamma_xy, gamma_xz,
+gamma_yy, gamma_yz, gamma_zz; K_xx .. K_zz (same order); V_x, V_y, V_z.
+Arrays are [16][nz][ny][nx] (x fastest), float64.
+
+Grid: cell-centred, x_i = x0 + (i + 1/2) dx with x0 = -L/2, matching the
+paper's x_r = -400 dr + (x - 1/2) dr for an 800-cell lattice (Sec. "Gauge
+Wave").
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+NF = 16
+PAIRS = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+
+
+def coords(shape, dx, origin=None):
+    """Cell-centre coordinates X, Y, Z of a (nx, ny, nz) lattice, each [nz, ny, nx]."""
+    nx, ny, nz = shape
+    o = [-0.5 * n * dx for n in shape] if origin is None else origin
+    xs = o[0] + (np.arange(nx) + 0.5) * dx
+    ys = o[1] + (np.arange(ny) + 0.5) * dx
+    zs = o[2] + (np.arange(nz) + 0.5) * dx
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    return X, Y, Z
+
+
+def _direction(direction, shape, dx):
+    """Unit propagation vector n and the wavelength d for which a wave of
+    phase 2 pi (n.x - t)/d is periodic on the box (side L = N dx)."""
+    nx, ny, nz = shape
+    L = nx * dx
+    if direction == "x":
+        return np.array([1.0, 0.0, 0.0]), L
+    if direction == "xy":
+        if ny != nx:
+            raise ValueError("xy wave needs a square lattice")
+        return np.array([1.0, 1.0, 0.0]) / math.sqrt(2), L / math.sqrt(2)
+    if direction == "xyz":
+        if not (ny == nx and nz == nx):
+            raise ValueError("xyz wave needs a cubic lattice")
+        return np.array([1.0, 1.0, 1.0]) / math.sqrt(3), L / math.sqrt(3)
+    raise ValueError(direction)
+
+
+def _pack(alpha, g, K, V, shape):
+    nx, ny, nz = shape
+    out = np.zeros((NF, nz, ny, nx))
+    out[0] = alpha
+    for p, (i, j) in enumerate(PAIRS):
+        out[1 + p] = g[i][j]
+        out[7 + p] = K[i][j]
+    for k in range(3):
+        out[13 + k] = V[k]
+    return out
+
+
+def gauge_wave(shape, dx, A, t=0.0, direction="x"):
+    """Gauge wave (Sec. "Gauge Wave"): ds^2 = -H dt^2 + H du^2 + (transverse),
+    H = 1 - A sin(2 pi (u - t)/d), u = n.x; alpha = sqrt(H),
+    gamma = delta + (H - 1) n n, K = -(pi A/d) cos(phase)/sqrt(H) n n, V = 0.
+    Harmonic slicing."""
+    n, d = _direction(direction, shape, dx)
+    X, Y, Z = coords(shape, dx)
+    u = n[0] * X + n[1] * Y + n[2] * Z
+    ph = 2 * math.pi * (u - t) / d
+    H = 1 - A * np.sin(ph)
+    Knn = -(math.pi * A / d) * np.cos(ph) / np.sqrt(H)
+    g = [[(1.0 if i == j else 0.0) + (H - 1) * n[i] * n[j] for j in range(3)] for i in range(3)]
+    K = [[Knn * n[i] * n[j] for j in range(3)] for i in range(3)]
+    zero = np.zeros_like(H)
+    return _pack(np.sqrt(H), g, K, [zero, zero, zero], shape)
+
+
+def _polarisation(direction):
+    if direction == "x":
+        return np.array([0.0, 1.0, 0.0]), np.array([0.0, 0.0, 1.0])
+    if direction == "xy":
+        return np.array([1.0, -1.0, 0.0]) / math.sqrt(2), np.array([0.0, 0.0, 1.0])
+    if direction == "xyz":
+        return (np.array([1.0, -1.0, 0.0]) / math.sqrt(2),
+                np.array([1.0, 1.0, -2.0]) / math.sqrt(6))
+    raise ValueError(direction)
+
+
+def linear_wave(shape, dx, A, t=0.0, direction="x"):
+    """Linear (gravitational) wave (Sec. "Linear Wave"): alpha = 1,
+    gamma = delta + b (e1 e1 - e2 e2), b = A sin(2 pi (u - t)/d),
+    K = (pi A/d) cos(phase) (e1 e1 - e2 e2). Geodesic slicing.
+    V_k = -b b' n_k / (1 - b^2) is V's defining combination of the closed-form
+    metric derivatives, with b' = db/du."""
+    n, d = _direction(direction, shape, dx)
+    e1, e2 = _polarisation(direction)
+    X, Y, Z = coords(shape, dx)
+    u = n[0] * X + n[1] * Y + n[2] * Z
+    ph = 2 * math.pi * (u - t) / d
+    b = A * np.sin(ph)
+    bp = (2 * math.pi * A / d) * np.cos(ph)
+    P = np.outer(e1, e1) - np.outer(e2, e2)
+    g = [[(1.0 if i == j else 0.0) + b * P[i, j] for j in range(3)] for i in range(3)]
+    K = [[(math.pi * A / d) * np.cos(ph) * P[i, j] for j in range(3)] for i in range(3)]
+    Vn = -b * bp / (1 - b * b)
+    V = [Vn * n[k] for k in range(3)]
+    return _pack(np.ones_like(b), g, K, V, shape)
+
+
+def kasner(shape, p=(-1 / 3, 2 / 3, 2 / 3), t=1.0):
+    """Kasner vacuum solution in synchronous gauge (alpha = 1, geodesic slicing):
+    gamma_ii = t^(2 p_i), K_ii = -p_i t^(2 p_i - 1), with sum p = sum p^2 = 1.
+    Spatially homogeneous, so every lattice reduces it to one cell."""
+    nx, ny, nz = shape
+    one = np.ones((nz, ny, nx))
+    g = [[(t ** (2 * p[i]) * one if i == j else 0 * one) for j in range(3)] for i in range(3)]
+    K = [[(-p[i] * t ** (2 * p[i] - 1) * one if i == j else 0 * one) for j in range(3)]
+         for i in range(3)]
+    return _pack(one, g, K, [0 * one] * 3, shape)
+
+
+def flat(shape):
+    """Minkowski space: alpha = 1, gamma = delta, K = V = 0."""
+    nx, ny, nz = shape
+    one = np.ones((nz, ny, nx))
+    zero = np.zeros((nz, ny, nx))
+    g = [[(one if i == j else zero) for j in range(3)] for i in range(3)]
+    return _pack(one, g, [[zero] * 3] * 3, [zero] * 3, shape)
+
+
+def add_noise(fields, amp, seed):
+    """Adds uniform noise U[-amp, amp] to all 16 fields (seeded)."""
+    rng = np.random.default_rng(seed)
+    return fields + rng.uniform(-amp, amp, size=fields.shape)
+
+
+def flat_value():
+    """Flat-space value of each of the 16 fields."""
+    v = np.zeros(NF)
+    v[0] = 1.0
+    v[1] = v[4] = v[6] = 1.0
+    return v
+
+
+def random_distributions(Q, weights, shape, seed, amp=1e-3, smooth_amp=2e-2):
+    """A seeded distribution state f[16][Q][cells] near flat space:
+    f = w_l (flat + smooth(x) + amp * u) with u ~ U[-1, 1] per value and a
+    smooth periodic perturbation per field. Used to exercise every term of
+    one step; it is not a solution of anything."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed)
+    X, Y, Z = coords(shape, 1.0 / nx)
+    w = np.asarray(weights, dtype=np.float64)
+    base = flat_value()
+    f = np.empty((NF, Q, nz * ny * nx))
+    for F in range(NF):
+        kx, ky, kz = rng.integers(1, 3, size=3)
+        ph = rng.uniform(0, 2 * math.pi, size=3)
+        sm = smooth_amp * (np.sin(2 * math.pi * kx * X + ph[0])
+                           * np.cos(2 * math.pi * ky * Y * (ny > 1) + ph[1])
+                           * np.cos(2 * math.pi * kz * Z * (nz > 1) + ph[2]))
+        sm = sm.reshape(-1)
+        for lam in range(Q):
+            f[F, lam] = w[lam] * (base[F] + sm + amp * rng.uniform(-1, 1, size=sm.shape))
+    return f
