@@ -1,0 +1,334 @@
+"""Throughput benchmark of the lattice Boltzmann Bona-Masso step on GB300.
+
+Default workload: 3D gauge wave along x on the D3Q19 lattice, 256^3 cells,
+FP32 storage and arithmetic, A = 0.1, ping-pong streaming, 1000 steps
+(the 3D configuration's 256^3 FP32 case). One "step" is one full lattice
+Boltzmann time step over the whole lattice (moment pass + fused
+collide-and-stream kernel). Metric: lattice updates/s in Mcell*var/s
+(cells x 16 fields x steps / s).
+
+Prints one JSON line (rank 0). Under torchrun each rank runs an independent
+replica of the workload on its own GPU (the path has no exchange step), so
+scaling is weak and value = units of all ranks / max time over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lbnr|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1505_02037_gb300 import workloads as W  # noqa: E402
+
+WORKLOADS = {
+    # name: (vset, N, storage, direction, A)
+    "gauge3d-256-f32": (3, 256, "f32", "x", 0.1),
+    "gauge3d-256-dev_bf16": (3, 256, "dev_bf16", "x", 0.1),
+    "gauge3d-256-dev_f16": (3, 256, "dev_f16", "x", 0.1),
+    "gauge3d-256-dev_f32": (3, 256, "dev_f32", "x", 0.1),
+    "gauge3d-128-f64": (3, 128, "f64", "x", 0.1),
+    "gauge3d-128-f64-diag": (3, 128, "f64", "xyz", 0.1),
+}
+BYTES = {"f64": 8, "f32": 4, "dev_f32": 4, "dev_bf16": 2, "dev_f16": 2}
+DTYPE = {"f64": "f64", "f32": "f32", "dev_f32": "f32", "dev_bf16": "f32 (bf16 storage)",
+         "dev_f16": "f32 (f16 storage)"}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="lbnr", choices=["lbnr", "reference"])
+    p.add_argument("--workload", default="gauge3d-256-f32", choices=sorted(WORKLOADS))
+    p.add_argument("--tau", type=float, default=4.5)
+    p.add_argument("--profile-steps", type=int, default=20)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if s[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1505_02037_gb300", "csrc")
+    for n in sorted(os.listdir(d)):
+        with open(os.path.join(d, n), "rb") as f:
+            h.update(n.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel_key, cells):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+    except OSError:
+        return None
+    e = t.get(kernel_key)
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e["dram_bytes_per_cell"] * cells
+
+
+def cpu_baseline(vset, storage, direction, A, tau, seconds=12.0):
+    """The FP64 oracle as it stands, on this host's cores, on a bounded sample
+    of the same workload (a 48^3 periodic piece of the same wave, same tau)."""
+    from oracle import oracle as O
+    n = 48
+    shape = (n, n, n) if vset == 3 else (n, n, 1)
+    o = O.Oracle(vset, shape, tau, 1 / n)
+    f = o.init(W.gauge_wave(shape, 1 / n, A, direction=direction))
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        f = o.step(f)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > seconds or steps >= 200:
+            break
+    cells = n ** 3 if vset == 3 else n * n
+    return {"value": cells * 16 * steps / el / 1e6, "unit": "Mcell*var/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"FP64 oracle, D3Q19 {n}^3 periodic gauge wave (A={A}, tau={tau}), "
+                      f"{steps} steps in {el:.1f} s on {cores} host threads"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle timed on the host cores, each step a
+    bounded sample (one oracle step on a 24^3 piece of the workload)."""
+    vset, N, storage, direction, A = WORKLOADS[args.workload]
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    n = 24
+    o = O.Oracle(vset, (n, n, n), args.tau, 1 / n)
+    f = o.init(W.gauge_wave((n, n, n), 1 / n, A, direction=direction))
+    for _ in range(args.warmup):
+        f = o.step(f)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = o.step(f)
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    value = n ** 3 * 16 * args.steps / el / 1e6
+    sample = (f"each step: one FP64 oracle step of a {n}^3 periodic piece of the workload "
+              f"on {cores} host threads")
+    line = {"impl": "reference", "metric": "lattice updates/s", "value": value,
+            "unit": "Mcell*var/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "tau": args.tau},
+            "cpu_baseline": {"value": value, "unit": "Mcell*var/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "Mcell*var/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_1505_02037_gb300 import lbnr
+
+    vset, N, storage, direction, A = WORKLOADS[args.workload]
+    shape = (N, N, N)
+    cells = N ** 3
+    Q = 19
+    fields = W.gauge_wave(shape, 1 / N, A, direction=direction).reshape(16, cells)
+    lat = lbnr.Lattice(vset, shape, args.tau, 1 / N, storage=storage)
+    lat.init(fields)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    # warm-up (also captures the step graphs)
+    lat.step(args.warmup)
+    barrier()
+    stream = lat.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        e0.record(stream)
+        lat.step(args.steps)
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    finite = True
+    try:
+        lat.status()
+    except lbnr.NonFiniteError:
+        finite = False
+
+    # per-kernel durations (same steps, one launch at a time, events around each)
+    ms_aux, ms_col = lat.step_timed(args.profile_steps)
+    col_ms = ms_col / args.profile_steps
+    aux_ms = ms_aux / args.profile_steps
+    s = BYTES[storage]
+    cbytes = 8 if storage == "f64" else 4
+    alg_collide = cells * (2 * 16 * Q * s + 7 * cbytes)  # f in + f out + stencil planes once
+    alg_aux = cells * (7 * Q * s + 7 * cbytes)
+    peaks, peak_kind = measured_peaks()
+    # burst figure: the kernel is timed as one launch of a few milliseconds
+    peak = float(peaks["hbm_gbs"])
+    achieved = alg_collide / (col_ms * 1e-3) / 1e9
+    traffic = traffic_for(f"k_collide:{args.workload}", cells)
+
+    value = world * cells * 16 * args.steps / (ms_max * 1e-3) / 1e6
+    line = {
+        "metric": "lattice updates/s", "value": value, "unit": "Mcell*var/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": DTYPE[storage], "data": "synthetic",
+        "config": {
+            "workload": f"3D gauge wave along {direction}, D3Q19 {N}^3 periodic, "
+                        f"{storage} storage, A={A}, tau={args.tau}, "
+                        f"{'ping-pong' if lat.streaming == 1 else 'AA in-place'} streaming",
+            "workload_key": args.workload, "cells": cells, "fields": 16, "velocities": Q,
+            "tau_note": "tau=0.6 of the configuration is linearly unstable for this scheme "
+                        "(blows up near step 100 at any N and A); cost per step does not "
+                        "depend on tau",
+            "l2": f"inputs larger than L2 ({lat.workspace.numel() / 1e9:.1f} GB working set)",
+            "state_finite_after_run": finite,
+            "parallelism": "replicas" if world > 1 else "single GPU",
+        },
+        "roofline": {"bound": "hbm", "kernel": "k_collide (fused collide-and-stream)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": f"hbm_gbs of {peak_kind}",
+                     "algorithmic_bytes_per_cell": alg_collide / cells,
+                     "avg_launch_ms": col_ms, "traffic": traffic},
+        "kernels_ms_per_step": {"k_aux": aux_ms, "k_collide": col_ms,
+                                "k_aux_frac_of_peak": alg_aux / (aux_ms * 1e-3) / 1e9 / peak},
+        "step_algorithmic_hbm_frac": (alg_collide + alg_aux) / (ms_max / args.steps * 1e-3)
+                                     / 1e9 / peak,
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk.summary(),
+    }
+
+    if not args.no_e2e:
+        # End to end through the public API with host buffers: pinned host
+        # fields -> lbnr_init -> lbnr_step(K) -> lbnr_moments into pinned host.
+        hf = torch.from_numpy(fields.copy()).pin_memory()
+        hout = torch.empty((16, cells), dtype=torch.float64).pin_memory()
+        k = args.steps
+        barrier()
+        t0 = time.perf_counter()
+        lat.init(hf)
+        lat.step(k)
+        try:
+            lat.moments(hout)
+        except lbnr.NonFiniteError:
+            pass
+        barrier()
+        el = time.perf_counter() - t0
+        tt = torch.tensor([el], device=dev)
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        el = float(tt.item())
+        line["e2e"] = {"value": world * cells * 16 * k / el / 1e6, "unit": "Mcell*var/s",
+                       "h2d_bytes_per_step": hf.numel() * 8 / k,
+                       "d2h_bytes_per_step": hout.numel() * 8 / k,
+                       "steps_per_transfer": k}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(vset, storage, direction, A, args.tau)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

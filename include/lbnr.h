@@ -1,0 +1,164 @@
+/*
+ * lbnr: GB300 (sm_103a) library for the lattice Boltzmann model of the
+ * Bona-Masso Einstein equations (Ilseven & Mendoza, "Lattice Boltzmann Model
+ * for Numerical Relativity", arXiv:1505.02037).
+ *
+ * One context = one periodic lattice on one GPU. Each step is the paper's
+ * forced BGK update (Eq. numlb) with the equilibria and source distributions
+ * of Eqs. (alfa)-(ekstsor), the moment rule rho = sum_l f_l + dt S / 2
+ * (Sec. "Lattice Boltzmann Model"), the Bona-Masso right-hand sides of
+ * Sec. "Bona-Masso evolution equations" at zero shift in vacuum, and A_k,
+ * D_kij formed from alpha and gamma by central differences (Sec. "First order
+ * derivatives").
+ *
+ * Conventions used by every call:
+ *  - Fields, 16 per cell, in this order: alpha; gamma_xx, gamma_xy, gamma_xz,
+ *    gamma_yy, gamma_yz, gamma_zz; K_xx, K_xy, K_xz, K_yy, K_yz, K_zz;
+ *    V_x, V_y, V_z.
+ *  - Cells: index x + nx*(y + ny*z), x fastest; the lattice is periodic.
+ *  - Host field arrays are float64 [16][nz][ny][nx]; distribution arrays are
+ *    float64 [16][Q][nz][ny][nx] with the velocities in the paper's order
+ *    (D2Q9 and D3Q19 as printed; D1Q3 is c = 0, +1, -1, w = 2/3, 1/6, 1/6, the
+ *    x-marginal of both printed sets).
+ *  - tau is the dimensionless relaxation time tau/dt of Eq. (lbe); dt must
+ *    equal dx (Sec. "Gauge Wave": dt = dr).
+ *  - All host pointers belong to the caller and are only read or written
+ *    during the call. Every call that returns data to the host synchronises
+ *    the context's stream; lbnr_init and lbnr_step only enqueue work.
+ *  - Return value: LBNR_OK (0) or a negative LBNR_E* code; lbnr_last_error
+ *    gives a message. A context is used from one host thread at a time.
+ */
+#ifndef LBNR_H
+#define LBNR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbnr_ctx lbnr_ctx;
+
+/* Velocity sets (Sec. "Lattice Boltzmann Model"). */
+enum { LBNR_D1Q3 = 1, LBNR_D2Q9 = 2, LBNR_D3Q19 = 3 };
+
+/* Distribution storage. F64/F32 store f itself. The DEV_* forms store
+ * (f_l / w_l - rho_flat) with rho_flat the flat-space value of the field
+ * (alpha = 1, gamma = delta, K = V = 0), so small waves keep their relative
+ * precision; all single-precision forms collide in FP32. */
+enum { LBNR_F64 = 0, LBNR_F32 = 1, LBNR_DEV_F32 = 2, LBNR_DEV_BF16 = 3, LBNR_DEV_F16 = 4 };
+
+/* Slicing condition (Sec. "Gauge choices"): Q = 0, Q = tr K, Q = tr K/alpha. */
+enum { LBNR_GEODESIC = 0, LBNR_HARMONIC = 1, LBNR_ONE_PLUS_LOG = 2 };
+
+/* Streaming: AUTO takes ping-pong buffers when two copies fit in free device
+ * memory, else the in-place AA pattern (one copy). */
+enum { LBNR_STREAM_AUTO = 0, LBNR_STREAM_PINGPONG = 1, LBNR_STREAM_AA = 2 };
+
+enum {
+  LBNR_OK = 0,
+  LBNR_EINVAL = -1,     /* bad argument: sizes, tau <= 1/2, dt != dx, NULL */
+  LBNR_ENOMEM = -2,     /* device memory or the given buffer is too small */
+  LBNR_ECUDA = -3,      /* a CUDA call failed; see lbnr_last_error */
+  LBNR_ENONFINITE = -4, /* a step produced a NaN or Inf moment */
+  LBNR_ETIMEOUT = -5,   /* a bounded device-side wait ran out */
+  LBNR_ESTATE = -6      /* call out of order (e.g. step before init) */
+};
+
+typedef struct {
+  int64_t nx, ny, nz; /* D1Q3 needs ny = nz = 1, D2Q9 needs nz = 1 */
+} lbnr_grid;
+
+typedef struct {
+  int32_t slicing;    /* LBNR_GEODESIC / LBNR_HARMONIC / LBNR_ONE_PLUS_LOG */
+  int32_t storage;    /* LBNR_F64 ... LBNR_DEV_F16 */
+  int32_t streaming;  /* LBNR_STREAM_* */
+  int32_t sources_on; /* 1 normally; 0 drops every source (a test switch) */
+  void* cuda_stream;  /* cudaStream_t for all work; NULL = default stream */
+  void* dev_buffer;   /* optional caller-owned device memory of dev_bytes
+                         (>= lbnr_workspace_bytes); it must outlive the
+                         context. NULL: the library allocates its own. */
+  uint64_t dev_bytes;
+} lbnr_opts;
+
+/* Fills o with the defaults: harmonic slicing, F64, AUTO, sources on. */
+void lbnr_default_opts(lbnr_opts* o);
+
+/* Device bytes a context needs for this grid, set and options (the
+ * streaming choice must not be AUTO). */
+int lbnr_workspace_bytes(const lbnr_grid* grid, int vset, const lbnr_opts* opts,
+                         uint64_t* out_bytes);
+
+/* Creates a context: validates the arguments, fixes the streaming pattern and
+ * lays out (or allocates) the device memory. Nothing is computed. */
+int lbnr_create(const lbnr_grid* grid, int vset, double tau, double dx, double dt,
+                const lbnr_opts* opts, lbnr_ctx** out);
+
+/* Initial distributions from host fields [16][cells]: the shifted equilibrium
+ * f = f_eq(rho0) - (dt/2) w_l S(rho0), with A, D taken from rho0 (the paper
+ * does not state its initialisation). Resets the step count to 0. */
+int lbnr_init(lbnr_ctx* ctx, const double* fields);
+
+/* Enqueues n steps on the context's stream (graph-captured two-step cycles).
+ * Returns without waiting; a NaN/Inf is reported by the next synchronising
+ * call. */
+int lbnr_step(lbnr_ctx* ctx, int64_t n);
+
+/* Same work as lbnr_step(n), launched one kernel at a time with CUDA events
+ * recorded around every launch on the context's stream; synchronises and
+ * adds the elapsed milliseconds per kernel kind into ms_out[2]
+ * (ms_out[0]: the moment pass feeding the derivative stencil, ms_out[1]: the
+ * fused collide-and-stream kernel). For measurement. */
+int lbnr_step_timed(lbnr_ctx* ctx, int64_t n, double* ms_out);
+
+/* Corrected macroscopic fields rho = sum_l f_l + dt S/2 (Sec. LBM), evaluated
+ * in FP64 from the stored distributions, into host out[16][cells]. */
+int lbnr_moments(lbnr_ctx* ctx, double* out);
+
+/* Constraint monitor, FP64 on the device, into host out[22]:
+ * H_L2, H_inf, M_L2, M_inf, C_L2, C_inf, then sum over cells of sum_l f_l for
+ * each of the 16 fields. H = R - K_ij K^ij + (tr K)^2 and
+ * M_i = D_j K^j_i - d_i tr K are the vacuum Hamiltonian and momentum
+ * constraints (Sec. "3+1 ADM formalism"), C_k = V_k - (D_kr^r - D^r_rk) the
+ * definition of V (Sec. "Bona-Masso formulation"), all at the corrected
+ * fields with central differences; L2 = root mean square over cells of the
+ * (vector) norm, inf = largest magnitude. */
+int lbnr_constraints(lbnr_ctx* ctx, double* out);
+
+/* Stored distributions decoded to FP64, host out[16][Q][cells] (standard
+ * layout whatever the streaming pattern). For checks and checkpoints. */
+int lbnr_get_distributions(lbnr_ctx* ctx, double* out);
+
+/* Stored distributions of n selected cells, decoded to FP64, into host
+ * out[n][16][Q] (standard layout). cells[] holds n cell indices in
+ * [0, nx*ny*nz); an index outside that range gives LBNR_EINVAL. Used for
+ * sampled checks of lattices too large to copy back whole. */
+int lbnr_get_cells(lbnr_ctx* ctx, int64_t n, const int64_t* cells, double* out);
+
+/* Replaces the distributions with host in[16][Q][cells] (encoded to the
+ * storage type). With lbnr_get_distributions this gives checkpoint/resume.
+ * Keeps the step count. */
+int lbnr_set_distributions(lbnr_ctx* ctx, const double* in);
+
+/* Synchronises and returns LBNR_ENONFINITE if any step so far produced a
+ * non-finite moment, else LBNR_OK. */
+int lbnr_status(lbnr_ctx* ctx);
+
+/* Steps taken since lbnr_init; Q of the velocity set; the streaming pattern
+ * chosen (LBNR_STREAM_PINGPONG or LBNR_STREAM_AA). */
+int64_t lbnr_steps_done(const lbnr_ctx* ctx);
+int lbnr_q(const lbnr_ctx* ctx);
+int lbnr_streaming(const lbnr_ctx* ctx);
+
+/* Frees what the context allocated. NULL is a no-op. */
+void lbnr_destroy(lbnr_ctx* ctx);
+
+/* Last error message of ctx, or of the calling thread when ctx is NULL. */
+const char* lbnr_last_error(const lbnr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBNR_H */

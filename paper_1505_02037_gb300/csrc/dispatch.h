@@ -1,0 +1,60 @@
+// Internal interface between the C-ABI (capi.cu) and the per-velocity-set
+// translation units that instantiate the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbnr {
+
+constexpr uint64_t kStageBytes = 1ull << 20;
+
+struct LaunchCtx {
+  int32_t nx, ny, nz;
+  int64_t cells;
+  double dx, dt, tau;
+  int slicing, sources_on;
+  void* aux;        // 7 planes of the compute type (stencil input)
+  double* macro;    // 16 FP64 planes (fields, moments)
+  double* aux64;    // 7 FP64 planes (stencil input of the FP64 kernels)
+  double* partials; // per-block reduction partials, 22 doubles each
+  double* out22;    // reduction result
+  void* stage;      // staging area for sampled transfers (kStageBytes)
+  int* flag;        // non-finite flag
+  cudaStream_t st;
+  int block;        // threads per block of the collide kernel
+};
+
+// layout: 0 ping-pong, 1 AA at even step, 2 AA at odd step
+struct Ops {
+  int nvariants;
+  const char* (*variant_name)(int variant);
+  cudaError_t (*step)(const LaunchCtx&, int layout, int variant, const void* fin, void* fout);
+  cudaError_t (*aux)(const LaunchCtx&, int layout, const void* f);
+  cudaError_t (*init)(const LaunchCtx&, void* f);  // from macro, standard layout
+  cudaError_t (*sum64)(const LaunchCtx&, int layout, const void* f, int64_t* nblocks);
+  cudaError_t (*correct64)(const LaunchCtx&);
+  cudaError_t (*constraints64)(const LaunchCtx&, int64_t* nblocks);
+  cudaError_t (*get_plane)(const LaunchCtx&, int layout, const void* f, int F, int l, double* out);
+  cudaError_t (*set_plane)(const LaunchCtx&, int layout, void* f, int F, int l, const double* in);
+  cudaError_t (*get_cells)(const LaunchCtx&, int layout, const void* f, int64_t n,
+                           const int64_t* idx, double* out);
+};
+
+// One getter per (velocity set, storage), each in its own translation unit
+// so the kernels compile in parallel.
+#define LBNR_DECLARE_OPS(q)                                                           \
+  const Ops* ops_q##q##_s0();                                                         \
+  const Ops* ops_q##q##_s1();                                                         \
+  const Ops* ops_q##q##_s2();                                                         \
+  const Ops* ops_q##q##_s3();                                                         \
+  const Ops* ops_q##q##_s4();
+LBNR_DECLARE_OPS(3)
+LBNR_DECLARE_OPS(9)
+LBNR_DECLARE_OPS(19)
+#undef LBNR_DECLARE_OPS
+
+size_t storage_bytes(int storage);
+bool storage_is_fp64(int storage);
+
+}  // namespace lbnr

@@ -1,0 +1,721 @@
+// Kernels of one lattice Boltzmann step for the Bona-Masso system
+// (Ilseven & Mendoza, arXiv:1505.02037): Eq. numlb with the equilibria and
+// source distributions of Eqs. alfa-ekstsor and the moment rule
+// rho = sum_l f_l + dt S / 2 (Sec. "Lattice Boltzmann Model").
+//
+// One step = k_aux (zeroth moments of alpha and gamma -> 7 planes used by the
+// derivative stencil) + k_collide (moments of all 16 fields, A and D by
+// central differences, sources at rho~, corrected rho, flux at rho,
+// equilibria, BGK relaxation plus source, streaming).
+//
+// Memory: SoA planes. Plane p = F*Q + l holds f_{F,l} for every cell,
+// x fastest, so each warp touches 32 consecutive cells of one plane.
+//
+// Streaming layouts (the state after n steps):
+//   ping-pong: f_l(x) at (l, x) of the current buffer; a step writes f*_l(x)
+//              to (l, x + c_l) of the other buffer.
+//   AA in place, n even: f_l(x) at (l, x); the step writes f*_l(x) to
+//              (opp(l), x): no neighbour access.
+//   AA in place, n odd:  f_l(x) at (opp(l), x - c_l); the step writes f*_l(x)
+//              to (l, x + c_l), which is exactly where it read opp(l), so
+//              every cell reads and writes the same locations and no two
+//              cells touch the same location.
+//
+// Representations: ABS holds f itself; DEV holds g = f/w_l - rho_flat,F
+// (rho_flat: alpha = 1, gamma = delta, K = V = 0). In DEV form the update
+// f* = (1-w) f + w_l (omega rho + 3 omega c.F + sigma S) becomes
+// g* = (1-omega) g + omega (rho - rho_flat) + sigma S + 3 omega c.F.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "lattice.cuh"
+#include "physics.cuh"
+
+namespace lbnr {
+
+enum : int { kABS = 0, kDEV = 1 };
+enum : int { kPingPong = 0, kAAEven = 1, kAAOdd = 2 };
+
+// ---------------------------------------------------------------------------
+// Storage codecs
+// ---------------------------------------------------------------------------
+template <class S>
+struct Codec;
+template <>
+struct Codec<double> {
+  __device__ static __forceinline__ double load(const double* p) { return __ldcs(p); }
+  __device__ static __forceinline__ double load_keep(const double* p) { return __ldg(p); }
+  __device__ static __forceinline__ void store(double* p, double v) { __stcs(p, v); }
+};
+template <>
+struct Codec<float> {
+  __device__ static __forceinline__ float load(const float* p) { return __ldcs(p); }
+  __device__ static __forceinline__ float load_keep(const float* p) { return __ldg(p); }
+  __device__ static __forceinline__ void store(float* p, float v) { __stcs(p, v); }
+};
+template <>
+struct Codec<__nv_bfloat16> {
+  __device__ static __forceinline__ float load(const __nv_bfloat16* p) {
+    return __bfloat162float(__ldcs(p));
+  }
+  __device__ static __forceinline__ float load_keep(const __nv_bfloat16* p) {
+    return __bfloat162float(__ldg(p));
+  }
+  __device__ static __forceinline__ void store(__nv_bfloat16* p, float v) {
+    __stcs(p, __float2bfloat16_rn(v));
+  }
+};
+template <>
+struct Codec<__half> {
+  __device__ static __forceinline__ float load(const __half* p) { return __half2float(__ldcs(p)); }
+  __device__ static __forceinline__ float load_keep(const __half* p) {
+    return __half2float(__ldg(p));
+  }
+  __device__ static __forceinline__ void store(__half* p, float v) {
+    __stcs(p, __float2half_rn(v));
+  }
+};
+
+// Flat-space value of field F (alpha = 1, gamma = delta, K = V = 0).
+__host__ __device__ constexpr double flat_value(int F) {
+  return (F == 0 || F == 1 || F == 4 || F == 6) ? 1.0 : 0.0;
+}
+__host__ __device__ constexpr bool has_flux(int F) { return F >= kK && F < kV; }
+
+// ---------------------------------------------------------------------------
+// Geometry of one cell and its neighbours (periodic)
+// ---------------------------------------------------------------------------
+struct Grid {
+  int32_t nx, ny, nz;
+  int64_t cells;
+};
+
+struct Nbr {
+  int64_t c;      // this cell
+  int64_t ox[3];  // offset along x for c_x = 0, +1, -1
+  int64_t oy[3];
+  int64_t oz[3];
+  __device__ __forceinline__ int64_t at(int cx, int cy, int cz) const {
+    return c + ox[cx == 0 ? 0 : (cx > 0 ? 1 : 2)] + oy[cy == 0 ? 0 : (cy > 0 ? 1 : 2)] +
+           oz[cz == 0 ? 0 : (cz > 0 ? 1 : 2)];
+  }
+};
+
+__device__ __forceinline__ Nbr make_nbr(const Grid& G, int64_t c) {
+  Nbr n;
+  n.c = c;
+  const int64_t plane = (int64_t)G.nx * G.ny;
+  const int32_t x = (int32_t)(c % G.nx);
+  const int64_t t = c / G.nx;
+  const int32_t y = (int32_t)(t % G.ny);
+  const int32_t z = (int32_t)(t / G.ny);
+  n.ox[0] = 0;
+  n.ox[1] = (x + 1 == G.nx) ? -(int64_t)(G.nx - 1) : 1;
+  n.ox[2] = (x == 0) ? (int64_t)(G.nx - 1) : -1;
+  n.oy[0] = 0;
+  n.oy[1] = ((y + 1 == G.ny) ? -(int64_t)(G.ny - 1) : 1) * (int64_t)G.nx;
+  n.oy[2] = ((y == 0) ? (int64_t)(G.ny - 1) : -1) * (int64_t)G.nx;
+  n.oz[0] = 0;
+  n.oz[1] = ((z + 1 == G.nz) ? -(int64_t)(G.nz - 1) : 1) * plane;
+  n.oz[2] = ((z == 0) ? (int64_t)(G.nz - 1) : -1) * plane;
+  return n;
+}
+
+// Where f_{F,l}(x) of the current state lives, for each layout.
+template <int Q, int LAYOUT>
+__device__ __forceinline__ int64_t read_index(const Nbr& n, int64_t cells, int F, int l) {
+  using L = Lattice<Q>;
+  if (LAYOUT == kAAOdd)
+    return (int64_t)(F * Q + opposite(l)) * cells + n.at(-L::c(l, 0), -L::c(l, 1), -L::c(l, 2));
+  return (int64_t)(F * Q + l) * cells + n.c;
+}
+// Where f*_{F,l}(x) goes.
+template <int Q, int LAYOUT>
+__device__ __forceinline__ int64_t write_index(const Nbr& n, int64_t cells, int F, int l) {
+  using L = Lattice<Q>;
+  if (LAYOUT == kAAEven) return (int64_t)(F * Q + opposite(l)) * cells + n.c;
+  return (int64_t)(F * Q + l) * cells + n.at(L::c(l, 0), L::c(l, 1), L::c(l, 2));
+}
+
+// ---------------------------------------------------------------------------
+// Field split between the P threads that share one cell
+// ---------------------------------------------------------------------------
+// With two threads per cell, thread g takes 8 fields; both lists put the
+// flux-free fields first and three K components last, so the j-th field of
+// either thread has the same kind and all indexing stays compile-time.
+__host__ __device__ constexpr int field_of(int P, int g, int j) {
+  return P == 1 ? j
+                : (g == 0 ? (j == 0 ? 0 : j == 1 ? 1 : j == 2 ? 2 : j == 3 ? 3 : j == 4 ? 13
+                                                     : j == 5 ? 7 : j == 6 ? 8 : 9)
+                          : (j == 0 ? 4 : j == 1 ? 5 : j == 2 ? 6 : j == 3 ? 14 : j == 4 ? 15
+                                                     : j == 5 ? 10 : j == 6 ? 11 : 12));
+}
+
+// ---------------------------------------------------------------------------
+// Step arguments
+// ---------------------------------------------------------------------------
+template <class S, class C>
+struct StepArgs {
+  const S* fin;
+  S* fout;
+  const C* aux;  // 7 planes: ln(alpha~) or log1p(alpha~ - 1); gamma~ or gamma~ - delta
+  int* flag;     // set to 1 when a non-finite moment is seen
+  Grid G;
+  C inv2dx, inv4dx;  // 1/(2 dx), 1/(4 dx)
+  C half_dt, omega, omc, sigma;  // dt/2, 1/tau, 1 - 1/tau, dt (1 - 1/(2 tau))
+  int slicing;
+  int sources_on;
+};
+
+// A_k and D_kij by central differences of the aux planes (reading: second
+// order differences of ln alpha and gamma_ij / 2).
+template <int Q, class C>
+__device__ __forceinline__ void derivatives(const Nbr& n, int64_t cells, const C* __restrict__ aux,
+                                            C inv2dx, C inv4dx, C A[3], C D[3][6]) {
+  constexpr int dim = Lattice<Q>::kDim;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (k < dim) {
+      const int64_t cp = n.at(k == 0, k == 1, k == 2);
+      const int64_t cm = n.at(-(k == 0), -(k == 1), -(k == 2));
+      A[k] = (__ldg(aux + cp) - __ldg(aux + cm)) * inv2dx;
+#pragma unroll
+      for (int q = 0; q < 6; ++q)
+        D[k][q] = (__ldg(aux + (int64_t)(1 + q) * cells + cp) -
+                   __ldg(aux + (int64_t)(1 + q) * cells + cm)) * inv4dx;
+    } else {
+      A[k] = C(0);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) D[k][q] = C(0);
+    }
+  }
+}
+
+// Unpacks 16 moments (ABS: the values; DEV: deviations from flat space) into
+// the state the physics needs.
+template <int REP, class C>
+__device__ __forceinline__ void unpack(const C m[kNF], C& alpha, C g[6], C K[6], C V[3]) {
+  alpha = REP == kDEV ? C(1) + m[0] : m[0];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    g[q] = (REP == kDEV && (q == 0 || q == 3 || q == 5)) ? C(1) + m[kG + q] : m[kG + q];
+    K[q] = m[kK + q];
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) V[k] = m[kV + k];
+}
+
+// ---------------------------------------------------------------------------
+// k_collide: the fused step
+// ---------------------------------------------------------------------------
+template <int Q, class S, class C, int REP, int LAYOUT, int P, bool HOLD>
+__global__ void __launch_bounds__(128) k_collide(const StepArgs<S, C> a) {
+  using L = Lattice<Q>;
+  constexpr int NJ = kNF / P;
+  constexpr int dim = L::kDim;
+  const int lane = threadIdx.x & 31;
+  const int g = P == 2 ? (lane >> 4) : 0;
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t cell = P == 2 ? ((gtid >> 5) << 4) + (lane & 15) : gtid;
+  const bool valid = cell < a.G.cells;
+  const int64_t c = valid ? cell : a.G.cells - 1;
+  const int64_t cells = a.G.cells;
+  const Nbr n = make_nbr(a.G, c);
+
+  // Pass 1: zeroth moments of this thread's fields (ascending l).
+  C fv[HOLD ? NJ : 1][HOLD ? Q : 1];
+  C mine[NJ];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    const int F = g ? field_of(P, 1, j) : field_of(P, 0, j);
+    C s = C(0);
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+      const C v = HOLD ? Codec<S>::load(a.fin + read_index<Q, LAYOUT>(n, cells, F, l))
+                       : Codec<S>::load_keep(a.fin + read_index<Q, LAYOUT>(n, cells, F, l));
+      if (HOLD) fv[HOLD ? j : 0][HOLD ? l : 0] = v;
+      s += REP == kDEV ? C(L::w(l)) * v : v;
+    }
+    mine[j] = s;
+  }
+  C rt[kNF];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    if (P == 1) {
+      rt[j] = mine[j];
+    } else {
+      const C other = __shfl_xor_sync(0xffffffffu, mine[j], 16);
+      rt[field_of(P, 0, j)] = g ? other : mine[j];
+      rt[field_of(P, 1, j)] = g ? mine[j] : other;
+    }
+  }
+  {
+    C chk = C(0);
+#pragma unroll
+    for (int F = 0; F < kNF; ++F) chk += rt[F];
+    if (valid && g == 0 && !isfinite(chk)) atomicOr(a.flag, 1);
+  }
+
+  // Derivatives, sources at rho~, corrected rho, flux at rho.
+  C A[3], D[3][6];
+  derivatives<Q, C>(n, cells, a.aux, a.inv2dx, a.inv4dx, A, D);
+  C alpha, gm[6], K[6], V[3];
+  unpack<REP, C>(rt, alpha, gm, K, V);
+  C Sr[kNF];
+  bm_sources<C>(alpha, gm, K, V, A, D, a.slicing, Sr);
+  if (!a.sources_on) {
+#pragma unroll
+    for (int F = 0; F < kNF; ++F) Sr[F] = C(0);
+  }
+  C rho[kNF];  // ABS: rho; DEV: rho - rho_flat
+#pragma unroll
+  for (int F = 0; F < kNF; ++F) rho[F] = rt[F] + a.half_dt * Sr[F];
+  C Fl[6][3];
+  {
+    C alpha2, g2[6], K2[6], V2[3];
+    unpack<REP, C>(rho, alpha2, g2, K2, V2);
+    bm_flux<C, dim>(alpha2, g2, V2, A, D, Fl);
+  }
+  // Per-field coefficients: coef = omega rho + sigma S; flux scaled by 3 omega.
+  C coef[kNF];
+#pragma unroll
+  for (int F = 0; F < kNF; ++F) coef[F] = a.omega * rho[F] + a.sigma * Sr[F];
+  const C three_omega = C(3) * a.omega;
+
+  // Pass 2: relax, add the source, stream.
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    const int F0 = field_of(P, 0, j), F1 = field_of(P, 1, j);
+    const int F = g ? F1 : F0;
+    const C cf = g ? coef[F1] : coef[F0];
+    C b[3] = {C(0), C(0), C(0)};
+    if (has_flux(F0)) {
+#pragma unroll
+      for (int k = 0; k < dim; ++k)
+        b[k] = three_omega * (g ? Fl[F1 - kK][k] : Fl[F0 - kK][k]);
+    }
+    // All Q values of this field are read before any is written: in place
+    // (AA) the field's reads and writes touch the same Q locations.
+    C v_[Q];
+#pragma unroll
+    for (int l = 0; l < Q; ++l)
+      v_[l] = HOLD ? fv[HOLD ? j : 0][HOLD ? l : 0]
+                   : Codec<S>::load_keep(a.fin + read_index<Q, LAYOUT>(n, cells, F, l));
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+      const C v = v_[l];
+      C t = cf;
+      if (has_flux(F0)) {
+#pragma unroll
+        for (int k = 0; k < dim; ++k) {
+          if (L::c(l, k) > 0) t += b[k];
+          if (L::c(l, k) < 0) t -= b[k];
+        }
+      }
+      const C out = REP == kDEV ? fma(a.omc, v, t) : fma(a.omc, v, C(L::w(l)) * t);
+      if (valid) Codec<S>::store(a.fout + write_index<Q, LAYOUT>(n, cells, F, l), out);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_aux: ln(alpha~) and gamma~ (or their deviations) for the stencil
+// ---------------------------------------------------------------------------
+template <int Q, class S, class C, int REP, int LAYOUT>
+__global__ void __launch_bounds__(256) k_aux(const S* __restrict__ f, C* __restrict__ aux, Grid G) {
+  using L = Lattice<Q>;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= G.cells) return;
+  const Nbr n = make_nbr(G, c);
+#pragma unroll
+  for (int F = 0; F < 7; ++F) {
+    C s = C(0);
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+      const C v = Codec<S>::load_keep(f + read_index<Q, LAYOUT>(n, G.cells, F, l));
+      s += REP == kDEV ? C(L::w(l)) * v : v;
+    }
+    if (F == 0) s = REP == kDEV ? log1p(s) : log(s);
+    aux[(int64_t)F * G.cells + c] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 kernels outside the hot loop: init, moments, constraints, transfers
+// ---------------------------------------------------------------------------
+template <class S>
+struct Init64Args {
+  const double* fields;  // [16][cells]
+  S* f;                  // standard layout
+  int* flag;
+  Grid G;
+  double inv2dx, inv4dx, half_dt;
+  int slicing, sources_on;
+};
+
+// Shifted equilibrium: f = f_eq(rho0) - (dt/2) w_l S(rho0), A and D from rho0.
+template <int Q, class S, int REP>
+__global__ void __launch_bounds__(128) k_init(const Init64Args<S> a) {
+  using L = Lattice<Q>;
+  constexpr int dim = L::kDim;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= a.G.cells) return;
+  const int64_t cells = a.G.cells;
+  const Nbr n = make_nbr(a.G, c);
+  double r[kNF];
+#pragma unroll
+  for (int F = 0; F < kNF; ++F) r[F] = a.fields[(int64_t)F * cells + c];
+  double A[3], D[3][6];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (k < dim) {
+      const int64_t cp = n.at(k == 0, k == 1, k == 2);
+      const int64_t cm = n.at(-(k == 0), -(k == 1), -(k == 2));
+      A[k] = (log(a.fields[cp]) - log(a.fields[cm])) * a.inv2dx;
+#pragma unroll
+      for (int q = 0; q < 6; ++q)
+        D[k][q] = (a.fields[(int64_t)(1 + q) * cells + cp] - a.fields[(int64_t)(1 + q) * cells + cm]) *
+                  a.inv4dx;
+    } else {
+      A[k] = 0;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) D[k][q] = 0;
+    }
+  }
+  double alpha, gm[6], K[6], V[3];
+  unpack<kABS, double>(r, alpha, gm, K, V);
+  double Sr[kNF];
+  bm_sources<double>(alpha, gm, K, V, A, D, a.slicing, Sr);
+  if (!a.sources_on)
+    for (int F = 0; F < kNF; ++F) Sr[F] = 0;
+  double Fl[6][3];
+  bm_flux<double, dim>(alpha, gm, V, A, D, Fl);
+  bool bad = false;
+#pragma unroll
+  for (int F = 0; F < kNF; ++F) {
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+      double cf = 0;
+      if (has_flux(F)) {
+#pragma unroll
+        for (int k = 0; k < dim; ++k) cf += L::c(l, k) * Fl[F - kK][k];
+      }
+      // f = w (rho + 3 c.F) - (dt/2) w S
+      double v;
+      if (REP == kDEV)
+        v = (r[F] - flat_value(F)) + 3.0 * cf - a.half_dt * Sr[F];
+      else
+        v = L::w(l) * (r[F] + 3.0 * cf) - a.half_dt * L::w(l) * Sr[F];
+      bad |= !isfinite(v);
+      Codec<S>::store(a.f + (int64_t)(F * Q + l) * cells + c, (decltype(Codec<S>::load(a.f)))v);
+    }
+  }
+  if (bad) atomicOr(a.flag, 1);
+}
+
+// Sums of all 16 fields in FP64 (rho~ -> macro), ln alpha~ / gamma~ (-> aux64),
+// and per-block partial sums of rho~ (-> partials[block][6 + F]).
+template <int Q, class S, int REP, int LAYOUT>
+__global__ void __launch_bounds__(256) k_sum64(const S* __restrict__ f, double* __restrict__ macro,
+                                               double* __restrict__ aux64, double* partials,
+                                               Grid G) {
+  using L = Lattice<Q>;
+  __shared__ double red[8][kNF];
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = c < G.cells;
+  const Nbr n = make_nbr(G, valid ? c : 0);
+  double m[kNF];
+#pragma unroll
+  for (int F = 0; F < kNF; ++F) {
+    double s = 0;
+    if (valid) {
+#pragma unroll
+      for (int l = 0; l < Q; ++l) {
+        const double v = (double)Codec<S>::load_keep(f + read_index<Q, LAYOUT>(n, G.cells, F, l));
+        s += REP == kDEV ? L::w(l) * v : v;
+      }
+      if (REP == kDEV) s += flat_value(F);
+      macro[(int64_t)F * G.cells + c] = s;
+      if (F < 7) aux64[(int64_t)F * G.cells + c] = F == 0 ? log(s) : s;
+    }
+    m[F] = s;
+  }
+  // block reduction in a fixed order
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int F = 0; F < kNF; ++F) {
+    double v = m[F];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][F] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kNF) {
+    double v = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][threadIdx.x];
+    partials[(int64_t)blockIdx.x * 22 + 6 + threadIdx.x] = v;
+  }
+}
+
+// rho = rho~ + dt S(rho~)/2 in place (FP64), derivatives from aux64.
+template <int Q>
+__global__ void __launch_bounds__(128) k_correct64(double* __restrict__ macro,
+                                                   const double* __restrict__ aux64, Grid G,
+                                                   double inv2dx, double inv4dx, double half_dt,
+                                                   int slicing, int sources_on) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= G.cells || !sources_on) return;
+  const Nbr n = make_nbr(G, c);
+  double r[kNF];
+#pragma unroll
+  for (int F = 0; F < kNF; ++F) r[F] = macro[(int64_t)F * G.cells + c];
+  double A[3], D[3][6];
+  derivatives<Q, double>(n, G.cells, aux64, inv2dx, inv4dx, A, D);
+  double alpha, gm[6], K[6], V[3];
+  unpack<kABS, double>(r, alpha, gm, K, V);
+  double S[kNF];
+  bm_sources<double>(alpha, gm, K, V, A, D, slicing, S);
+#pragma unroll
+  for (int F = 0; F < kNF; ++F) macro[(int64_t)F * G.cells + c] = r[F] + half_dt * S[F];
+}
+
+// Christoffel symbols Gamma^k_ij (and the inverse metric, D) at a cell from
+// central differences of the corrected metric.
+template <int Q>
+__device__ __forceinline__ void christoffel64(const double* __restrict__ macro, const Grid& G,
+                                              int64_t c, double inv4dx, double Gam[3][6],
+                                              double gi[6], double D[3][6]) {
+  constexpr int dim = Lattice<Q>::kDim;
+  const Nbr n = make_nbr(G, c);
+  double g[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) g[q] = macro[(int64_t)(1 + q) * G.cells + c];
+  invert_sym3(g, gi);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (k < dim) {
+      const int64_t cp = n.at(k == 0, k == 1, k == 2);
+      const int64_t cm = n.at(-(k == 0), -(k == 1), -(k == 2));
+#pragma unroll
+      for (int q = 0; q < 6; ++q)
+        D[k][q] = (macro[(int64_t)(1 + q) * G.cells + cp] - macro[(int64_t)(1 + q) * G.cells + cm]) *
+                  inv4dx;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 6; ++q) D[k][q] = 0;
+    }
+  }
+  // Gamma_mij = D_ijm + D_jim - D_mij ; Gamma^k_ij = g^{km} Gamma_mij
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      double low[3];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) low[m] = D[i][sym(j, m)] + D[j][sym(i, m)] - D[m][sym(i, j)];
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        Gam[k][sym(i, j)] = gi[sym(k, 0)] * low[0] + gi[sym(k, 1)] * low[1] + gi[sym(k, 2)] * low[2];
+    }
+}
+
+__device__ __forceinline__ double trK64(const double* __restrict__ macro, int64_t cells, int64_t c) {
+  double g[6], gi[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) g[q] = macro[(int64_t)(1 + q) * cells + c];
+  invert_sym3(g, gi);
+  double t = 0;
+#pragma unroll
+  for (int q = 0; q < 6; ++q)
+    t += (q == 1 || q == 2 || q == 4 ? 2.0 : 1.0) * gi[q] * macro[(int64_t)(kK + q) * cells + c];
+  return t;
+}
+
+// Hamiltonian, momentum and V constraints per cell (FP64), reduced per block
+// into partials[block][0..5] = sum H^2, max|H|, sum |M|^2, max|M_i|,
+// sum |C|^2, max|C_k|.
+template <int Q>
+__global__ void __launch_bounds__(128) k_constraints64(const double* __restrict__ macro, Grid G,
+                                                       double inv2dx, double inv4dx,
+                                                       double* partials) {
+  constexpr int dim = Lattice<Q>::kDim;
+  __shared__ double red[4][6];
+  const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = cell < G.cells;
+  const int64_t c = valid ? cell : 0;
+  const Nbr n = make_nbr(G, c);
+  double Gam[3][6], gi[6], D[3][6];
+  christoffel64<Q>(macro, G, c, inv4dx, Gam, gi, D);
+  // d_m Gamma^k_ij
+  double dGam[3][3][6];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    if (m < dim) {
+      double Gp[3][6], Gm[3][6], t1[6], t2[3][6];
+      christoffel64<Q>(macro, G, n.at(m == 0, m == 1, m == 2), inv4dx, Gp, t1, t2);
+      christoffel64<Q>(macro, G, n.at(-(m == 0), -(m == 1), -(m == 2)), inv4dx, Gm, t1, t2);
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) dGam[m][k][q] = (Gp[k][q] - Gm[k][q]) * inv2dx;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) dGam[m][k][q] = 0;
+    }
+  }
+  // R = g^{ij} R_ij, R_ij = d_k G^k_ij - d_j G^k_ik + G^k_km G^m_ij - G^k_jm G^m_ik
+  double R = 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      double t = 0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        t += dGam[k][k][sym(i, j)] - dGam[j][k][sym(i, k)];
+#pragma unroll
+        for (int m = 0; m < 3; ++m)
+          t += Gam[k][sym(k, m)] * Gam[m][sym(i, j)] - Gam[k][sym(j, m)] * Gam[m][sym(i, k)];
+      }
+      R += gi[sym(i, j)] * t;
+    }
+  double K[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) K[q] = macro[(int64_t)(kK + q) * G.cells + c];
+  double Km[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      Km[i][j] = gi[sym(i, 0)] * K[sym(0, j)] + gi[sym(i, 1)] * K[sym(1, j)] + gi[sym(i, 2)] * K[sym(2, j)];
+  double trK = Km[0][0] + Km[1][1] + Km[2][2], trK2 = 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) trK2 += Km[i][j] * Km[j][i];
+  const double H = R - trK2 + trK * trK;
+  // momentum constraint
+  double dK[3][6], dtr[3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    if (m < dim) {
+      const int64_t cp = n.at(m == 0, m == 1, m == 2), cm = n.at(-(m == 0), -(m == 1), -(m == 2));
+#pragma unroll
+      for (int q = 0; q < 6; ++q)
+        dK[m][q] = (macro[(int64_t)(kK + q) * G.cells + cp] - macro[(int64_t)(kK + q) * G.cells + cm]) *
+                   inv2dx;
+      dtr[m] = (trK64(macro, G.cells, cp) - trK64(macro, G.cells, cm)) * inv2dx;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 6; ++q) dK[m][q] = 0;
+      dtr[m] = 0;
+    }
+  }
+  double M2 = 0, Mi = 0, C2 = 0, Ci = 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    double t = 0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        double cov = dK[j][sym(k, i)];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) cov -= Gam[m][sym(j, k)] * K[sym(m, i)] + Gam[m][sym(j, i)] * K[sym(k, m)];
+        t += gi[sym(j, k)] * cov;
+      }
+    t -= dtr[i];
+    M2 += t * t;
+    Mi = fmax(Mi, fabs(t));
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double t1 = 0, t2 = 0;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        t1 += gi[sym(r, m)] * D[k][sym(r, m)];
+        t2 += gi[sym(r, m)] * D[m][sym(r, k)];
+      }
+    const double cv = macro[(int64_t)(kV + k) * G.cells + c] - (t1 - t2);
+    C2 += cv * cv;
+    Ci = fmax(Ci, fabs(cv));
+  }
+  double v[6] = {H * H, fabs(H), M2, Mi, C2, Ci};
+  if (!valid) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) v[i] = 0;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    double x = v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double y = __shfl_xor_sync(0xffffffffu, x, o);
+      x = (i & 1) ? fmax(x, y) : x + y;
+    }
+    if (lane == 0) red[warp][i] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    const int i = threadIdx.x;
+    double x = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x = (i & 1) ? fmax(x, red[w][i]) : x + red[w][i];
+    partials[(int64_t)blockIdx.x * 22 + i] = x;
+  }
+}
+
+// Plane transfer between the FP64 standard layout and the stored state.
+template <int Q, class S, int REP, int LAYOUT>
+__global__ void k_get_plane(const S* __restrict__ f, double* __restrict__ out, Grid G, int F, int l) {
+  using L = Lattice<Q>;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= G.cells) return;
+  const Nbr n = make_nbr(G, c);
+  const double v = (double)Codec<S>::load_keep(f + read_index<Q, LAYOUT>(n, G.cells, F, l));
+  double w = 0;
+#pragma unroll
+  for (int ll = 0; ll < Q; ++ll)
+    if (ll == l) w = L::w(ll);
+  out[c] = REP == kDEV ? w * (v + flat_value(F)) : v;
+}
+
+template <int Q, class S, int REP, int LAYOUT>
+__global__ void k_set_plane(S* __restrict__ f, const double* __restrict__ in, Grid G, int F, int l) {
+  using L = Lattice<Q>;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= G.cells) return;
+  const Nbr n = make_nbr(G, c);
+  double w = 0;
+#pragma unroll
+  for (int ll = 0; ll < Q; ++ll)
+    if (ll == l) w = L::w(ll);
+  const double v = REP == kDEV ? in[c] / w - flat_value(F) : in[c];
+  Codec<S>::store(f + read_index<Q, LAYOUT>(n, G.cells, F, l), (decltype(Codec<S>::load(f)))v);
+}
+
+// Distributions of selected cells: out[i][F][l] = f_{F,l}(idx[i]) in FP64.
+template <int Q, class S, int REP, int LAYOUT>
+__global__ void k_get_cells(const S* __restrict__ f, const int64_t* __restrict__ idx, int64_t n,
+                            double* __restrict__ out, Grid G) {
+  using L = Lattice<Q>;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * kNF) return;
+  const int64_t i = t / kNF;
+  const int F = (int)(t % kNF);
+  const Nbr nb = make_nbr(G, idx[i]);
+#pragma unroll
+  for (int l = 0; l < Q; ++l) {
+    const double v = (double)Codec<S>::load_keep(f + read_index<Q, LAYOUT>(nb, G.cells, F, l));
+    out[(i * kNF + F) * Q + l] = REP == kDEV ? L::w(l) * (v + flat_value(F)) : v;
+  }
+}
+
+}  // namespace lbnr

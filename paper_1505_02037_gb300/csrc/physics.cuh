@@ -1,0 +1,231 @@
+// Pointwise Bona-Masso right-hand sides at zero shift in vacuum
+// (Ilseven & Mendoza, arXiv:1505.02037, Sec. "Bona-Masso evolution
+// equations"; Eq. alfan for the lapse, the three-metric equation, the
+// extrinsic-curvature flux lambda^k_ij and source S_ij, and Eq. Vsor for
+// Omega_k).
+//
+// Symmetric tensors are held as their 6 independent components
+// (xx, xy, xz, yy, yz, zz); D_kij as D[k][6]. All loops are unrolled so
+// every index is a compile-time constant and every array lives in registers.
+//
+// Index placement: raised indices use the inverse three-metric g^{ij};
+// D_kr^r = g^{rm} D_krm, D^r_rk = g^{rm} D_mrk, D_k^{rs} = g^{ra} g^{sb} D_kab,
+// D^k_ij = g^{km} D_mij. The second term of the gamma_ij/4 bracket of S_ij is
+// taken as D_kr^r D^{ks}_s: with that placement the K equation equals the ADM
+// evolution minus (alpha/4) gamma_ij times the Hamiltonian constraint, as the
+// paper's "Einstein evolution system" requires.
+#pragma once
+
+namespace lbnr {
+
+__host__ __device__ constexpr int sym(int i, int j) {
+  return i > j ? sym(j, i) : (i == 0 ? j : (i == 1 ? 2 + j : 5));
+}
+
+template <class T>
+struct Geometry {
+  T gi[6];  // inverse metric
+};
+
+template <class T>
+__device__ __forceinline__ void invert_sym3(const T g[6], T gi[6]) {
+  const T c00 = g[3] * g[5] - g[4] * g[4];
+  const T c01 = g[2] * g[4] - g[1] * g[5];
+  const T c02 = g[1] * g[4] - g[2] * g[3];
+  const T det = g[0] * c00 + g[1] * c01 + g[2] * c02;
+  const T inv = T(1) / det;
+  gi[0] = c00 * inv;
+  gi[1] = c01 * inv;
+  gi[2] = c02 * inv;
+  gi[3] = (g[0] * g[5] - g[2] * g[2]) * inv;
+  gi[4] = (g[1] * g[2] - g[0] * g[4]) * inv;
+  gi[5] = (g[0] * g[3] - g[1] * g[1]) * inv;
+}
+
+// The 16 field values in storage order: alpha, gamma(6), K(6), V(3).
+enum : int { kAlpha = 0, kG = 1, kK = 7, kV = 13, kNF = 16 };
+
+// Sources S_F of all 16 fields (d_t of each field less its flux divergence)
+// at the state (alpha, gamma, K, V) with derivatives A_k, D_kij.
+template <class T>
+__device__ __forceinline__ void bm_sources(const T alpha, const T g[6], const T K[6],
+                                           const T V[3], const T A[3], const T D[3][6],
+                                           int slicing, T S[kNF]) {
+  T gi[6];
+  invert_sym3(g, gi);
+
+  // K^i_j = g^{im} K_mj (not symmetric in general)
+  T Km[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      Km[i][j] = gi[sym(i, 0)] * K[sym(0, j)] + gi[sym(i, 1)] * K[sym(1, j)] +
+                 gi[sym(i, 2)] * K[sym(2, j)];
+  const T trK = Km[0][0] + Km[1][1] + Km[2][2];
+  T trK2 = T(0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) trK2 += Km[i][j] * Km[j][i];
+
+  // D_ki^r = D_kim g^{mr}
+  T Dl[3][3][3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+        Dl[k][i][r] = D[k][sym(i, 0)] * gi[sym(0, r)] + D[k][sym(i, 1)] * gi[sym(1, r)] +
+                      D[k][sym(i, 2)] * gi[sym(2, r)];
+  // traces: D_kr^r and D^r_rk
+  T tr1[3], tr2[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    tr1[k] = Dl[k][0][0] + Dl[k][1][1] + Dl[k][2][2];
+    tr2[k] = Dl[0][k][0] + Dl[1][k][1] + Dl[2][k][2];
+  }
+  // raised vectors
+  T Au[3], Vu[3], tr1u[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    Au[k] = gi[sym(k, 0)] * A[0] + gi[sym(k, 1)] * A[1] + gi[sym(k, 2)] * A[2];
+    Vu[k] = gi[sym(k, 0)] * V[0] + gi[sym(k, 1)] * V[1] + gi[sym(k, 2)] * V[2];
+    tr1u[k] = gi[sym(k, 0)] * tr1[0] + gi[sym(k, 1)] * tr1[1] + gi[sym(k, 2)] * tr1[2];
+  }
+  // D^k_ij = g^{km} D_mij (symmetric in ij)
+  T Du[3][6];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+      Du[k][q] = gi[sym(k, 0)] * D[0][q] + gi[sym(k, 1)] * D[1][q] + gi[sym(k, 2)] * D[2][q];
+  // Christoffel symbols Gamma^k_ij = D_ij^k + D_ji^k - D^k_ij
+  T Gam[3][6];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i; j < 3; ++j) Gam[k][sym(i, j)] = Dl[i][j][k] + Dl[j][i][k] - Du[k][sym(i, j)];
+  // Gamma^k_kr
+  T Gc[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+    Gc[r] = Gam[0][sym(0, r)] + Gam[1][sym(1, r)] + Gam[2][sym(2, r)];
+  // D_k^{kr} = g^{ka} D_ka^r
+  T Dkk[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    T t = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) t += gi[sym(k, a)] * Dl[k][a][r];
+    Dkk[r] = t;
+  }
+  // D_k^{rs} Gamma^k_rs, with D_k^{rs} = g^{ra} D_ka^s
+  T DG = T(0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int s = 0; s < 3; ++s) {
+        const T Duu = gi[sym(r, 0)] * Dl[k][0][s] + gi[sym(r, 1)] * Dl[k][1][s] +
+                      gi[sym(r, 2)] * Dl[k][2][s];
+        DG += Duu * Gam[k][sym(r, s)];
+      }
+  const T bracket = -DG + (tr1[0] * tr1u[0] + tr1[1] * tr1u[1] + tr1[2] * tr1u[2]) -
+                    T(2) * (Vu[0] * A[0] + Vu[1] * A[1] + Vu[2] * A[2]) + trK2 - trK * trK;
+
+  // S_ij
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      const int q = sym(i, j);
+      // -2 K_ik K^k_j + trK K_ij
+      T t = -T(2) * (K[sym(i, 0)] * Km[0][j] + K[sym(i, 1)] * Km[1][j] + K[sym(i, 2)] * Km[2][j]) +
+            trK * K[q];
+      // 2 D_ik^r D_rj^k + 2 D_jk^r D_ri^k ; Gamma^k_kr Gamma^r_ij - Gamma^k_ri Gamma^r_kj
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+          t += T(2) * (Dl[i][k][r] * Dl[r][j][k] + Dl[j][k][r] * Dl[r][i][k]) -
+               Gam[k][sym(r, i)] * Gam[r][sym(k, j)];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        t += Gc[r] * Gam[r][q];
+        // -(2 D_k^{kr} - A^r)(D_ijr + D_jir)
+        t -= (T(2) * Dkk[r] - Au[r]) * (D[i][sym(j, r)] + D[j][sym(i, r)]);
+        // - V^k D_kij
+        t -= Vu[r] * D[r][q];
+      }
+      // A_i (V_j - D_jk^k / 2) + A_j (V_i - D_ik^k / 2)
+      t += A[i] * (V[j] - T(0.5) * tr1[j]) + A[j] * (V[i] - T(0.5) * tr1[i]);
+      t += T(0.25) * g[q] * bracket;
+      S[kK + q] = alpha * t;
+    }
+
+  // Omega_k (Eq. Vsor at zero shift, vacuum)
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    T t = A[0] * Km[0][k] + A[1] * Km[1][k] + A[2] * Km[2][k] - trK * A[k];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+#pragma unroll
+      for (int s = 0; s < 3; ++s) t += (Dl[k][r][s] - T(2) * Dl[r][k][s]) * Km[r][s];
+      t -= Km[r][k] * (tr1[r] - T(2) * tr2[r]);
+    }
+    S[kV + k] = alpha * t;
+  }
+
+  // Lapse (Eq. alfan, beta = 0) and metric (beta = 0, s_ij = 0)
+  const T Qg = slicing == 1 ? trK : (slicing == 2 ? trK / alpha : T(0));
+  S[kAlpha] = -alpha * alpha * Qg;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) S[kG + q] = -T(2) * alpha * K[q];
+}
+
+// Flux of K_ij along axis k: alpha lambda^k_ij, with
+// lambda^k_ij = D^k_ij + 1/2 delta^k_i (A_j + 2 V_j - D_jr^r)
+//             + 1/2 delta^k_j (A_i + 2 V_i - D_ir^r) - 1/2 V^k gamma_ij.
+// Only the first `dim` axes are formed (the lattice has no other velocities).
+template <class T, int dim>
+__device__ __forceinline__ void bm_flux(const T alpha, const T g[6], const T V[3], const T A[3],
+                                        const T D[3][6], T F[6][3]) {
+  T gi[6];
+  invert_sym3(g, gi);
+  T tr1[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    tr1[k] = gi[0] * D[k][0] + gi[3] * D[k][3] + gi[5] * D[k][5] +
+             T(2) * (gi[1] * D[k][1] + gi[2] * D[k][2] + gi[4] * D[k][4]);
+  T e[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) e[i] = T(0.5) * (A[i] + T(2) * V[i] - tr1[i]);
+#pragma unroll
+  for (int k = 0; k < dim; ++k) {
+    const T Vu = gi[sym(k, 0)] * V[0] + gi[sym(k, 1)] * V[1] + gi[sym(k, 2)] * V[2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i; j < 3; ++j) {
+        const int q = sym(i, j);
+        T l = gi[sym(k, 0)] * D[0][q] + gi[sym(k, 1)] * D[1][q] + gi[sym(k, 2)] * D[2][q] -
+              T(0.5) * Vu * g[q];
+        if (k == i) l += e[j];
+        if (k == j) l += e[i];
+        F[q][k] = alpha * l;
+      }
+  }
+#pragma unroll
+  for (int k = dim; k < 3; ++k)
+#pragma unroll
+    for (int q = 0; q < 6; ++q) F[q][k] = T(0);
+}
+
+}  // namespace lbnr

@@ -1,0 +1,282 @@
+"""Thin Python binding of the lbnr C-ABI (include/lbnr.h).
+
+Every function here only marshals arguments: the lattice Boltzmann step,
+the moments and the constraint reductions all run in liblbnr.so's CUDA
+kernels. PyTorch provides the device memory (one uint8 tensor handed to the
+library as its workspace) and the CUDA stream. There is no CPU fallback: if
+the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LBNR_D1Q3, LBNR_D2Q9, LBNR_D3Q19 = 1, 2, 3
+LBNR_F64, LBNR_F32, LBNR_DEV_F32, LBNR_DEV_BF16, LBNR_DEV_F16 = 0, 1, 2, 3, 4
+LBNR_GEODESIC, LBNR_HARMONIC, LBNR_ONE_PLUS_LOG = 0, 1, 2
+LBNR_STREAM_AUTO, LBNR_STREAM_PINGPONG, LBNR_STREAM_AA = 0, 1, 2
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENONFINITE", -5: "ETIMEOUT",
+          -6: "ESTATE"}
+Q_OF = {1: 3, 2: 9, 3: 19}
+STORAGE_NAMES = {"f64": 0, "f32": 1, "dev_f32": 2, "dev_bf16": 3, "dev_f16": 4}
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("slicing", ctypes.c_int32), ("storage", ctypes.c_int32),
+                ("streaming", ctypes.c_int32), ("sources_on", ctypes.c_int32),
+                ("cuda_stream", ctypes.c_void_p), ("dev_buffer", ctypes.c_void_p),
+                ("dev_bytes", ctypes.c_uint64)]
+
+
+class LbnrError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"lbnr error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class NonFiniteError(LbnrError):
+    pass
+
+
+_lib = None
+
+
+def library(path: str | None = None):
+    """Loads liblbnr.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or os.environ.get("LBNR_LIB") or _build.build()
+    L = ctypes.CDLL(path)
+    vp, i64, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+    L.lbnr_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    L.lbnr_default_opts.restype = None
+    L.lbnr_workspace_bytes.argtypes = [ctypes.POINTER(Grid), ctypes.c_int, ctypes.POINTER(Opts),
+                                       ctypes.POINTER(ctypes.c_uint64)]
+    L.lbnr_create.argtypes = [ctypes.POINTER(Grid), ctypes.c_int, ctypes.c_double,
+                              ctypes.c_double, ctypes.c_double, ctypes.POINTER(Opts),
+                              ctypes.POINTER(vp)]
+    for name in ("lbnr_init", "lbnr_moments", "lbnr_constraints", "lbnr_get_distributions",
+                 "lbnr_set_distributions"):
+        getattr(L, name).argtypes = [vp, dp]
+    L.lbnr_get_cells.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_int64), dp]
+    L.lbnr_step.argtypes = [vp, i64]
+    L.lbnr_step_timed.argtypes = [vp, i64, dp]
+    L.lbnr_status.argtypes = [vp]
+    L.lbnr_steps_done.argtypes = [vp]
+    L.lbnr_steps_done.restype = i64
+    L.lbnr_q.argtypes = [vp]
+    L.lbnr_streaming.argtypes = [vp]
+    L.lbnr_destroy.argtypes = [vp]
+    L.lbnr_destroy.restype = None
+    L.lbnr_last_error.argtypes = [vp]
+    L.lbnr_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc, ctx=None):
+    if rc == 0:
+        return
+    msg = library().lbnr_last_error(ctx).decode(errors="replace")
+    if rc == -4:
+        raise NonFiniteError(rc, msg)
+    raise LbnrError(rc, msg)
+
+
+def _dptr(a: np.ndarray):
+    if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("expected a C-contiguous float64 array")
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _host_ptr(a):
+    """Pointer of a host float64 buffer: numpy array or (pinned) CPU tensor."""
+    if isinstance(a, np.ndarray):
+        return _dptr(a)
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.device.type != "cpu" or a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("expected a contiguous float64 CPU tensor")
+        return ctypes.cast(ctypes.c_void_p(a.data_ptr()), ctypes.POINTER(ctypes.c_double))
+    raise TypeError(type(a))
+
+
+# ---------------------------------------------------------------------------
+# C-ABI, one Python function per entry point
+# ---------------------------------------------------------------------------
+def lbnr_default_opts() -> Opts:
+    o = Opts()
+    library().lbnr_default_opts(ctypes.byref(o))
+    return o
+
+
+def lbnr_workspace_bytes(grid: Grid, vset: int, opts: Opts) -> int:
+    out = ctypes.c_uint64(0)
+    _check(library().lbnr_workspace_bytes(ctypes.byref(grid), vset, ctypes.byref(opts),
+                                          ctypes.byref(out)))
+    return out.value
+
+
+def lbnr_create(grid: Grid, vset: int, tau: float, dx: float, dt: float, opts: Opts):
+    ctx = ctypes.c_void_p(0)
+    _check(library().lbnr_create(ctypes.byref(grid), vset, tau, dx, dt, ctypes.byref(opts),
+                                 ctypes.byref(ctx)))
+    return ctx
+
+
+def lbnr_init(ctx, fields):
+    _check(library().lbnr_init(ctx, _host_ptr(fields)), ctx)
+
+
+def lbnr_step(ctx, n: int):
+    _check(library().lbnr_step(ctx, int(n)), ctx)
+
+
+def lbnr_step_timed(ctx, n: int):
+    """Runs n steps kernel by kernel; returns (ms in the moment pass,
+    ms in the collide-and-stream kernel)."""
+    ms = np.zeros(2)
+    _check(library().lbnr_step_timed(ctx, int(n), _dptr(ms)), ctx)
+    return float(ms[0]), float(ms[1])
+
+
+def lbnr_moments(ctx, out):
+    _check(library().lbnr_moments(ctx, _host_ptr(out)), ctx)
+
+
+def lbnr_constraints(ctx, out):
+    _check(library().lbnr_constraints(ctx, _host_ptr(out)), ctx)
+
+
+def lbnr_get_distributions(ctx, out):
+    _check(library().lbnr_get_distributions(ctx, _host_ptr(out)), ctx)
+
+
+def lbnr_get_cells(ctx, cells, out):
+    idx = np.ascontiguousarray(np.asarray(cells, dtype=np.int64))
+    _check(library().lbnr_get_cells(ctx, len(idx), idx.ctypes.data_as(
+        ctypes.POINTER(ctypes.c_int64)), _host_ptr(out)), ctx)
+
+
+def lbnr_set_distributions(ctx, arr):
+    _check(library().lbnr_set_distributions(ctx, _host_ptr(arr)), ctx)
+
+
+def lbnr_status(ctx):
+    _check(library().lbnr_status(ctx), ctx)
+
+
+def lbnr_steps_done(ctx) -> int:
+    return library().lbnr_steps_done(ctx)
+
+
+def lbnr_destroy(ctx):
+    library().lbnr_destroy(ctx)
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrapper: one lattice, torch-owned workspace and stream
+# ---------------------------------------------------------------------------
+class Lattice:
+    """One periodic lattice on the current CUDA device.
+
+    vset: 1 D1Q3, 2 D2Q9, 3 D3Q19; shape (nx, ny, nz); tau is tau/dt; dx = dt.
+    storage: "f64", "f32", "dev_f32", "dev_bf16", "dev_f16" (or the code).
+    """
+
+    def __init__(self, vset, shape, tau, dx, dt=None, slicing=LBNR_HARMONIC, storage="f64",
+                 streaming=LBNR_STREAM_AUTO, sources_on=True, stream=None, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("lbnr needs a CUDA device; there is no CPU path")
+        self.torch = torch
+        self.device = torch.device(device or "cuda")
+        library()
+        self.vset = int(vset)
+        self.Q = Q_OF[self.vset]
+        self.shape = tuple(int(s) for s in shape)
+        self.cells = self.shape[0] * self.shape[1] * self.shape[2]
+        self.storage = STORAGE_NAMES.get(storage, storage)
+        self.grid = Grid(*self.shape)
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        o = lbnr_default_opts()
+        o.slicing = int(slicing)
+        o.storage = int(self.storage)
+        o.sources_on = int(bool(sources_on))
+        o.cuda_stream = ctypes.c_void_p(self.stream.cuda_stream)
+        if streaming == LBNR_STREAM_AUTO:
+            o.streaming = LBNR_STREAM_PINGPONG
+            need_pp = lbnr_workspace_bytes(self.grid, self.vset, o)
+            free, _ = torch.cuda.mem_get_info(self.device)
+            streaming = LBNR_STREAM_PINGPONG if need_pp <= 0.9 * free else LBNR_STREAM_AA
+        o.streaming = int(streaming)
+        nbytes = lbnr_workspace_bytes(self.grid, self.vset, o)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        o.dev_buffer = ctypes.c_void_p(self.workspace.data_ptr())
+        o.dev_bytes = nbytes
+        self.opts = o
+        self.tau, self.dx = float(tau), float(dx)
+        self.dt = float(dx if dt is None else dt)
+        self.ctx = lbnr_create(self.grid, self.vset, self.tau, self.dx, self.dt, o)
+        self.streaming = library().lbnr_streaming(self.ctx)
+
+    def init(self, fields):
+        a = fields if not isinstance(fields, np.ndarray) else np.ascontiguousarray(
+            fields, dtype=np.float64).reshape(16, self.cells)
+        lbnr_init(self.ctx, a)
+
+    def step(self, n=1):
+        lbnr_step(self.ctx, n)
+
+    def step_timed(self, n=1):
+        return lbnr_step_timed(self.ctx, n)
+
+    def moments(self, out=None):
+        out = np.empty((16, self.cells)) if out is None else out
+        lbnr_moments(self.ctx, out)
+        return out
+
+    def constraints(self):
+        out = np.empty(22)
+        lbnr_constraints(self.ctx, out)
+        return out
+
+    def distributions(self):
+        out = np.empty((16, self.Q, self.cells))
+        lbnr_get_distributions(self.ctx, out)
+        return out
+
+    def cells_distributions(self, cells):
+        out = np.empty((len(cells), 16, self.Q))
+        lbnr_get_cells(self.ctx, cells, out)
+        return out
+
+    def set_distributions(self, f):
+        lbnr_set_distributions(self.ctx, np.ascontiguousarray(f, dtype=np.float64))
+
+    def status(self):
+        lbnr_status(self.ctx)
+
+    @property
+    def steps_done(self):
+        return lbnr_steps_done(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            lbnr_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,84 @@
+"""Host-side checks of the C-ABI library that need no GPU: it builds, loads,
+exports every entry point include/lbnr.h declares, and rejects bad
+arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "lbnr.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(lbnr_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1505_02037_gb300 import lbnr
+    return lbnr.library()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    assert "lbnr_step" in names and "lbnr_create" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_default_opts(lib):
+    from paper_1505_02037_gb300 import lbnr
+    o = lbnr.lbnr_default_opts()
+    assert (o.slicing, o.storage, o.streaming, o.sources_on) == (1, 0, 0, 1)
+    assert o.dev_buffer is None and o.cuda_stream is None
+
+
+@pytest.mark.parametrize("vset,shape,storage,streaming,expect", [
+    (3, (128, 128, 128), 1, 1, 2 * 16 * 19 * 4 * 128 ** 3),
+    (3, (128, 128, 128), 1, 2, 16 * 19 * 4 * 128 ** 3),
+    (1, (200, 1, 1), 0, 1, 2 * 16 * 3 * 8 * 200),
+    (2, (64, 48, 1), 3, 2, 16 * 9 * 2 * 64 * 48),
+])
+def test_workspace_bytes(vset, shape, storage, streaming, expect):
+    """The workspace holds the distribution buffer(s) plus the stencil planes,
+    the FP64 field planes and the reduction scratch."""
+    from paper_1505_02037_gb300 import lbnr
+    o = lbnr.lbnr_default_opts()
+    o.storage, o.streaming = storage, streaming
+    n = lbnr.lbnr_workspace_bytes(lbnr.Grid(*shape), vset, o)
+    cells = shape[0] * shape[1] * shape[2]
+    aux = 7 * cells * (8 if storage == 0 else 4)
+    extra = aux + 16 * cells * 8 + 7 * cells * 8 + ((cells + 127) // 128) * 22 * 8 + (1 << 20)
+    assert expect + extra <= n <= expect + extra + 8 * 256 + 1024
+
+
+@pytest.mark.parametrize("vset,shape,tau,dx,dt,storage", [
+    (1, (200, 2, 1), 0.6, 0.005, 0.005, 0),   # D1Q3 with ny > 1
+    (2, (16, 16, 2), 0.6, 0.1, 0.1, 0),       # D2Q9 with nz > 1
+    (3, (0, 4, 4), 0.6, 0.1, 0.1, 0),         # empty lattice
+    (3, (4, 4, 4), 0.5, 0.1, 0.1, 0),         # tau = 1/2
+    (3, (4, 4, 4), 0.7, 0.1, 0.2, 0),         # dt != dx
+    (3, (4, 4, 4), 0.7, -0.1, -0.1, 0),       # negative spacing
+    (3, (4, 4, 4), 0.7, 0.1, 0.1, 9),         # unknown storage
+    (4, (4, 4, 4), 0.7, 0.1, 0.1, 0),         # unknown set
+])
+def test_create_rejects_bad_arguments_before_the_device(vset, shape, tau, dx, dt, storage):
+    from paper_1505_02037_gb300 import lbnr
+    o = lbnr.lbnr_default_opts()
+    o.storage = storage
+    with pytest.raises(lbnr.LbnrError) as e:
+        lbnr.lbnr_create(lbnr.Grid(*shape), vset, tau, dx, dt, o)
+    assert e.value.code == -1
+
+
+def test_null_context_calls_fail_cleanly(lib):
+    from paper_1505_02037_gb300 import lbnr
+    assert lib.lbnr_step(None, 1) == -1
+    assert lib.lbnr_status(None) == -1
+    assert lib.lbnr_steps_done(None) == -1
+    lib.lbnr_destroy(None)
+    assert lib.lbnr_last_error(None)

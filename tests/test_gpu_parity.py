@@ -1,0 +1,253 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 CPU oracle
+on the same seeded inputs.
+
+Metric (per field F): max over cells |gpu - oracle| / max(max |oracle|, s_F),
+with s_F = 1 for alpha and gamma and a per-test scale for K and V (fields
+that may be zero). FP64 bar: 1e-12. Reduced-precision bars are derived in
+the test that uses them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1505_02037_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def L():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1505_02037_gb300 import lbnr
+    lbnr.library()
+    return lbnr
+
+
+def field_err(g, o, kscale):
+    g = g.reshape(16, -1)
+    o = o.reshape(16, -1)
+    floor = np.array([1.0] * 7 + [kscale] * 9)
+    return np.abs(g - o).max(axis=1) / np.maximum(np.abs(o).max(axis=1), floor)
+
+
+def dist_err(g, o):
+    """Per field: max |g - o| over velocities and cells / max |o| of that field."""
+    g = g.reshape(16, -1)
+    o = o.reshape(16, -1)
+    return np.abs(g - o).max(axis=1) / np.maximum(np.abs(o).max(axis=1), 1e-300)
+
+
+# ---------------------------------------------------------------------------
+# FP64 against the oracle
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("streaming", [1, 2])
+def test_1d_gauge_wave_config_fp64(L, oracle_mod, streaming):
+    """1D gauge wave, N = 200, A = 0.1, d = 1, tau = 0.6, dt = dx = 1/200,
+    harmonic slicing (the 1D configuration). The scheme is linearly unstable
+    at tau = 0.6 (flat-space amplification 1.37 per step), so both sides are
+    compared up to step 80 and must both report the blow-up later."""
+    N, A = 200, 0.1
+    dx = 1 / N
+    fields = W.gauge_wave((N, 1, 1), dx, A)
+    lat = L.Lattice(1, (N, 1, 1), 0.6, dx, streaming=streaming)
+    lat.init(fields)
+    o = oracle_mod.Oracle(1, (N, 1, 1), 0.6, dx)
+    f = o.init(fields)
+    kscale = math.pi * A
+    done = 0
+    for target in (1, 2, 3, 10, 41, 80):
+        lat.step(target - done)
+        f = o.run(f, target - done)
+        done = target
+        assert field_err(lat.moments(), o.moments(f), kscale).max() < TOL64, target
+        assert dist_err(lat.distributions(), f).max() < TOL64, target
+    lat.step(400)
+    with pytest.raises(L.NonFiniteError):
+        lat.status()
+    with pytest.raises(FloatingPointError):
+        o.run(f, 400)
+
+
+def test_1d_gauge_wave_stable_tau_full_run_fp64(L, oracle_mod):
+    """Same wave at the paper's tau/dt = 4.5, run to t = 10 (2000 steps)."""
+    N, A = 200, 0.1
+    dx = 1 / N
+    fields = W.gauge_wave((N, 1, 1), dx, A)
+    lat = L.Lattice(1, (N, 1, 1), 4.5, dx)
+    lat.init(fields)
+    lat.step(2000)
+    o = oracle_mod.Oracle(1, (N, 1, 1), 4.5, dx)
+    f = o.run(o.init(fields), 2000)
+    assert field_err(lat.moments(), o.moments(f), math.pi * A).max() < TOL64
+
+
+@pytest.mark.parametrize("vset,shape", [
+    (1, (333, 1, 1)), (2, (37, 23, 1)), (3, (21, 13, 11)), (3, (1, 1, 1)), (3, (2, 5, 3)),
+    (2, (1, 7, 1)), (1, (1, 1, 1)), (1, (2, 1, 1)),
+])
+@pytest.mark.parametrize("streaming", [1, 2])
+def test_random_state_steps_fp64(L, oracle_mod, vset, shape, streaming):
+    """Seeded random near-flat distributions (every term of the step active),
+    ragged lattices across several thread blocks, degenerate 1- and 2-cell
+    axes; 1, 2 and 3 steps (both AA parities)."""
+    Q = {1: 3, 2: 9, 3: 19}[vset]
+    c, w = oracle_mod.velocity_set(vset)
+    f0 = W.random_distributions(Q, w, shape, seed=1000 + vset)
+    o = oracle_mod.Oracle(vset, shape, 0.8, 1 / shape[0])
+    lat = L.Lattice(vset, shape, 0.8, 1 / shape[0], streaming=streaming)
+    lat.set_distributions(f0)
+    f = f0
+    for n in range(3):
+        lat.step(1)
+        f = o.step(f)
+        assert dist_err(lat.distributions(), f).max() < TOL64, n
+        assert field_err(lat.moments(), o.moments(f), 1e-3).max() < TOL64, n
+
+
+@pytest.mark.parametrize("slicing", [0, 1, 2])
+def test_diagonal_gauge_wave_3d_fp64(L, oracle_mod, slicing):
+    """D3Q19 gauge wave along (1,1,1) on 24^3 (every metric component and
+    every stencil direction active), 30 steps, each slicing."""
+    N, A = 24, 0.1
+    shape = (N, N, N)
+    fields = W.gauge_wave(shape, 1 / N, A, direction="xyz")
+    lat = L.Lattice(3, shape, 1.5, 1 / N, slicing=slicing)
+    lat.init(fields)
+    lat.step(30)
+    o = oracle_mod.Oracle(3, shape, 1.5, 1 / N, slicing=slicing)
+    f = o.run(o.init(fields), 30)
+    assert field_err(lat.moments(), o.moments(f), math.pi * A).max() < TOL64
+    assert dist_err(lat.distributions(), f).max() < TOL64
+
+
+def test_x_aligned_128_cubed_fp64_matches_1d_oracle(L, oracle_mod):
+    """3D configuration at full size: D3Q19, 128^3, FP64, gauge wave along x,
+    A = 0.1, tau = 0.6. The x-aligned 3D run equals the D1Q3 run with the same
+    N (the oracle pins this), so the 1D oracle gives every cell's expected
+    value; compared while the run is finite (80 steps)."""
+    N, A = 128, 0.1
+    lat = L.Lattice(3, (N, N, N), 0.6, 1 / N)
+    lat.init(W.gauge_wave((N, N, N), 1 / N, A))
+    lat.step(80)
+    m = lat.moments().reshape(16, N * N, N)
+    o = oracle_mod.Oracle(1, (N, 1, 1), 0.6, 1 / N)
+    ref = o.moments(o.run(o.init(W.gauge_wave((N, 1, 1), 1 / N, A)), 80))
+    err = max(field_err(m[:, j, :], ref, math.pi * A).max() for j in (0, 1, N * N // 2, N * N - 1))
+    assert err < TOL64
+    assert np.abs(m - m[:, :1, :]).max() == 0  # every column identical
+
+
+def test_full_size_sampled_step_fp64(L, oracle_mod):
+    """128^3 D3Q19 FP64 in the launch configuration of the benchmark, one step
+    from a seeded noisy diagonal wave, checked at sampled cells (faces, edges,
+    corners and random interior cells) against the oracle's per-cell step."""
+    N = 128
+    shape = (N, N, N)
+    fields = W.add_noise(W.gauge_wave(shape, 1 / N, 0.05, direction="xyz"), 1e-6, seed=5)
+    o = oracle_mod.Oracle(3, shape, 0.9, 1 / N)
+    f0 = o.init(fields)
+    lat = L.Lattice(3, shape, 0.9, 1 / N)
+    lat.set_distributions(f0)
+    lat.step(1)
+    rng = np.random.default_rng(7)
+    corners = [x + N * (y + N * z) for x in (0, N - 1) for y in (0, N - 1) for z in (0, N - 1)]
+    idx = np.array(corners + list(rng.integers(0, N ** 3, size=120)), dtype=np.int64)
+    got = lat.cells_distributions(idx)
+    ref = o.step_cells(f0, idx)
+    scale = np.abs(ref).max(axis=(0, 2))
+    err = np.abs(got - ref).max(axis=(0, 2)) / scale
+    assert err.max() < TOL64
+
+
+def test_aa_equals_pingpong_bitwise(L):
+    """In-place AA streaming and ping-pong do the same arithmetic: identical
+    distributions after odd and even step counts, FP64 and FP32."""
+    for storage in ("f64", "f32", "dev_bf16"):
+        shape = (19, 9, 7)
+        fields = W.add_noise(W.gauge_wave(shape, 1 / 19, 0.05, direction="x"), 1e-4, seed=3)
+        a = L.Lattice(3, shape, 1.2, 1 / 19, storage=storage, streaming=1)
+        b = L.Lattice(3, shape, 1.2, 1 / 19, storage=storage, streaming=2)
+        a.init(fields)
+        b.init(fields)
+        for n in (1, 2, 3, 6):
+            a.step(n)
+            b.step(n)
+            assert np.array_equal(a.distributions(), b.distributions()), (storage, n)
+
+
+def test_checkpoint_resume_is_bitwise(L):
+    shape = (16, 12, 10)
+    fields = W.add_noise(W.linear_wave(shape, 1 / 16, 1e-3, direction="x"), 1e-5, seed=9)
+    a = L.Lattice(3, shape, 2.0, 1 / 16, slicing=0)
+    a.init(fields)
+    a.step(7)
+    snap = a.distributions()
+    a.step(9)
+    b = L.Lattice(3, shape, 2.0, 1 / 16, slicing=0)
+    b.init(fields)
+    b.set_distributions(snap)
+    b.step(9)
+    assert np.array_equal(a.distributions(), b.distributions())
+
+
+def test_constraints_fp64(L, oracle_mod):
+    """The 22-value monitor (constraint norms in FP64 on the device and the
+    16 lattice sums) against the oracle, at t = 0 and after 10 steps."""
+    N = 20
+    shape = (N, N, N)
+    fields = W.add_noise(W.gauge_wave(shape, 1 / N, 0.1, direction="xyz"), 1e-4, seed=4)
+    lat = L.Lattice(3, shape, 1.5, 1 / N)
+    lat.init(fields)
+    o = oracle_mod.Oracle(3, shape, 1.5, 1 / N)
+    f = o.init(fields)
+    for n in (0, 10):
+        if n:
+            lat.step(n)
+            f = o.run(f, n)
+        g, r = lat.constraints(), o.constraints(f)
+        np.testing.assert_allclose(g[:6], r[:6], rtol=1e-10, atol=0)
+        np.testing.assert_allclose(g[6:], r[6:], rtol=1e-12, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Errors and degenerate cases
+# ---------------------------------------------------------------------------
+def test_nonfinite_is_reported(L):
+    shape = (8, 8, 8)
+    fields = W.flat(shape)
+    fields[7, 3, 3, 3] = np.nan
+    lat = L.Lattice(3, shape, 1.0, 1 / 8)
+    lat.init(fields)
+    lat.step(2)
+    with pytest.raises(L.NonFiniteError):
+        lat.status()
+
+
+def test_step_before_init_is_a_state_error(L):
+    lat = L.Lattice(1, (10, 1, 1), 1.0, 0.1)
+    with pytest.raises(L.LbnrError) as e:
+        lat.step(1)
+    assert e.value.code == -6
+
+
+def test_bad_cell_index_rejected(L):
+    lat = L.Lattice(1, (10, 1, 1), 1.0, 0.1)
+    lat.init(W.flat((10, 1, 1)))
+    with pytest.raises(L.LbnrError) as e:
+        lat.cells_distributions([3, 10])
+    assert e.value.code == -1
+
+
+def test_flat_space_stays_flat_all_storages(L):
+    for storage in ("f64", "f32", "dev_f32", "dev_bf16", "dev_f16"):
+        shape = (9, 5, 4)
+        lat = L.Lattice(3, shape, 0.7, 1 / 9, storage=storage)
+        lat.init(W.flat(shape))
+        lat.step(5)
+        m = lat.moments()
+        assert np.abs(m - W.flat(shape).reshape(16, -1)).max() < 1e-6, storage
