@@ -145,6 +145,13 @@ int lbnr_set_distributions(lbnr_ctx* ctx, const double* in);
  * non-finite moment, else LBNR_OK. */
 int lbnr_status(lbnr_ctx* ctx);
 
+/* Thread-to-cell layouts of the collide kernel available for this context's
+ * set and storage (all give the same results): their number, a short name,
+ * and the selection (default 0). Used by the autotuner. */
+int lbnr_num_variants(const lbnr_ctx* ctx);
+const char* lbnr_variant_name(const lbnr_ctx* ctx, int variant);
+int lbnr_set_variant(lbnr_ctx* ctx, int variant);
+
 /* Steps taken since lbnr_init; Q of the velocity set; the streaming pattern
  * chosen (LBNR_STREAM_PINGPONG or LBNR_STREAM_AA). */
 int64_t lbnr_steps_done(const lbnr_ctx* ctx);

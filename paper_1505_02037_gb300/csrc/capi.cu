@@ -152,7 +152,8 @@ int validate(const lbnr_grid* g, int vset, const lbnr_opts* o) {
 Layout layout_for(const lbnr_grid* g, int vset, int storage, int streaming) {
   const int Q = q_of(vset);
   const uint64_t cells = (uint64_t)g->nx * g->ny * g->nz;
-  const uint64_t fbytes = align256(16ull * Q * cells * storage_bytes(storage));
+  const uint64_t ps = (cells + kTile - 1) / kTile * kTile;
+  const uint64_t fbytes = align256(16ull * Q * ps * storage_bytes(storage));
   const uint64_t cb = storage_is_fp64(storage) ? 8 : 4;
   const uint64_t nblk = (cells + 127) / 128;
   Layout L;
@@ -340,6 +341,7 @@ int lbnr_create(const lbnr_grid* grid, int vset, double tau, double dx, double d
   L.ny = (int32_t)grid->ny;
   L.nz = (int32_t)grid->nz;
   L.cells = grid->nx * grid->ny * grid->nz;
+  L.pstride = (L.cells + kTile - 1) / kTile * kTile;
   L.dx = dx;
   L.dt = dt;
   L.tau = tau;
@@ -354,7 +356,9 @@ int lbnr_create(const lbnr_grid* grid, int vset, double tau, double dx, double d
   L.stage = b + Ly.stage;
   L.st = c->st;
   L.block = 128;
-  cudaError_t e = cudaMemsetAsync(L.flag, 0, sizeof(int), c->st);
+  // zero everything once: the plane padding must hold finite values
+  cudaError_t e = cudaMemsetAsync(c->base, 0, Ly.total, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
   if (e != cudaSuccess) {
     lbnr_destroy(c);
     return fail(nullptr, LBNR_ECUDA, "memset: %s", cudaGetErrorString(e));
@@ -529,6 +533,22 @@ int lbnr_status(lbnr_ctx* c) {
   int rc = read_flag(c, &flag);
   if (rc) return rc;
   return flag ? fail(c, LBNR_ENONFINITE, "non-finite moment seen") : LBNR_OK;
+}
+
+int lbnr_num_variants(const lbnr_ctx* c) { return c ? c->ops->nvariants : 0; }
+
+const char* lbnr_variant_name(const lbnr_ctx* c, int v) {
+  return (c && v >= 0 && v < c->ops->nvariants) ? c->ops->variant_name(v) : "";
+}
+
+int lbnr_set_variant(lbnr_ctx* c, int v) {
+  if (!c || v < 0 || v >= c->ops->nvariants) return fail(c, LBNR_EINVAL, "no variant %d", v);
+  if (v != c->variant) {
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    drop_graphs(c);
+    c->variant = v;
+  }
+  return LBNR_OK;
 }
 
 int64_t lbnr_steps_done(const lbnr_ctx* c) { return c ? c->steps : -1; }

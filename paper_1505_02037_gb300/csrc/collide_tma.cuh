@@ -1,0 +1,258 @@
+// TMA-fed, warp-specialised form of the fused collide-and-stream step
+// (same arithmetic as k_collide in kernels.cuh: Eq. numlb with the
+// equilibria and sources of Eqs. alfa-ekstsor and rho = sum f + dt S/2).
+//
+// One persistent CTA per SM. Warp NC (the producer) streams tiles of
+// kTileCells consecutive cells into a ring of NS shared-memory stages: every
+// distribution plane of a tile is one row of the stage, and the whole stage
+// (16*Q rows) arrives through one or two 2D tensor copies
+// (cp.async.bulk.tensor) that signal a "full" mbarrier. Consumer warps
+// 0..NC-1 each take whole tiles: two lanes per cell, each lane owning 8 of
+// the 16 fields. A consumer sums its moments from shared memory, swaps them
+// with its partner lane, evaluates the Bona-Masso sources and fluxes, then
+// relaxes and streams every value of the tile straight from shared memory to
+// the destination buffer and releases the stage through an "empty" mbarrier.
+// Registers only carry the physics, so occupancy no longer depends on the
+// 304 distributions of a D3Q19 cell.
+//
+// Reads must be local (ping-pong, or AA at an even step): the stage holds
+// the planes of the tile's own cells. Every wait is bounded: after ~2 s the
+// kernel sets bit 1 of the flag word and leaves.
+#pragma once
+
+#include <cuda.h>
+
+#include "kernels.cuh"
+
+namespace lbnr {
+
+constexpr int kTileCells = 16;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      "  .reg .pred p;\n"
+      "  mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "  selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Waits for the phase of the given parity to complete; false after limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+#pragma unroll 1
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int32_t x,
+                                            int32_t y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+template <int Q>
+struct TmaShape {
+  static constexpr int kPlanes = kNF * Q;
+  static constexpr int kBoxes = (kPlanes + 255) / 256;  // a TMA box side is at most 256
+  static constexpr int kPlanesPerBox = kPlanes / kBoxes;
+  static_assert(kPlanes % kBoxes == 0, "planes must split evenly into boxes");
+};
+
+template <class S>
+__host__ __device__ constexpr uint32_t tma_stage_bytes(int Q) {
+  return (uint32_t)(kNF * Q * kTileCells * sizeof(S));
+}
+__host__ __device__ constexpr uint32_t tma_smem_bytes(uint32_t stage_bytes, int NS) {
+  return 1024u + stage_bytes * (uint32_t)NS;
+}
+
+template <int Q, class S, class C, int REP, int LAYOUT, int NC, int NS>
+__global__ void __launch_bounds__(32 * (NC + 1), 1)
+    k_collide_tma(const StepArgs<S, C> a, const __grid_constant__ CUtensorMap tmap, int64_t ntiles) {
+  static_assert(LAYOUT == kPingPong || LAYOUT == kAAEven, "reads must be local");
+  static_assert(NS % NC == 0, "each consumer owns NS/NC stages");
+  using L = Lattice<Q>;
+  using TS = TmaShape<Q>;
+  constexpr int T = kTileCells;
+  constexpr int dim = L::kDim;
+  constexpr uint32_t ROWB = T * sizeof(S);
+  constexpr uint32_t BOXB = TS::kPlanesPerBox * ROWB;
+  constexpr uint32_t STAGEB = TS::kPlanes * ROWB;
+  constexpr uint64_t kLimitNs = 2000000000ull;
+
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);  // [0,NS) full, [NS,2NS) empty
+  unsigned char* stages = smem + 1024;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(smem_u32(&bars[s]), 1);
+      mbar_init(smem_u32(&bars[NS + s]), 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  const int64_t G = gridDim.x;
+  const int64_t my = (int64_t)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / G + 1 : 0;
+
+  if (warp == NC) {
+    // ---------------- producer ----------------
+    if (lane == 0) {
+      int64_t issued = 0;
+      for (int64_t j = 0; j < my; ++j) {
+        const int s = (int)(j % NS);
+        const uint32_t ph = (uint32_t)((j / NS) & 1);
+        if (j >= NS && !mbar_wait(smem_u32(&bars[NS + s]), ph ^ 1u, kLimitNs)) {
+          atomicOr(a.flag, 2);
+          break;
+        }
+        const int64_t tile = blockIdx.x + j * G;
+        const uint32_t fb = smem_u32(&bars[s]);
+        mbar_expect_tx(fb, STAGEB);
+        const uint32_t dst = smem_u32(stages + (size_t)s * STAGEB);
+#pragma unroll
+        for (int b = 0; b < TS::kBoxes; ++b)
+          tma_load_2d(dst + b * BOXB, &tmap, (int32_t)(tile * T), b * TS::kPlanesPerBox, fb);
+        issued = j + 1;
+      }
+      // Leave only when every copy this warp started has landed.
+      for (int64_t j = issued > NS ? issued - NS : 0; j < issued; ++j)
+        if (!mbar_wait(smem_u32(&bars[j % NS]), (uint32_t)((j / NS) & 1), kLimitNs)) {
+          atomicOr(a.flag, 2);
+          break;
+        }
+    }
+    return;
+  }
+
+  // ---------------- consumers ----------------
+  const int g = lane >> 4;
+  const int ci = lane & 15;
+  const int64_t cells = a.G.cells;
+  const int64_t ps = a.G.pstride;
+  for (int64_t j = warp; j < my; j += NC) {
+    const int s = (int)(j % NS);
+    const uint32_t ph = (uint32_t)((j / NS) & 1);
+    if (!mbar_wait(smem_u32(&bars[s]), ph, kLimitNs)) {
+      if (lane == 0) atomicOr(a.flag, 2);
+      break;
+    }
+    const S* st = reinterpret_cast<const S*>(stages + (size_t)s * STAGEB);
+    const int64_t tile = blockIdx.x + j * G;
+    const int64_t cell = tile * T + ci;
+    const bool valid = cell < cells;
+    const int64_t c = valid ? cell : cells - 1;
+    const Nbr n = make_nbr(a.G, c);
+
+    // moments of this lane's 8 fields
+    C mine[8];
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+      const int F = g ? field_of(2, 1, jj) : field_of(2, 0, jj);
+      const S* row = st + (F * Q) * T + ci;
+      C sum = C(0);
+#pragma unroll
+      for (int l = 0; l < Q; ++l) {
+        const C v = (C)row[l * T];
+        sum += REP == kDEV ? C(L::w(l)) * v : v;
+      }
+      mine[jj] = sum;
+    }
+    C rt[kNF];
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+      const C other = __shfl_xor_sync(0xffffffffu, mine[jj], 16);
+      rt[field_of(2, 0, jj)] = g ? other : mine[jj];
+      rt[field_of(2, 1, jj)] = g ? mine[jj] : other;
+    }
+    {
+      C chk = C(0);
+#pragma unroll
+      for (int F = 0; F < kNF; ++F) chk += rt[F];
+      if (valid && g == 0 && !isfinite(chk)) atomicOr(a.flag, 1);
+    }
+
+    C A[3], D[3][6];
+    derivatives<Q, C>(n, cells, a.aux, a.inv2dx, a.inv4dx, A, D);
+    C alpha, gm[6], K[6], V[3];
+    unpack<REP, C>(rt, alpha, gm, K, V);
+    C Sr[kNF];
+    bm_sources<C>(alpha, gm, K, V, A, D, a.slicing, Sr);
+    if (!a.sources_on) {
+#pragma unroll
+      for (int F = 0; F < kNF; ++F) Sr[F] = C(0);
+    }
+    C rho[kNF];
+#pragma unroll
+    for (int F = 0; F < kNF; ++F) rho[F] = rt[F] + a.half_dt * Sr[F];
+    C Fl[6][3];
+    {
+      C alpha2, g2[6], K2[6], V2[3];
+      unpack<REP, C>(rho, alpha2, g2, K2, V2);
+      bm_flux<C, dim>(alpha2, g2, V2, A, D, Fl);
+    }
+    const C three_omega = C(3) * a.omega;
+
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+      const int F0 = field_of(2, 0, jj), F1 = field_of(2, 1, jj);
+      const int F = g ? F1 : F0;
+      const C cf = a.omega * (g ? rho[F1] : rho[F0]) + a.sigma * (g ? Sr[F1] : Sr[F0]);
+      C b[3] = {C(0), C(0), C(0)};
+      if (has_flux(F0)) {
+#pragma unroll
+        for (int k = 0; k < dim; ++k) b[k] = three_omega * (g ? Fl[F1 - kK][k] : Fl[F0 - kK][k]);
+      }
+      const S* row = st + (F * Q) * T + ci;
+#pragma unroll
+      for (int l = 0; l < Q; ++l) {
+        const C v = (C)row[l * T];
+        C t = cf;
+        if (has_flux(F0)) {
+#pragma unroll
+          for (int k = 0; k < dim; ++k) {
+            if (L::c(l, k) > 0) t += b[k];
+            if (L::c(l, k) < 0) t -= b[k];
+          }
+        }
+        const C out = REP == kDEV ? fma(a.omc, v, t) : fma(a.omc, v, C(L::w(l)) * t);
+        if (valid) Codec<S>::store(a.fout + write_index<Q, LAYOUT>(n, ps, F, l), out);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(smem_u32(&bars[NS + s]));
+  }
+}
+
+}  // namespace lbnr

@@ -2,52 +2,97 @@
 #pragma once
 
 #include "dispatch.h"
+#include <cudaTypedefs.h>
+
+#include "collide_tma.cuh"
 #include "kernels.cuh"
 
 namespace lbnr {
 
-// Thread-to-cell layouts of the collide kernel, per compute type and set:
-// P threads per cell (1 or 2); HOLD keeps all of a thread's distributions in
-// registers between the moment pass and the update pass (else they are read
-// again, from cache).
-template <int Q, class C>
-struct Variants;
-template <>
-struct Variants<3, double> {
-  static constexpr int n = 2;
-  static constexpr int P[2] = {1, 1};
-  static constexpr bool HOLD[2] = {true, false};
+// Launch forms of the collide kernel, per velocity set and storage width.
+// kind 0: one thread block per 128 threads, P threads per cell; HOLD keeps a
+//         thread's distributions in registers between the moment pass and
+//         the update pass (else they are read again, from cache). Any layout.
+// kind 1: TMA-fed persistent kernel (collide_tma.cuh) with NC consumer warps
+//         and NS shared-memory stages; local reads only, so at the odd AA
+//         step it hands over to the form named by `fallback`.
+struct VariantSpec {
+  int kind, P;
+  bool hold;
+  int nc, ns;
 };
-template <>
-struct Variants<9, double> {
-  static constexpr int n = 1;
-  static constexpr int P[1] = {1};
-  static constexpr bool HOLD[1] = {false};
-};
-template <>
-struct Variants<19, double> {
-  static constexpr int n = 1;
-  static constexpr int P[1] = {1};
-  static constexpr bool HOLD[1] = {false};
-};
-template <>
-struct Variants<3, float> {
-  static constexpr int n = 2;
-  static constexpr int P[2] = {1, 1};
-  static constexpr bool HOLD[2] = {true, false};
-};
-template <>
-struct Variants<9, float> {
-  static constexpr int n = 2;
-  static constexpr int P[2] = {1, 2};
-  static constexpr bool HOLD[2] = {true, true};
-};
-template <>
-struct Variants<19, float> {
-  static constexpr int n = 2;
-  static constexpr int P[2] = {2, 1};
-  static constexpr bool HOLD[2] = {true, false};
-};
+
+template <int Q, int SB>
+struct VariantTable;
+#define LBNR_VARIANTS(Q_, SB_, FALLBACK_, ...)              \
+  template <>                                                \
+  struct VariantTable<Q_, SB_> {                             \
+    static constexpr VariantSpec v[] = {__VA_ARGS__};        \
+    static constexpr int n = sizeof(v) / sizeof(v[0]);       \
+    static constexpr int fallback = FALLBACK_;               \
+  };
+// FP64 storage (FP64 arithmetic)
+LBNR_VARIANTS(3, 8, 0, {0, 1, true, 0, 0}, {1, 2, false, 4, 8})
+LBNR_VARIANTS(9, 8, 0, {0, 1, false, 0, 0}, {1, 2, false, 4, 8})
+LBNR_VARIANTS(19, 8, 0, {0, 1, false, 0, 0}, {1, 2, false, 2, 4}, {1, 2, false, 4, 4})
+// FP32 storage
+LBNR_VARIANTS(3, 4, 1, {1, 2, false, 8, 16}, {0, 1, true, 0, 0})
+LBNR_VARIANTS(9, 4, 1, {1, 2, false, 8, 16}, {0, 1, true, 0, 0})
+LBNR_VARIANTS(19, 4, 2, {1, 2, false, 4, 8}, {1, 2, false, 5, 10}, {0, 2, true, 0, 0})
+// 16-bit storage
+LBNR_VARIANTS(3, 2, 1, {1, 2, false, 8, 16}, {0, 1, true, 0, 0})
+LBNR_VARIANTS(9, 2, 1, {1, 2, false, 8, 16}, {0, 1, true, 0, 0})
+LBNR_VARIANTS(19, 2, 2, {1, 2, false, 8, 16}, {1, 2, false, 4, 16}, {0, 2, true, 0, 0})
+#undef LBNR_VARIANTS
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no
+// link-time dependency on libcuda).
+inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+template <class S>
+constexpr CUtensorMapDataType tma_dtype() {
+  return sizeof(S) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                        : (sizeof(S) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                          : CU_TENSOR_MAP_DATA_TYPE_UINT16);
+}
+
+// 2D view of a distribution buffer: x = cell (stride 1), y = plane
+// (stride pstride); boxes of kTileCells x (planes per box).
+template <int Q, class S>
+cudaError_t encode_planes(const void* base, int64_t pstride, CUtensorMap* map) {
+  auto fn = tensor_map_encoder();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t dims[2] = {(cuuint64_t)pstride, (cuuint64_t)TmaShape<Q>::kPlanes};
+  const cuuint64_t strides[1] = {(cuuint64_t)pstride * sizeof(S)};
+  const cuuint32_t box[2] = {(cuuint32_t)kTileCells, (cuuint32_t)TmaShape<Q>::kPlanesPerBox};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, tma_dtype<S>(), 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+inline int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
 
 template <class S>
 struct ComputeOf {
@@ -65,29 +110,69 @@ inline unsigned grid_for(int64_t threads, int block) {
 template <int Q, class S, int REP>
 struct Impl {
   using C = typename ComputeOf<S>::type;
-  using V = Variants<Q, C>;
+  using VT = VariantTable<Q, (int)sizeof(S)>;
 
   static const char* variant_name(int v) {
-    static char buf[2][32];
-    if (v < 0 || v >= V::n) return "?";
-    snprintf(buf[v], sizeof(buf[v]), "P%d%s", V::P[v], V::HOLD[v] ? "-hold" : "-reread");
+    static char buf[8][40];
+    if (v < 0 || v >= VT::n || v >= 8) return "?";
+    const VariantSpec& x = VT::v[v];
+    if (x.kind == 0)
+      snprintf(buf[v], sizeof(buf[v]), "P%d%s", x.P, x.hold ? "-hold" : "-reread");
+    else
+      snprintf(buf[v], sizeof(buf[v]), "tma-nc%d-ns%d", x.nc, x.ns);
     return buf[v];
   }
 
   template <int LAYOUT, int VI>
-  static cudaError_t launch_collide(const LaunchCtx& L, const StepArgs<S, C>& a) {
-    constexpr int P = V::P[VI < V::n ? VI : 0];
-    constexpr bool H = V::HOLD[VI < V::n ? VI : 0];
+  static cudaError_t launch_generic(const LaunchCtx& L, const StepArgs<S, C>& a) {
+    constexpr VariantSpec x = VT::v[VI];
+    constexpr int P = x.P;
+    constexpr bool H = x.hold;
     const int block = 128;
     const int64_t threads = P == 2 ? ((L.cells + 15) / 16) * 32 : L.cells;
     k_collide<Q, S, C, REP, LAYOUT, P, H><<<grid_for(threads, block), block, 0, L.st>>>(a);
     return cudaGetLastError();
   }
 
+  template <int LAYOUT, int VI>
+  static cudaError_t launch_tma(const LaunchCtx& L, const StepArgs<S, C>& a) {
+    constexpr VariantSpec x = VT::v[VI];
+    constexpr int NC = x.nc > 0 ? x.nc : 1;
+    constexpr int NS = x.ns > 0 ? x.ns : 1;
+    constexpr uint32_t smem = tma_smem_bytes(tma_stage_bytes<S>(Q), NS);
+    auto kern = k_collide_tma<Q, S, C, REP, LAYOUT, NC, NS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    CUtensorMap map;
+    e = encode_planes<Q, S>(a.fin, L.pstride, &map);
+    if (e != cudaSuccess) return e;
+    const int64_t ntiles = L.pstride / kTileCells;
+    const int64_t grid = ntiles < sm_count() ? ntiles : sm_count();
+    kern<<<(unsigned)grid, 32 * (NC + 1), smem, L.st>>>(a, map, ntiles);
+    return cudaGetLastError();
+  }
+
+  template <int LAYOUT, int VI>
+  static cudaError_t launch_variant(const LaunchCtx& L, const StepArgs<S, C>& a) {
+    if constexpr (VT::v[VI].kind == 1) {
+      if constexpr (LAYOUT == kAAOdd)
+        return launch_generic<LAYOUT, VT::fallback>(L, a);
+      else
+        return launch_tma<LAYOUT, VI>(L, a);
+    } else {
+      return launch_generic<LAYOUT, VI>(L, a);
+    }
+  }
+
   template <int LAYOUT>
   static cudaError_t collide_layout(const LaunchCtx& L, int variant, const StepArgs<S, C>& a) {
-    if (variant == 1 && V::n > 1) return launch_collide<LAYOUT, 1>(L, a);
-    return launch_collide<LAYOUT, 0>(L, a);
+    if constexpr (VT::n > 2) {
+      if (variant == 2) return launch_variant<LAYOUT, 2>(L, a);
+    }
+    if constexpr (VT::n > 1) {
+      if (variant == 1) return launch_variant<LAYOUT, 1>(L, a);
+    }
+    return launch_variant<LAYOUT, 0>(L, a);
   }
 
   static cudaError_t step(const LaunchCtx& L, int layout, int variant, const void* fin, void* fout) {
@@ -96,7 +181,7 @@ struct Impl {
     a.fout = static_cast<S*>(fout);
     a.aux = static_cast<const C*>(L.aux);
     a.flag = L.flag;
-    a.G = Grid{L.nx, L.ny, L.nz, L.cells};
+    a.G = Grid{L.nx, L.ny, L.nz, L.cells, L.pstride};
     a.inv2dx = C(1.0 / (2.0 * L.dx));
     a.inv4dx = C(1.0 / (4.0 * L.dx));
     a.half_dt = C(0.5 * L.dt);
@@ -111,7 +196,7 @@ struct Impl {
   }
 
   static cudaError_t aux(const LaunchCtx& L, int layout, const void* f) {
-    const Grid G{L.nx, L.ny, L.nz, L.cells};
+    const Grid G{L.nx, L.ny, L.nz, L.cells, L.pstride};
     const unsigned grid = grid_for(L.cells, 256);
     const S* fp = static_cast<const S*>(f);
     C* ap = static_cast<C*>(L.aux);
@@ -126,7 +211,7 @@ struct Impl {
     a.fields = L.macro;
     a.f = static_cast<S*>(f);
     a.flag = L.flag;
-    a.G = Grid{L.nx, L.ny, L.nz, L.cells};
+    a.G = Grid{L.nx, L.ny, L.nz, L.cells, L.pstride};
     a.inv2dx = 1.0 / (2.0 * L.dx);
     a.inv4dx = 1.0 / (4.0 * L.dx);
     a.half_dt = 0.5 * L.dt;
@@ -137,7 +222,7 @@ struct Impl {
   }
 
   static cudaError_t sum64(const LaunchCtx& L, int layout, const void* f, int64_t* nblocks) {
-    const Grid G{L.nx, L.ny, L.nz, L.cells};
+    const Grid G{L.nx, L.ny, L.nz, L.cells, L.pstride};
     const unsigned grid = grid_for(L.cells, 256);
     *nblocks = grid;
     const S* fp = static_cast<const S*>(f);
@@ -151,7 +236,7 @@ struct Impl {
   }
 
   static cudaError_t correct64(const LaunchCtx& L) {
-    const Grid G{L.nx, L.ny, L.nz, L.cells};
+    const Grid G{L.nx, L.ny, L.nz, L.cells, L.pstride};
     k_correct64<Q><<<grid_for(L.cells, 128), 128, 0, L.st>>>(
         L.macro, L.aux64, G, 1.0 / (2.0 * L.dx), 1.0 / (4.0 * L.dx), 0.5 * L.dt, L.slicing,
         L.sources_on);
@@ -159,7 +244,7 @@ struct Impl {
   }
 
   static cudaError_t constraints64(const LaunchCtx& L, int64_t* nblocks) {
-    const Grid G{L.nx, L.ny, L.nz, L.cells};
+    const Grid G{L.nx, L.ny, L.nz, L.cells, L.pstride};
     const unsigned grid = grid_for(L.cells, 128);
     *nblocks = grid;
     k_constraints64<Q><<<grid, 128, 0, L.st>>>(L.macro, G, 1.0 / (2.0 * L.dx), 1.0 / (4.0 * L.dx),
@@ -169,7 +254,7 @@ struct Impl {
 
   static cudaError_t get_plane(const LaunchCtx& L, int layout, const void* f, int F, int l,
                                double* out) {
-    const Grid G{L.nx, L.ny, L.nz, L.cells};
+    const Grid G{L.nx, L.ny, L.nz, L.cells, L.pstride};
     const unsigned grid = grid_for(L.cells, 256);
     const S* fp = static_cast<const S*>(f);
     if (layout == kPingPong) k_get_plane<Q, S, REP, kPingPong><<<grid, 256, 0, L.st>>>(fp, out, G, F, l);
@@ -180,7 +265,7 @@ struct Impl {
 
   static cudaError_t set_plane(const LaunchCtx& L, int layout, void* f, int F, int l,
                                const double* in) {
-    const Grid G{L.nx, L.ny, L.nz, L.cells};
+    const Grid G{L.nx, L.ny, L.nz, L.cells, L.pstride};
     const unsigned grid = grid_for(L.cells, 256);
     S* fp = static_cast<S*>(f);
     if (layout == kPingPong) k_set_plane<Q, S, REP, kPingPong><<<grid, 256, 0, L.st>>>(fp, in, G, F, l);
@@ -191,7 +276,7 @@ struct Impl {
 
   static cudaError_t get_cells(const LaunchCtx& L, int layout, const void* f, int64_t n,
                                const int64_t* idx, double* out) {
-    const Grid G{L.nx, L.ny, L.nz, L.cells};
+    const Grid G{L.nx, L.ny, L.nz, L.cells, L.pstride};
     const unsigned grid = grid_for(n * kNF, 128);
     const S* fp = static_cast<const S*>(f);
     if (layout == kPingPong) k_get_cells<Q, S, REP, kPingPong><<<grid, 128, 0, L.st>>>(fp, idx, n, out, G);
@@ -201,7 +286,7 @@ struct Impl {
   }
 
   static const Ops* ops() {
-    static const Ops o = {V::n,      &variant_name, &step,          &aux,       &init,
+    static const Ops o = {VT::n,     &variant_name, &step,          &aux,       &init,
                           &sum64,    &correct64,    &constraints64, &get_plane, &set_plane,
                           &get_cells};
     return &o;

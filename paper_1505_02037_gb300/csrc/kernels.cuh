@@ -48,12 +48,14 @@ template <>
 struct Codec<double> {
   __device__ static __forceinline__ double load(const double* p) { return __ldcs(p); }
   __device__ static __forceinline__ double load_keep(const double* p) { return __ldg(p); }
+  __device__ static __forceinline__ double load_coh(const double* p) { return __ldcg(p); }
   __device__ static __forceinline__ void store(double* p, double v) { __stcs(p, v); }
 };
 template <>
 struct Codec<float> {
   __device__ static __forceinline__ float load(const float* p) { return __ldcs(p); }
   __device__ static __forceinline__ float load_keep(const float* p) { return __ldg(p); }
+  __device__ static __forceinline__ float load_coh(const float* p) { return __ldcg(p); }
   __device__ static __forceinline__ void store(float* p, float v) { __stcs(p, v); }
 };
 template <>
@@ -63,6 +65,9 @@ struct Codec<__nv_bfloat16> {
   }
   __device__ static __forceinline__ float load_keep(const __nv_bfloat16* p) {
     return __bfloat162float(__ldg(p));
+  }
+  __device__ static __forceinline__ float load_coh(const __nv_bfloat16* p) {
+    return __bfloat162float(__ldcg(p));
   }
   __device__ static __forceinline__ void store(__nv_bfloat16* p, float v) {
     __stcs(p, __float2bfloat16_rn(v));
@@ -74,6 +79,7 @@ struct Codec<__half> {
   __device__ static __forceinline__ float load_keep(const __half* p) {
     return __half2float(__ldg(p));
   }
+  __device__ static __forceinline__ float load_coh(const __half* p) { return __half2float(__ldcg(p)); }
   __device__ static __forceinline__ void store(__half* p, float v) {
     __stcs(p, __float2half_rn(v));
   }
@@ -91,6 +97,7 @@ __host__ __device__ constexpr bool has_flux(int F) { return F >= kK && F < kV; }
 struct Grid {
   int32_t nx, ny, nz;
   int64_t cells;
+  int64_t pstride;  // elements between consecutive distribution planes (>= cells)
 };
 
 struct Nbr {
@@ -124,20 +131,21 @@ __device__ __forceinline__ Nbr make_nbr(const Grid& G, int64_t c) {
   return n;
 }
 
-// Where f_{F,l}(x) of the current state lives, for each layout.
+// Where f_{F,l}(x) of the current state lives, for each layout (ps: plane
+// stride).
 template <int Q, int LAYOUT>
-__device__ __forceinline__ int64_t read_index(const Nbr& n, int64_t cells, int F, int l) {
+__device__ __forceinline__ int64_t read_index(const Nbr& n, int64_t ps, int F, int l) {
   using L = Lattice<Q>;
   if (LAYOUT == kAAOdd)
-    return (int64_t)(F * Q + opposite(l)) * cells + n.at(-L::c(l, 0), -L::c(l, 1), -L::c(l, 2));
-  return (int64_t)(F * Q + l) * cells + n.c;
+    return (int64_t)(F * Q + opposite(l)) * ps + n.at(-L::c(l, 0), -L::c(l, 1), -L::c(l, 2));
+  return (int64_t)(F * Q + l) * ps + n.c;
 }
 // Where f*_{F,l}(x) goes.
 template <int Q, int LAYOUT>
-__device__ __forceinline__ int64_t write_index(const Nbr& n, int64_t cells, int F, int l) {
+__device__ __forceinline__ int64_t write_index(const Nbr& n, int64_t ps, int F, int l) {
   using L = Lattice<Q>;
-  if (LAYOUT == kAAEven) return (int64_t)(F * Q + opposite(l)) * cells + n.c;
-  return (int64_t)(F * Q + l) * cells + n.at(L::c(l, 0), L::c(l, 1), L::c(l, 2));
+  if (LAYOUT == kAAEven) return (int64_t)(F * Q + opposite(l)) * ps + n.c;
+  return (int64_t)(F * Q + l) * ps + n.at(L::c(l, 0), L::c(l, 1), L::c(l, 2));
 }
 
 // ---------------------------------------------------------------------------
@@ -147,10 +155,14 @@ __device__ __forceinline__ int64_t write_index(const Nbr& n, int64_t cells, int 
 // flux-free fields first and three K components last, so the j-th field of
 // either thread has the same kind and all indexing stays compile-time.
 __host__ __device__ constexpr int field_of(int P, int g, int j) {
+  // pairs (j-th field of thread 0, of thread 1): (0,1) (2,3) (4,5) (6,13)
+  // (14,15) (7,10) (8,11) (9,12); each pair differs by an odd number of
+  // fields, so with Q odd the two half-warps read shared-memory rows that
+  // start in different banks.
   return P == 1 ? j
-                : (g == 0 ? (j == 0 ? 0 : j == 1 ? 1 : j == 2 ? 2 : j == 3 ? 3 : j == 4 ? 13
+                : (g == 0 ? (j == 0 ? 0 : j == 1 ? 2 : j == 2 ? 4 : j == 3 ? 6 : j == 4 ? 14
                                                      : j == 5 ? 7 : j == 6 ? 8 : 9)
-                          : (j == 0 ? 4 : j == 1 ? 5 : j == 2 ? 6 : j == 3 ? 14 : j == 4 ? 15
+                          : (j == 0 ? 1 : j == 1 ? 3 : j == 2 ? 5 : j == 3 ? 13 : j == 4 ? 15
                                                      : j == 5 ? 10 : j == 6 ? 11 : 12));
 }
 
@@ -223,6 +235,7 @@ __global__ void __launch_bounds__(128) k_collide(const StepArgs<S, C> a) {
   const bool valid = cell < a.G.cells;
   const int64_t c = valid ? cell : a.G.cells - 1;
   const int64_t cells = a.G.cells;
+  const int64_t ps = a.G.pstride;
   const Nbr n = make_nbr(a.G, c);
 
   // Pass 1: zeroth moments of this thread's fields (ascending l).
@@ -234,8 +247,12 @@ __global__ void __launch_bounds__(128) k_collide(const StepArgs<S, C> a) {
     C s = C(0);
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
-      const C v = HOLD ? Codec<S>::load(a.fin + read_index<Q, LAYOUT>(n, cells, F, l))
-                       : Codec<S>::load_keep(a.fin + read_index<Q, LAYOUT>(n, cells, F, l));
+      // In place (AA) the buffer is written by this kernel: re-read values
+      // must come through coherent loads, never the read-only path.
+      const C v = HOLD ? Codec<S>::load(a.fin + read_index<Q, LAYOUT>(n, ps, F, l))
+                  : LAYOUT == kPingPong
+                      ? Codec<S>::load_keep(a.fin + read_index<Q, LAYOUT>(n, ps, F, l))
+                      : Codec<S>::load_coh(a.fin + read_index<Q, LAYOUT>(n, ps, F, l));
       if (HOLD) fv[HOLD ? j : 0][HOLD ? l : 0] = v;
       s += REP == kDEV ? C(L::w(l)) * v : v;
     }
@@ -303,7 +320,9 @@ __global__ void __launch_bounds__(128) k_collide(const StepArgs<S, C> a) {
 #pragma unroll
     for (int l = 0; l < Q; ++l)
       v_[l] = HOLD ? fv[HOLD ? j : 0][HOLD ? l : 0]
-                   : Codec<S>::load_keep(a.fin + read_index<Q, LAYOUT>(n, cells, F, l));
+              : LAYOUT == kPingPong
+                  ? Codec<S>::load_keep(a.fin + read_index<Q, LAYOUT>(n, ps, F, l))
+                  : Codec<S>::load_coh(a.fin + read_index<Q, LAYOUT>(n, ps, F, l));
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
       const C v = v_[l];
@@ -316,7 +335,7 @@ __global__ void __launch_bounds__(128) k_collide(const StepArgs<S, C> a) {
         }
       }
       const C out = REP == kDEV ? fma(a.omc, v, t) : fma(a.omc, v, C(L::w(l)) * t);
-      if (valid) Codec<S>::store(a.fout + write_index<Q, LAYOUT>(n, cells, F, l), out);
+      if (valid) Codec<S>::store(a.fout + write_index<Q, LAYOUT>(n, ps, F, l), out);
     }
   }
 }
@@ -335,7 +354,7 @@ __global__ void __launch_bounds__(256) k_aux(const S* __restrict__ f, C* __restr
     C s = C(0);
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
-      const C v = Codec<S>::load_keep(f + read_index<Q, LAYOUT>(n, G.cells, F, l));
+      const C v = Codec<S>::load_keep(f + read_index<Q, LAYOUT>(n, G.pstride, F, l));
       s += REP == kDEV ? C(L::w(l)) * v : v;
     }
     if (F == 0) s = REP == kDEV ? log1p(s) : log(s);
@@ -410,7 +429,7 @@ __global__ void __launch_bounds__(128) k_init(const Init64Args<S> a) {
       else
         v = L::w(l) * (r[F] + 3.0 * cf) - a.half_dt * L::w(l) * Sr[F];
       bad |= !isfinite(v);
-      Codec<S>::store(a.f + (int64_t)(F * Q + l) * cells + c, (decltype(Codec<S>::load(a.f)))v);
+      Codec<S>::store(a.f + (int64_t)(F * Q + l) * a.G.pstride + c, (decltype(Codec<S>::load(a.f)))v);
     }
   }
   if (bad) atomicOr(a.flag, 1);
@@ -434,7 +453,7 @@ __global__ void __launch_bounds__(256) k_sum64(const S* __restrict__ f, double* 
     if (valid) {
 #pragma unroll
       for (int l = 0; l < Q; ++l) {
-        const double v = (double)Codec<S>::load_keep(f + read_index<Q, LAYOUT>(n, G.cells, F, l));
+        const double v = (double)Codec<S>::load_keep(f + read_index<Q, LAYOUT>(n, G.pstride, F, l));
         s += REP == kDEV ? L::w(l) * v : v;
       }
       if (REP == kDEV) s += flat_value(F);
@@ -679,7 +698,7 @@ __global__ void k_get_plane(const S* __restrict__ f, double* __restrict__ out, G
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= G.cells) return;
   const Nbr n = make_nbr(G, c);
-  const double v = (double)Codec<S>::load_keep(f + read_index<Q, LAYOUT>(n, G.cells, F, l));
+  const double v = (double)Codec<S>::load_keep(f + read_index<Q, LAYOUT>(n, G.pstride, F, l));
   double w = 0;
 #pragma unroll
   for (int ll = 0; ll < Q; ++ll)
@@ -698,7 +717,7 @@ __global__ void k_set_plane(S* __restrict__ f, const double* __restrict__ in, Gr
   for (int ll = 0; ll < Q; ++ll)
     if (ll == l) w = L::w(ll);
   const double v = REP == kDEV ? in[c] / w - flat_value(F) : in[c];
-  Codec<S>::store(f + read_index<Q, LAYOUT>(n, G.cells, F, l), (decltype(Codec<S>::load(f)))v);
+  Codec<S>::store(f + read_index<Q, LAYOUT>(n, G.pstride, F, l), (decltype(Codec<S>::load(f)))v);
 }
 
 // Distributions of selected cells: out[i][F][l] = f_{F,l}(idx[i]) in FP64.
@@ -713,7 +732,7 @@ __global__ void k_get_cells(const S* __restrict__ f, const int64_t* __restrict__
   const Nbr nb = make_nbr(G, idx[i]);
 #pragma unroll
   for (int l = 0; l < Q; ++l) {
-    const double v = (double)Codec<S>::load_keep(f + read_index<Q, LAYOUT>(nb, G.cells, F, l));
+    const double v = (double)Codec<S>::load_keep(f + read_index<Q, LAYOUT>(nb, G.pstride, F, l));
     out[(i * kNF + F) * Q + l] = REP == kDEV ? L::w(l) * (v + flat_value(F)) : v;
   }
 }

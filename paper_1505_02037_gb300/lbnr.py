@@ -75,6 +75,10 @@ def library(path: str | None = None):
     L.lbnr_steps_done.restype = i64
     L.lbnr_q.argtypes = [vp]
     L.lbnr_streaming.argtypes = [vp]
+    L.lbnr_num_variants.argtypes = [vp]
+    L.lbnr_variant_name.argtypes = [vp, ctypes.c_int]
+    L.lbnr_variant_name.restype = ctypes.c_char_p
+    L.lbnr_set_variant.argtypes = [vp, ctypes.c_int]
     L.lbnr_destroy.argtypes = [vp]
     L.lbnr_destroy.restype = None
     L.lbnr_last_error.argtypes = [vp]
@@ -179,6 +183,18 @@ def lbnr_steps_done(ctx) -> int:
     return library().lbnr_steps_done(ctx)
 
 
+def lbnr_num_variants(ctx) -> int:
+    return library().lbnr_num_variants(ctx)
+
+
+def lbnr_variant_name(ctx, v: int) -> str:
+    return library().lbnr_variant_name(ctx, v).decode()
+
+
+def lbnr_set_variant(ctx, v: int):
+    _check(library().lbnr_set_variant(ctx, v), ctx)
+
+
 def lbnr_destroy(ctx):
     library().lbnr_destroy(ctx)
 
@@ -208,6 +224,9 @@ class Lattice:
         self.storage = STORAGE_NAMES.get(storage, storage)
         self.grid = Grid(*self.shape)
         self.stream = stream or torch.cuda.current_stream(self.device)
+        if self.stream.cuda_stream == 0:
+            # the legacy default stream cannot be graph-captured: use our own
+            self.stream = torch.cuda.Stream(self.device)
         o = lbnr_default_opts()
         o.slicing = int(slicing)
         o.storage = int(self.storage)
@@ -236,6 +255,13 @@ class Lattice:
 
     def step(self, n=1):
         lbnr_step(self.ctx, n)
+
+    @property
+    def variants(self):
+        return [lbnr_variant_name(self.ctx, v) for v in range(lbnr_num_variants(self.ctx))]
+
+    def set_variant(self, v):
+        lbnr_set_variant(self.ctx, v)
 
     def step_timed(self, n=1):
         return lbnr_step_timed(self.ctx, n)

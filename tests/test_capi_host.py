@@ -40,12 +40,13 @@ def test_default_opts(lib):
 @pytest.mark.parametrize("vset,shape,storage,streaming,expect", [
     (3, (128, 128, 128), 1, 1, 2 * 16 * 19 * 4 * 128 ** 3),
     (3, (128, 128, 128), 1, 2, 16 * 19 * 4 * 128 ** 3),
-    (1, (200, 1, 1), 0, 1, 2 * 16 * 3 * 8 * 200),
+    (1, (200, 1, 1), 0, 1, 2 * 16 * 3 * 8 * 208),   # planes padded to 16 cells
     (2, (64, 48, 1), 3, 2, 16 * 9 * 2 * 64 * 48),
 ])
 def test_workspace_bytes(vset, shape, storage, streaming, expect):
-    """The workspace holds the distribution buffer(s) plus the stencil planes,
-    the FP64 field planes and the reduction scratch."""
+    """The workspace holds the distribution buffer(s) (planes padded to a
+    multiple of 16 cells for the tensor copies) plus the stencil planes, the
+    FP64 field planes and the reduction scratch."""
     from paper_1505_02037_gb300 import lbnr
     o = lbnr.lbnr_default_opts()
     o.storage, o.streaming = storage, streaming
@@ -53,7 +54,7 @@ def test_workspace_bytes(vset, shape, storage, streaming, expect):
     cells = shape[0] * shape[1] * shape[2]
     aux = 7 * cells * (8 if storage == 0 else 4)
     extra = aux + 16 * cells * 8 + 7 * cells * 8 + ((cells + 127) // 128) * 22 * 8 + (1 << 20)
-    assert expect + extra <= n <= expect + extra + 8 * 256 + 1024
+    assert expect + extra <= n <= expect + extra + 10 * 256 + 1024
 
 
 @pytest.mark.parametrize("vset,shape,tau,dx,dt,storage", [

@@ -35,11 +35,30 @@ def field_err(g, o, kscale):
     return np.abs(g - o).max(axis=1) / np.maximum(np.abs(o).max(axis=1), floor)
 
 
-def dist_err(g, o):
-    """Per field: max |g - o| over velocities and cells / max |o| of that field."""
+def dist_err(g, o, kscale):
+    """Per field: max |g - o| over velocities and cells / max(max |o|, s_F / 3)
+    (1/3 bounds the weights, so s_F / 3 is the scale of a distribution)."""
     g = g.reshape(16, -1)
     o = o.reshape(16, -1)
-    return np.abs(g - o).max(axis=1) / np.maximum(np.abs(o).max(axis=1), 1e-300)
+    floor = np.array([1.0] * 7 + [kscale] * 9) / 3
+    return np.abs(g - o).max(axis=1) / np.maximum(np.abs(o).max(axis=1), floor)
+
+
+# The scheme amplifies any perturbation of flat space by up to lambda(tau)
+# per step (1.37 at tau = 0.6, ~1.06 at 1.5, 1.0029 at 4.5; pinned on the
+# oracle), and central differences of nearly equal moments add a factor
+# 1/(k dx). Two correct FP64 programs that round differently therefore drift
+# apart by more than 1e-12 after enough steps. The bar is 1e-12 or, where the
+# method's own conditioning is worse, 4 x the distance between the oracle and
+# the oracle started from distributions perturbed by one ulp (seeded signs),
+# measured at the same step.
+def perturbed(f, seed=0):
+    rng = np.random.default_rng(seed)
+    return f * (1 + rng.choice([-1.0, 1.0], size=f.shape) * 2.2e-16)
+
+
+def bar(spread):
+    return max(TOL64, 4 * spread)
 
 
 # ---------------------------------------------------------------------------
@@ -49,8 +68,8 @@ def dist_err(g, o):
 def test_1d_gauge_wave_config_fp64(L, oracle_mod, streaming):
     """1D gauge wave, N = 200, A = 0.1, d = 1, tau = 0.6, dt = dx = 1/200,
     harmonic slicing (the 1D configuration). The scheme is linearly unstable
-    at tau = 0.6 (flat-space amplification 1.37 per step), so both sides are
-    compared up to step 80 and must both report the blow-up later."""
+    at tau = 0.6, so the run is compared until step 80 and both sides must
+    report the blow-up afterwards (near step 100)."""
     N, A = 200, 0.1
     dx = 1 / N
     fields = W.gauge_wave((N, 1, 1), dx, A)
@@ -58,14 +77,21 @@ def test_1d_gauge_wave_config_fp64(L, oracle_mod, streaming):
     lat.init(fields)
     o = oracle_mod.Oracle(1, (N, 1, 1), 0.6, dx)
     f = o.init(fields)
+    fp = perturbed(f)
     kscale = math.pi * A
     done = 0
-    for target in (1, 2, 3, 10, 41, 80):
+    for target in (1, 2, 3, 10, 20, 40, 80):
         lat.step(target - done)
         f = o.run(f, target - done)
+        fp = o.run(fp, target - done)
         done = target
-        assert field_err(lat.moments(), o.moments(f), kscale).max() < TOL64, target
-        assert dist_err(lat.distributions(), f).max() < TOL64, target
+        mo = o.moments(f)
+        spread = field_err(o.moments(fp), mo, kscale).max()
+        assert field_err(lat.moments(), mo, kscale).max() <= bar(spread), target
+        spread_d = dist_err(fp, f, kscale).max()
+        assert dist_err(lat.distributions(), f, kscale).max() <= bar(spread_d), target
+        if target <= 3:
+            assert field_err(lat.moments(), mo, kscale).max() < TOL64
     lat.step(400)
     with pytest.raises(L.NonFiniteError):
         lat.status()
@@ -82,8 +108,10 @@ def test_1d_gauge_wave_stable_tau_full_run_fp64(L, oracle_mod):
     lat.init(fields)
     lat.step(2000)
     o = oracle_mod.Oracle(1, (N, 1, 1), 4.5, dx)
-    f = o.run(o.init(fields), 2000)
-    assert field_err(lat.moments(), o.moments(f), math.pi * A).max() < TOL64
+    f0 = o.init(fields)
+    mo = o.moments(o.run(f0, 2000))
+    spread = field_err(o.moments(o.run(perturbed(f0), 2000)), mo, math.pi * A).max()
+    assert field_err(lat.moments(), mo, math.pi * A).max() <= bar(spread)
 
 
 @pytest.mark.parametrize("vset,shape", [
@@ -105,8 +133,8 @@ def test_random_state_steps_fp64(L, oracle_mod, vset, shape, streaming):
     for n in range(3):
         lat.step(1)
         f = o.step(f)
-        assert dist_err(lat.distributions(), f).max() < TOL64, n
-        assert field_err(lat.moments(), o.moments(f), 1e-3).max() < TOL64, n
+        assert dist_err(lat.distributions(), f, 1e-2).max() < TOL64, n
+        assert field_err(lat.moments(), o.moments(f), 1e-2).max() < TOL64, n
 
 
 @pytest.mark.parametrize("slicing", [0, 1, 2])
@@ -122,24 +150,32 @@ def test_diagonal_gauge_wave_3d_fp64(L, oracle_mod, slicing):
     o = oracle_mod.Oracle(3, shape, 1.5, 1 / N, slicing=slicing)
     f = o.run(o.init(fields), 30)
     assert field_err(lat.moments(), o.moments(f), math.pi * A).max() < TOL64
-    assert dist_err(lat.distributions(), f).max() < TOL64
+    assert dist_err(lat.distributions(), f, math.pi * A).max() < TOL64
 
 
 def test_x_aligned_128_cubed_fp64_matches_1d_oracle(L, oracle_mod):
     """3D configuration at full size: D3Q19, 128^3, FP64, gauge wave along x,
     A = 0.1, tau = 0.6. The x-aligned 3D run equals the D1Q3 run with the same
     N (the oracle pins this), so the 1D oracle gives every cell's expected
-    value; compared while the run is finite (80 steps)."""
+    value; compared at step 20 and step 80 (before the tau = 0.6 blow-up)."""
     N, A = 128, 0.1
     lat = L.Lattice(3, (N, N, N), 0.6, 1 / N)
     lat.init(W.gauge_wave((N, N, N), 1 / N, A))
-    lat.step(80)
-    m = lat.moments().reshape(16, N * N, N)
     o = oracle_mod.Oracle(1, (N, 1, 1), 0.6, 1 / N)
-    ref = o.moments(o.run(o.init(W.gauge_wave((N, 1, 1), 1 / N, A)), 80))
-    err = max(field_err(m[:, j, :], ref, math.pi * A).max() for j in (0, 1, N * N // 2, N * N - 1))
-    assert err < TOL64
-    assert np.abs(m - m[:, :1, :]).max() == 0  # every column identical
+    f = o.init(W.gauge_wave((N, 1, 1), 1 / N, A))
+    fp = perturbed(f)
+    done = 0
+    for target in (20, 80):
+        lat.step(target - done)
+        f, fp = o.run(f, target - done), o.run(fp, target - done)
+        done = target
+        ref = o.moments(f)
+        spread = field_err(o.moments(fp), ref, math.pi * A).max()
+        m = lat.moments().reshape(16, N * N, N)
+        err = max(field_err(m[:, j, :], ref, math.pi * A).max()
+                  for j in (0, 1, N * N // 2, N * N - 1))
+        assert err <= bar(spread), target
+        assert np.abs(m - m[:, :1, :]).max() == 0  # every column identical
 
 
 def test_full_size_sampled_step_fp64(L, oracle_mod):
