@@ -230,7 +230,9 @@ def main():
             dist.barrier()
             torch.cuda.synchronize()
 
-    # warm-up (also captures the step graphs)
+    # warm-up: the autotuner's trial steps, then graph capture
+    from paper_1505_02037_gb300 import autotune
+    tuning = autotune.tune(lat)
     lat.step(args.warmup)
     barrier()
     stream = lat.stream
@@ -294,6 +296,8 @@ def main():
         "step_algorithmic_hbm_frac": (alg_collide + alg_aux) / (ms_max / args.steps * 1e-3)
                                      / 1e9 / peak,
         "gpu_launches": 2 * args.steps,
+        "launch_form": lat.variants[lat.variant] if hasattr(lat, "variant") else None,
+        "autotune_ms_per_collide": tuning,
         "clocks": clk.summary(),
     }
 

@@ -247,6 +247,7 @@ class Lattice:
         self.dt = float(dx if dt is None else dt)
         self.ctx = lbnr_create(self.grid, self.vset, self.tau, self.dx, self.dt, o)
         self.streaming = library().lbnr_streaming(self.ctx)
+        self.variant = 0
 
     def init(self, fields):
         a = fields if not isinstance(fields, np.ndarray) else np.ascontiguousarray(
@@ -262,6 +263,7 @@ class Lattice:
 
     def set_variant(self, v):
         lbnr_set_variant(self.ctx, v)
+        self.variant = v
 
     def step_timed(self, n=1):
         return lbnr_step_timed(self.ctx, n)
