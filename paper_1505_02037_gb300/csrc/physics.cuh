@@ -18,14 +18,12 @@
 
 namespace lbnr {
 
+// Index of the stored component (i, j) of a symmetric tensor. Not recursive,
+// so that every use with constant arguments folds to an immediate and the
+// arrays it indexes stay in registers.
 __host__ __device__ constexpr int sym(int i, int j) {
-  return i > j ? sym(j, i) : (i == 0 ? j : (i == 1 ? 2 + j : 5));
+  return (i < j ? i : j) == 0 ? (i < j ? j : i) : ((i < j ? i : j) == 1 ? 2 + (i < j ? j : i) : 5);
 }
-
-template <class T>
-struct Geometry {
-  T gi[6];  // inverse metric
-};
 
 template <class T>
 __device__ __forceinline__ void invert_sym3(const T g[6], T gi[6]) {
