@@ -139,6 +139,13 @@ int validate(const lbnr_grid* g, int vset, const lbnr_opts* o) {
     return fail(nullptr, LBNR_EINVAL, "grid sizes must be positive");
   if (g->nx > (1 << 30) || g->ny > (1 << 30) || g->nz > (1 << 30))
     return fail(nullptr, LBNR_EINVAL, "grid side too large");
+  {
+    // 32-bit cell indices, and 32-bit offsets inside a field's Q planes
+    const uint64_t cells = (uint64_t)g->nx * g->ny * g->nz;
+    const uint64_t ps = (cells + kTile - 1) / kTile * kTile;
+    if (cells >= (1ull << 31) || (uint64_t)q_of(vset) * ps >= (1ull << 32))
+      return fail(nullptr, LBNR_EINVAL, "lattice too large (%llu cells)", (unsigned long long)cells);
+  }
   if (vset == LBNR_D1Q3 && (g->ny != 1 || g->nz != 1))
     return fail(nullptr, LBNR_EINVAL, "D1Q3 needs ny = nz = 1");
   if (vset == LBNR_D2Q9 && g->nz != 1) return fail(nullptr, LBNR_EINVAL, "D2Q9 needs nz = 1");

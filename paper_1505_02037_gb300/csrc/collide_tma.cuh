@@ -99,7 +99,7 @@ template <int Q, class S, class C, int REP, int LAYOUT, int NC, int NS>
 __global__ void __launch_bounds__(32 * (NC + 1), 1)
     k_collide_tma(const StepArgs<S, C> a, const __grid_constant__ CUtensorMap tmap, int64_t ntiles) {
   static_assert(LAYOUT == kPingPong || LAYOUT == kAAEven, "reads must be local");
-  static_assert(NS % NC == 0, "each consumer owns NS/NC stages");
+  static_assert(NS > NC, "the ring must hold more stages than consumers");
   using L = Lattice<Q>;
   using TS = TmaShape<Q>;
   constexpr int T = kTileCells;
@@ -157,23 +157,31 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
   }
 
   // ---------------- consumers ----------------
+  // Tile j of this CTA uses stage j % NS and consumer warp j % NC. The
+  // producer refills stage s for tile j only after tile j - NS released it;
+  // that tile belongs to a consumer whose earlier tiles precede it, so the
+  // ring cannot deadlock for any NS > NC.
   const int g = lane >> 4;
   const int ci = lane & 15;
   const int64_t cells = a.G.cells;
   const int64_t ps = a.G.pstride;
+  const uint32_t ps32 = (uint32_t)ps;
   for (int64_t j = warp; j < my; j += NC) {
     const int s = (int)(j % NS);
     const uint32_t ph = (uint32_t)((j / NS) & 1);
-    if (!mbar_wait(smem_u32(&bars[s]), ph, kLimitNs)) {
-      if (lane == 0) atomicOr(a.flag, 2);
-      break;
-    }
-    const S* st = reinterpret_cast<const S*>(stages + (size_t)s * STAGEB);
     const int64_t tile = blockIdx.x + j * G;
     const int64_t cell = tile * T + ci;
     const bool valid = cell < cells;
     const int64_t c = valid ? cell : cells - 1;
     const Nbr n = make_nbr(a.G, c);
+    // stencil loads first: their latency overlaps the wait for the stage
+    C A[3], D[3][6];
+    derivatives<Q, C>(n, cells, a.aux, a.inv2dx, a.inv4dx, A, D);
+    if (!mbar_wait(smem_u32(&bars[s]), ph, kLimitNs)) {
+      if (lane == 0) atomicOr(a.flag, 2);
+      break;
+    }
+    const S* st = reinterpret_cast<const S*>(stages + (size_t)s * STAGEB);
 
     // moments of this lane's 8 fields
     C mine[8];
@@ -203,8 +211,6 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
       if (valid && g == 0 && !isfinite(chk)) atomicOr(a.flag, 1);
     }
 
-    C A[3], D[3][6];
-    derivatives<Q, C>(n, cells, a.aux, a.inv2dx, a.inv4dx, A, D);
     C alpha, gm[6], K[6], V[3];
     unpack<REP, C>(rt, alpha, gm, K, V);
     C Sr[kNF];
@@ -235,6 +241,7 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
         for (int k = 0; k < dim; ++k) b[k] = three_omega * (g ? Fl[F1 - kK][k] : Fl[F0 - kK][k]);
       }
       const S* row = st + (F * Q) * T + ci;
+      S* ob = a.fout + field_base<Q>(F, ps);
 #pragma unroll
       for (int l = 0; l < Q; ++l) {
         const C v = (C)row[l * T];
@@ -247,7 +254,7 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
           }
         }
         const C out = REP == kDEV ? fma(a.omc, v, t) : fma(a.omc, v, C(L::w(l)) * t);
-        if (valid) Codec<S>::store(a.fout + write_index<Q, LAYOUT>(n, ps, F, l), out);
+        if (valid) Codec<S>::store(ob + write_off<Q, LAYOUT>(n, ps32, l), out);
       }
     }
     __syncwarp();

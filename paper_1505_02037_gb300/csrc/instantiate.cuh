@@ -32,17 +32,17 @@ struct VariantTable;
     static constexpr int fallback = FALLBACK_;               \
   };
 // FP64 storage (FP64 arithmetic)
-LBNR_VARIANTS(3, 8, 0, {0, 1, true, 0, 0}, {1, 2, false, 4, 8})
-LBNR_VARIANTS(9, 8, 0, {0, 1, false, 0, 0}, {1, 2, false, 4, 8})
-LBNR_VARIANTS(19, 8, 0, {0, 1, false, 0, 0}, {1, 2, false, 2, 4}, {1, 2, false, 4, 4})
+LBNR_VARIANTS(3, 8, 0, {0, 1, true, 0, 0}, {1, 2, false, 8, 16})
+LBNR_VARIANTS(9, 8, 0, {0, 1, false, 0, 0}, {1, 2, false, 8, 11})
+LBNR_VARIANTS(19, 8, 0, {0, 1, false, 0, 0}, {1, 2, false, 2, 5}, {1, 2, false, 4, 5})
 // FP32 storage
 LBNR_VARIANTS(3, 4, 1, {1, 2, false, 8, 16}, {0, 1, true, 0, 0})
 LBNR_VARIANTS(9, 4, 1, {1, 2, false, 8, 16}, {0, 1, true, 0, 0})
-LBNR_VARIANTS(19, 4, 2, {1, 2, false, 4, 8}, {1, 2, false, 5, 10}, {0, 2, true, 0, 0})
+LBNR_VARIANTS(19, 4, 2, {1, 2, false, 8, 11}, {1, 2, false, 6, 9}, {0, 2, true, 0, 0})
 // 16-bit storage
 LBNR_VARIANTS(3, 2, 1, {1, 2, false, 8, 16}, {0, 1, true, 0, 0})
 LBNR_VARIANTS(9, 2, 1, {1, 2, false, 8, 16}, {0, 1, true, 0, 0})
-LBNR_VARIANTS(19, 2, 2, {1, 2, false, 8, 16}, {1, 2, false, 4, 16}, {0, 2, true, 0, 0})
+LBNR_VARIANTS(19, 2, 2, {1, 2, false, 12, 20}, {1, 2, false, 8, 16}, {0, 2, true, 0, 0})
 #undef LBNR_VARIANTS
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no
@@ -181,7 +181,7 @@ struct Impl {
     a.fout = static_cast<S*>(fout);
     a.aux = static_cast<const C*>(L.aux);
     a.flag = L.flag;
-    a.G = Grid{L.nx, L.ny, L.nz, L.cells, L.pstride};
+    a.G = make_grid(L.nx, L.ny, L.nz, L.cells, L.pstride);
     a.inv2dx = C(1.0 / (2.0 * L.dx));
     a.inv4dx = C(1.0 / (4.0 * L.dx));
     a.half_dt = C(0.5 * L.dt);
@@ -196,7 +196,7 @@ struct Impl {
   }
 
   static cudaError_t aux(const LaunchCtx& L, int layout, const void* f) {
-    const Grid G{L.nx, L.ny, L.nz, L.cells, L.pstride};
+    const Grid G = make_grid(L.nx, L.ny, L.nz, L.cells, L.pstride);
     const unsigned grid = grid_for(L.cells, 256);
     const S* fp = static_cast<const S*>(f);
     C* ap = static_cast<C*>(L.aux);
@@ -211,7 +211,7 @@ struct Impl {
     a.fields = L.macro;
     a.f = static_cast<S*>(f);
     a.flag = L.flag;
-    a.G = Grid{L.nx, L.ny, L.nz, L.cells, L.pstride};
+    a.G = make_grid(L.nx, L.ny, L.nz, L.cells, L.pstride);
     a.inv2dx = 1.0 / (2.0 * L.dx);
     a.inv4dx = 1.0 / (4.0 * L.dx);
     a.half_dt = 0.5 * L.dt;
@@ -222,7 +222,7 @@ struct Impl {
   }
 
   static cudaError_t sum64(const LaunchCtx& L, int layout, const void* f, int64_t* nblocks) {
-    const Grid G{L.nx, L.ny, L.nz, L.cells, L.pstride};
+    const Grid G = make_grid(L.nx, L.ny, L.nz, L.cells, L.pstride);
     const unsigned grid = grid_for(L.cells, 256);
     *nblocks = grid;
     const S* fp = static_cast<const S*>(f);
@@ -236,7 +236,7 @@ struct Impl {
   }
 
   static cudaError_t correct64(const LaunchCtx& L) {
-    const Grid G{L.nx, L.ny, L.nz, L.cells, L.pstride};
+    const Grid G = make_grid(L.nx, L.ny, L.nz, L.cells, L.pstride);
     k_correct64<Q><<<grid_for(L.cells, 128), 128, 0, L.st>>>(
         L.macro, L.aux64, G, 1.0 / (2.0 * L.dx), 1.0 / (4.0 * L.dx), 0.5 * L.dt, L.slicing,
         L.sources_on);
@@ -244,7 +244,7 @@ struct Impl {
   }
 
   static cudaError_t constraints64(const LaunchCtx& L, int64_t* nblocks) {
-    const Grid G{L.nx, L.ny, L.nz, L.cells, L.pstride};
+    const Grid G = make_grid(L.nx, L.ny, L.nz, L.cells, L.pstride);
     const unsigned grid = grid_for(L.cells, 128);
     *nblocks = grid;
     k_constraints64<Q><<<grid, 128, 0, L.st>>>(L.macro, G, 1.0 / (2.0 * L.dx), 1.0 / (4.0 * L.dx),
@@ -254,7 +254,7 @@ struct Impl {
 
   static cudaError_t get_plane(const LaunchCtx& L, int layout, const void* f, int F, int l,
                                double* out) {
-    const Grid G{L.nx, L.ny, L.nz, L.cells, L.pstride};
+    const Grid G = make_grid(L.nx, L.ny, L.nz, L.cells, L.pstride);
     const unsigned grid = grid_for(L.cells, 256);
     const S* fp = static_cast<const S*>(f);
     if (layout == kPingPong) k_get_plane<Q, S, REP, kPingPong><<<grid, 256, 0, L.st>>>(fp, out, G, F, l);
@@ -265,7 +265,7 @@ struct Impl {
 
   static cudaError_t set_plane(const LaunchCtx& L, int layout, void* f, int F, int l,
                                const double* in) {
-    const Grid G{L.nx, L.ny, L.nz, L.cells, L.pstride};
+    const Grid G = make_grid(L.nx, L.ny, L.nz, L.cells, L.pstride);
     const unsigned grid = grid_for(L.cells, 256);
     S* fp = static_cast<S*>(f);
     if (layout == kPingPong) k_set_plane<Q, S, REP, kPingPong><<<grid, 256, 0, L.st>>>(fp, in, G, F, l);
@@ -276,7 +276,7 @@ struct Impl {
 
   static cudaError_t get_cells(const LaunchCtx& L, int layout, const void* f, int64_t n,
                                const int64_t* idx, double* out) {
-    const Grid G{L.nx, L.ny, L.nz, L.cells, L.pstride};
+    const Grid G = make_grid(L.nx, L.ny, L.nz, L.cells, L.pstride);
     const unsigned grid = grid_for(n * kNF, 128);
     const S* fp = static_cast<const S*>(f);
     if (layout == kPingPong) k_get_cells<Q, S, REP, kPingPong><<<grid, 128, 0, L.st>>>(fp, idx, n, out, G);

@@ -94,58 +94,99 @@ __host__ __device__ constexpr bool has_flux(int F) { return F >= kK && F < kV; }
 // ---------------------------------------------------------------------------
 // Geometry of one cell and its neighbours (periodic)
 // ---------------------------------------------------------------------------
+// n / d for n < 2^31 by a multiply-high with a precomputed round-up
+// multiplier (Granlund-Montgomery); d = 1 is passed through.
+struct FastDiv {
+  uint32_t d, mul, shift;
+  __device__ __forceinline__ uint32_t div(uint32_t n) const {
+    return d == 1 ? n : (__umulhi(n, mul) >> shift);
+  }
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f{d, 0, 0};
+  if (d > 1) {
+    uint32_t l = 0;
+    while ((1ull << l) < d) ++l;  // ceil(log2 d)
+    const uint32_t p = 31 + l;
+    f.mul = (uint32_t)(((1ull << p) + d - 1) / d);
+    f.shift = p - 32;
+  }
+  return f;
+}
+
 struct Grid {
   int32_t nx, ny, nz;
-  int64_t cells;
+  int64_t cells;    // < 2^31, and Q * pstride < 2^32
   int64_t pstride;  // elements between consecutive distribution planes (>= cells)
+  FastDiv fx, fy;   // division by nx and by ny
 };
 
+inline Grid make_grid(int32_t nx, int32_t ny, int32_t nz, int64_t cells, int64_t pstride) {
+  return Grid{nx, ny, nz, cells, pstride, make_fastdiv((uint32_t)nx), make_fastdiv((uint32_t)ny)};
+}
+
+// A cell and its periodic neighbours, as 32-bit cell indices.
 struct Nbr {
-  int64_t c;      // this cell
-  int64_t ox[3];  // offset along x for c_x = 0, +1, -1
-  int64_t oy[3];
-  int64_t oz[3];
-  __device__ __forceinline__ int64_t at(int cx, int cy, int cz) const {
-    return c + ox[cx == 0 ? 0 : (cx > 0 ? 1 : 2)] + oy[cy == 0 ? 0 : (cy > 0 ? 1 : 2)] +
-           oz[cz == 0 ? 0 : (cz > 0 ? 1 : 2)];
+  uint32_t c;
+  int32_t ox[3];  // offset along x for c_x = 0, +1, -1
+  int32_t oy[3];
+  int32_t oz[3];
+  __device__ __forceinline__ uint32_t at(int cx, int cy, int cz) const {
+    return (uint32_t)((int32_t)c + ox[cx == 0 ? 0 : (cx > 0 ? 1 : 2)] +
+                      oy[cy == 0 ? 0 : (cy > 0 ? 1 : 2)] + oz[cz == 0 ? 0 : (cz > 0 ? 1 : 2)]);
   }
 };
 
-__device__ __forceinline__ Nbr make_nbr(const Grid& G, int64_t c) {
+__device__ __forceinline__ Nbr make_nbr(const Grid& G, int64_t c64) {
   Nbr n;
+  const uint32_t c = (uint32_t)c64;
   n.c = c;
-  const int64_t plane = (int64_t)G.nx * G.ny;
-  const int32_t x = (int32_t)(c % G.nx);
-  const int64_t t = c / G.nx;
-  const int32_t y = (int32_t)(t % G.ny);
-  const int32_t z = (int32_t)(t / G.ny);
+  const uint32_t t = G.fx.div(c);
+  const int32_t x = (int32_t)(c - t * (uint32_t)G.nx);
+  const uint32_t zz = G.fy.div(t);
+  const int32_t y = (int32_t)(t - zz * (uint32_t)G.ny);
+  const int32_t z = (int32_t)zz;
+  const int32_t plane = G.nx * G.ny;
   n.ox[0] = 0;
-  n.ox[1] = (x + 1 == G.nx) ? -(int64_t)(G.nx - 1) : 1;
-  n.ox[2] = (x == 0) ? (int64_t)(G.nx - 1) : -1;
+  n.ox[1] = (x + 1 == G.nx) ? -(G.nx - 1) : 1;
+  n.ox[2] = (x == 0) ? (G.nx - 1) : -1;
   n.oy[0] = 0;
-  n.oy[1] = ((y + 1 == G.ny) ? -(int64_t)(G.ny - 1) : 1) * (int64_t)G.nx;
-  n.oy[2] = ((y == 0) ? (int64_t)(G.ny - 1) : -1) * (int64_t)G.nx;
+  n.oy[1] = ((y + 1 == G.ny) ? -(G.ny - 1) : 1) * G.nx;
+  n.oy[2] = ((y == 0) ? (G.ny - 1) : -1) * G.nx;
   n.oz[0] = 0;
-  n.oz[1] = ((z + 1 == G.nz) ? -(int64_t)(G.nz - 1) : 1) * plane;
-  n.oz[2] = ((z == 0) ? (int64_t)(G.nz - 1) : -1) * plane;
+  n.oz[1] = ((z + 1 == G.nz) ? -(G.nz - 1) : 1) * plane;
+  n.oz[2] = ((z == 0) ? (G.nz - 1) : -1) * plane;
   return n;
 }
 
-// Where f_{F,l}(x) of the current state lives, for each layout (ps: plane
-// stride).
+// Addresses: field F's Q planes start at field_base(F) (64-bit); inside the
+// block every distribution is a 32-bit offset l' * pstride + cell.
+template <int Q>
+__device__ __forceinline__ size_t field_base(int F, int64_t ps) {
+  return (size_t)(F * Q) * (size_t)ps;
+}
+// Where f_{F,l}(x) of the current state lives, for each layout.
 template <int Q, int LAYOUT>
-__device__ __forceinline__ int64_t read_index(const Nbr& n, int64_t ps, int F, int l) {
+__device__ __forceinline__ uint32_t read_off(const Nbr& n, uint32_t ps, int l) {
   using L = Lattice<Q>;
   if (LAYOUT == kAAOdd)
-    return (int64_t)(F * Q + opposite(l)) * ps + n.at(-L::c(l, 0), -L::c(l, 1), -L::c(l, 2));
-  return (int64_t)(F * Q + l) * ps + n.c;
+    return (uint32_t)opposite(l) * ps + n.at(-L::c(l, 0), -L::c(l, 1), -L::c(l, 2));
+  return (uint32_t)l * ps + n.c;
 }
 // Where f*_{F,l}(x) goes.
 template <int Q, int LAYOUT>
-__device__ __forceinline__ int64_t write_index(const Nbr& n, int64_t ps, int F, int l) {
+__device__ __forceinline__ uint32_t write_off(const Nbr& n, uint32_t ps, int l) {
   using L = Lattice<Q>;
-  if (LAYOUT == kAAEven) return (int64_t)(F * Q + opposite(l)) * ps + n.c;
-  return (int64_t)(F * Q + l) * ps + n.at(L::c(l, 0), L::c(l, 1), L::c(l, 2));
+  if (LAYOUT == kAAEven) return (uint32_t)opposite(l) * ps + n.c;
+  return (uint32_t)l * ps + n.at(L::c(l, 0), L::c(l, 1), L::c(l, 2));
+}
+template <int Q, int LAYOUT>
+__device__ __forceinline__ size_t read_index(const Nbr& n, int64_t ps, int F, int l) {
+  return field_base<Q>(F, ps) + read_off<Q, LAYOUT>(n, (uint32_t)ps, l);
+}
+template <int Q, int LAYOUT>
+__device__ __forceinline__ size_t write_index(const Nbr& n, int64_t ps, int F, int l) {
+  return field_base<Q>(F, ps) + write_off<Q, LAYOUT>(n, (uint32_t)ps, l);
 }
 
 // ---------------------------------------------------------------------------
@@ -191,13 +232,14 @@ __device__ __forceinline__ void derivatives(const Nbr& n, int64_t cells, const C
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     if (k < dim) {
-      const int64_t cp = n.at(k == 0, k == 1, k == 2);
-      const int64_t cm = n.at(-(k == 0), -(k == 1), -(k == 2));
+      const uint32_t cp = n.at(k == 0, k == 1, k == 2);
+      const uint32_t cm = n.at(-(k == 0), -(k == 1), -(k == 2));
       A[k] = (__ldg(aux + cp) - __ldg(aux + cm)) * inv2dx;
 #pragma unroll
-      for (int q = 0; q < 6; ++q)
-        D[k][q] = (__ldg(aux + (int64_t)(1 + q) * cells + cp) -
-                   __ldg(aux + (int64_t)(1 + q) * cells + cm)) * inv4dx;
+      for (int q = 0; q < 6; ++q) {
+        const C* plane = aux + (size_t)(1 + q) * (size_t)cells;
+        D[k][q] = (__ldg(plane + cp) - __ldg(plane + cm)) * inv4dx;
+      }
     } else {
       A[k] = C(0);
 #pragma unroll
@@ -236,6 +278,7 @@ __global__ void __launch_bounds__(128) k_collide(const StepArgs<S, C> a) {
   const int64_t c = valid ? cell : a.G.cells - 1;
   const int64_t cells = a.G.cells;
   const int64_t ps = a.G.pstride;
+  const uint32_t ps32 = (uint32_t)ps;
   const Nbr n = make_nbr(a.G, c);
 
   // Pass 1: zeroth moments of this thread's fields (ascending l).
@@ -244,15 +287,15 @@ __global__ void __launch_bounds__(128) k_collide(const StepArgs<S, C> a) {
 #pragma unroll
   for (int j = 0; j < NJ; ++j) {
     const int F = g ? field_of(P, 1, j) : field_of(P, 0, j);
+    const S* fb = a.fin + field_base<Q>(F, ps);
     C s = C(0);
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
       // In place (AA) the buffer is written by this kernel: re-read values
       // must come through coherent loads, never the read-only path.
-      const C v = HOLD ? Codec<S>::load(a.fin + read_index<Q, LAYOUT>(n, ps, F, l))
-                  : LAYOUT == kPingPong
-                      ? Codec<S>::load_keep(a.fin + read_index<Q, LAYOUT>(n, ps, F, l))
-                      : Codec<S>::load_coh(a.fin + read_index<Q, LAYOUT>(n, ps, F, l));
+      const S* src = fb + read_off<Q, LAYOUT>(n, ps32, l);
+      const C v = HOLD ? Codec<S>::load(src)
+                  : LAYOUT == kPingPong ? Codec<S>::load_keep(src) : Codec<S>::load_coh(src);
       if (HOLD) fv[HOLD ? j : 0][HOLD ? l : 0] = v;
       s += REP == kDEV ? C(L::w(l)) * v : v;
     }
@@ -316,13 +359,15 @@ __global__ void __launch_bounds__(128) k_collide(const StepArgs<S, C> a) {
     }
     // All Q values of this field are read before any is written: in place
     // (AA) the field's reads and writes touch the same Q locations.
+    const S* fb = a.fin + field_base<Q>(F, ps);
+    S* ob = a.fout + field_base<Q>(F, ps);
     C v_[Q];
 #pragma unroll
-    for (int l = 0; l < Q; ++l)
+    for (int l = 0; l < Q; ++l) {
+      const S* src = fb + read_off<Q, LAYOUT>(n, ps32, l);
       v_[l] = HOLD ? fv[HOLD ? j : 0][HOLD ? l : 0]
-              : LAYOUT == kPingPong
-                  ? Codec<S>::load_keep(a.fin + read_index<Q, LAYOUT>(n, ps, F, l))
-                  : Codec<S>::load_coh(a.fin + read_index<Q, LAYOUT>(n, ps, F, l));
+              : LAYOUT == kPingPong ? Codec<S>::load_keep(src) : Codec<S>::load_coh(src);
+    }
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
       const C v = v_[l];
@@ -335,7 +380,7 @@ __global__ void __launch_bounds__(128) k_collide(const StepArgs<S, C> a) {
         }
       }
       const C out = REP == kDEV ? fma(a.omc, v, t) : fma(a.omc, v, C(L::w(l)) * t);
-      if (valid) Codec<S>::store(a.fout + write_index<Q, LAYOUT>(n, ps, F, l), out);
+      if (valid) Codec<S>::store(ob + write_off<Q, LAYOUT>(n, ps32, l), out);
     }
   }
 }
