@@ -174,6 +174,10 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
     const bool valid = cell < cells;
     const int64_t c = valid ? cell : cells - 1;
     const Nbr n = make_nbr(a.G, c);
+    // destination offset of each velocity inside a field's block of planes
+    uint32_t woff[Q];
+#pragma unroll
+    for (int l = 0; l < Q; ++l) woff[l] = write_off<Q, LAYOUT>(n, ps32, l);
     // stencil loads first: their latency overlaps the wait for the stage
     C A[3], D[3][6];
     derivatives<Q, C>(n, cells, a.aux, a.inv2dx, a.inv4dx, A, D);
@@ -254,7 +258,7 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
           }
         }
         const C out = REP == kDEV ? fma(a.omc, v, t) : fma(a.omc, v, C(L::w(l)) * t);
-        if (valid) Codec<S>::store(ob + write_off<Q, LAYOUT>(n, ps32, l), out);
+        if (valid) Codec<S>::store(ob + woff[l], out);
       }
     }
     __syncwarp();

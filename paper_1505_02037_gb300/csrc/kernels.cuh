@@ -49,14 +49,16 @@ struct Codec<double> {
   __device__ static __forceinline__ double load(const double* p) { return __ldcs(p); }
   __device__ static __forceinline__ double load_keep(const double* p) { return __ldg(p); }
   __device__ static __forceinline__ double load_coh(const double* p) { return __ldcg(p); }
-  __device__ static __forceinline__ void store(double* p, double v) { __stcs(p, v); }
+  // Plain stores: the compiler predicates them (an asm store under a
+  // condition would become a branch around every store).
+  __device__ static __forceinline__ void store(double* p, double v) { *p = v; }
 };
 template <>
 struct Codec<float> {
   __device__ static __forceinline__ float load(const float* p) { return __ldcs(p); }
   __device__ static __forceinline__ float load_keep(const float* p) { return __ldg(p); }
   __device__ static __forceinline__ float load_coh(const float* p) { return __ldcg(p); }
-  __device__ static __forceinline__ void store(float* p, float v) { __stcs(p, v); }
+  __device__ static __forceinline__ void store(float* p, float v) { *p = v; }
 };
 template <>
 struct Codec<__nv_bfloat16> {
@@ -70,7 +72,7 @@ struct Codec<__nv_bfloat16> {
     return __bfloat162float(__ldcg(p));
   }
   __device__ static __forceinline__ void store(__nv_bfloat16* p, float v) {
-    __stcs(p, __float2bfloat16_rn(v));
+    *p = __float2bfloat16_rn(v);
   }
 };
 template <>
@@ -80,9 +82,7 @@ struct Codec<__half> {
     return __half2float(__ldg(p));
   }
   __device__ static __forceinline__ float load_coh(const __half* p) { return __half2float(__ldcg(p)); }
-  __device__ static __forceinline__ void store(__half* p, float v) {
-    __stcs(p, __float2half_rn(v));
-  }
+  __device__ static __forceinline__ void store(__half* p, float v) { *p = __float2half_rn(v); }
 };
 
 // Flat-space value of field F (alpha = 1, gamma = delta, K = V = 0).
@@ -288,12 +288,14 @@ __global__ void __launch_bounds__(128) k_collide(const StepArgs<S, C> a) {
   for (int j = 0; j < NJ; ++j) {
     const int F = g ? field_of(P, 1, j) : field_of(P, 0, j);
     const S* fb = a.fin + field_base<Q>(F, ps);
+    const S* fbc = fb + n.c;
     C s = C(0);
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
       // In place (AA) the buffer is written by this kernel: re-read values
       // must come through coherent loads, never the read-only path.
-      const S* src = fb + read_off<Q, LAYOUT>(n, ps32, l);
+      const S* src = LAYOUT == kAAOdd ? fb + read_off<Q, LAYOUT>(n, ps32, l)
+                                      : fbc + (size_t)((uint32_t)l * ps32);
       const C v = HOLD ? Codec<S>::load(src)
                   : LAYOUT == kPingPong ? Codec<S>::load_keep(src) : Codec<S>::load_coh(src);
       if (HOLD) fv[HOLD ? j : 0][HOLD ? l : 0] = v;
@@ -360,11 +362,13 @@ __global__ void __launch_bounds__(128) k_collide(const StepArgs<S, C> a) {
     // All Q values of this field are read before any is written: in place
     // (AA) the field's reads and writes touch the same Q locations.
     const S* fb = a.fin + field_base<Q>(F, ps);
+    const S* fbc = fb + n.c;
     S* ob = a.fout + field_base<Q>(F, ps);
     C v_[Q];
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
-      const S* src = fb + read_off<Q, LAYOUT>(n, ps32, l);
+      const S* src = LAYOUT == kAAOdd ? fb + read_off<Q, LAYOUT>(n, ps32, l)
+                                      : fbc + (size_t)((uint32_t)l * ps32);
       v_[l] = HOLD ? fv[HOLD ? j : 0][HOLD ? l : 0]
               : LAYOUT == kPingPong ? Codec<S>::load_keep(src) : Codec<S>::load_coh(src);
     }
@@ -394,12 +398,16 @@ __global__ void __launch_bounds__(256) k_aux(const S* __restrict__ f, C* __restr
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= G.cells) return;
   const Nbr n = make_nbr(G, c);
-#pragma unroll
+  const uint32_t ps32 = (uint32_t)G.pstride;
+  // One field at a time: its Q loads are in flight together, and the
+  // register count stays low enough for full occupancy.
+#pragma unroll 1
   for (int F = 0; F < 7; ++F) {
+    const S* fb = f + field_base<Q>(F, G.pstride);
     C s = C(0);
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
-      const C v = Codec<S>::load_keep(f + read_index<Q, LAYOUT>(n, G.pstride, F, l));
+      const C v = Codec<S>::load_keep(fb + read_off<Q, LAYOUT>(n, ps32, l));
       s += REP == kDEV ? C(L::w(l)) * v : v;
     }
     if (F == 0) s = REP == kDEV ? log1p(s) : log(s);
