@@ -3,7 +3,7 @@
 // equilibria and sources of Eqs. alfa-ekstsor and rho = sum f + dt S/2).
 //
 // One persistent CTA per SM. Warp NC (the producer) streams tiles of
-// kTileCells consecutive cells into a ring of NS shared-memory stages: every
+// TC consecutive cells into a ring of NS shared-memory stages: every
 // distribution plane of a tile is one row of the stage, and the whole stage
 // (16*Q rows) arrives through one or two 2D tensor copies
 // (cp.async.bulk.tensor) that signal a "full" mbarrier. Consumer warps
@@ -26,7 +26,6 @@
 
 namespace lbnr {
 
-constexpr int kTileCells = 16;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -88,21 +87,26 @@ struct TmaShape {
 };
 
 template <class S>
-__host__ __device__ constexpr uint32_t tma_stage_bytes(int Q) {
-  return (uint32_t)(kNF * Q * kTileCells * sizeof(S));
+__host__ __device__ constexpr uint32_t tma_stage_bytes(int Q, int TC) {
+  return (uint32_t)(kNF * Q * TC * sizeof(S));
 }
 __host__ __device__ constexpr uint32_t tma_smem_bytes(uint32_t stage_bytes, int NS) {
   return 1024u + stage_bytes * (uint32_t)NS;
 }
 
-template <int Q, class S, class C, int REP, int LAYOUT, int NC, int NS>
+// TC cells per tile (16 or 32); a tile is consumed by TC/16 warps together.
+template <int Q, class S, class C, int REP, int LAYOUT, int NC, int NS, int TC>
 __global__ void __launch_bounds__(32 * (NC + 1), 1)
     k_collide_tma(const StepArgs<S, C> a, const __grid_constant__ CUtensorMap tmap, int64_t ntiles) {
   static_assert(LAYOUT == kPingPong || LAYOUT == kAAEven, "reads must be local");
-  static_assert(NS > NC, "the ring must hold more stages than consumers");
+  constexpr int WPT = TC / 16;   // warps per tile
+  constexpr int NP = NC / WPT;   // tiles in flight among the consumers
+  static_assert(TC == 16 || TC == 32, "tile of 16 or 32 cells");
+  static_assert(NC % WPT == 0, "whole warp groups per tile");
+  static_assert(NS > NP, "the ring must hold more stages than tiles being consumed");
   using L = Lattice<Q>;
   using TS = TmaShape<Q>;
-  constexpr int T = kTileCells;
+  constexpr int T = TC;
   constexpr int dim = L::kDim;
   constexpr uint32_t ROWB = T * sizeof(S);
   constexpr uint32_t BOXB = TS::kPlanesPerBox * ROWB;
@@ -117,7 +121,7 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) {
       mbar_init(smem_u32(&bars[s]), 1);
-      mbar_init(smem_u32(&bars[NS + s]), 1);
+      mbar_init(smem_u32(&bars[NS + s]), WPT);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -157,16 +161,18 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
   }
 
   // ---------------- consumers ----------------
-  // Tile j of this CTA uses stage j % NS and consumer warp j % NC. The
-  // producer refills stage s for tile j only after tile j - NS released it;
-  // that tile belongs to a consumer whose earlier tiles precede it, so the
-  // ring cannot deadlock for any NS > NC.
+  // Tile j of this CTA uses stage j % NS and warp group j % NP (WPT warps,
+  // 16 cells each). The producer refills stage s for tile j only after tile
+  // j - NS released it; that tile belongs to a group whose earlier tiles
+  // precede it, so the ring cannot deadlock for any NS > NP.
   const int g = lane >> 4;
-  const int ci = lane & 15;
+  const int grp = warp / WPT;
+  const int half = warp % WPT;
+  const int ci = half * 16 + (lane & 15);
   const int64_t cells = a.G.cells;
   const int64_t ps = a.G.pstride;
   const uint32_t ps32 = (uint32_t)ps;
-  for (int64_t j = warp; j < my; j += NC) {
+  for (int64_t j = grp; j < my; j += NP) {
     const int s = (int)(j % NS);
     const uint32_t ph = (uint32_t)((j / NS) & 1);
     const int64_t tile = blockIdx.x + j * G;
@@ -258,7 +264,7 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
           }
         }
         const C out = REP == kDEV ? fma(a.omc, v, t) : fma(a.omc, v, C(L::w(l)) * t);
-        if (valid) Codec<S>::store(ob + woff[l], out);
+        Codec<S>::store_if(ob + woff[l], out, valid);
       }
     }
     __syncwarp();

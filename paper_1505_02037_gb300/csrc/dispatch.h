@@ -8,7 +8,7 @@
 namespace lbnr {
 
 constexpr uint64_t kStageBytes = 1ull << 20;
-constexpr int64_t kTile = 16;  // cells per tile of the TMA-fed kernel
+constexpr int64_t kTile = 32;  // plane padding: a multiple of every TMA tile width
 
 struct LaunchCtx {
   int32_t nx, ny, nz;

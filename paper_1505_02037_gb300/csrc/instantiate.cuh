@@ -19,7 +19,7 @@ namespace lbnr {
 struct VariantSpec {
   int kind, P;
   bool hold;
-  int nc, ns;
+  int nc, ns, tc;  // consumer warps, stages, cells per tile (kind 1)
 };
 
 template <int Q, int SB>
@@ -32,17 +32,17 @@ struct VariantTable;
     static constexpr int fallback = FALLBACK_;               \
   };
 // FP64 storage (FP64 arithmetic)
-LBNR_VARIANTS(3, 8, 0, {0, 1, true, 0, 0}, {1, 2, false, 8, 16})
-LBNR_VARIANTS(9, 8, 0, {0, 1, false, 0, 0}, {1, 2, false, 8, 11})
-LBNR_VARIANTS(19, 8, 0, {0, 1, false, 0, 0}, {1, 2, false, 2, 5}, {1, 2, false, 4, 5})
+LBNR_VARIANTS(3, 8, 0, {0, 1, true, 0, 0, 0}, {1, 2, false, 8, 16, 16})
+LBNR_VARIANTS(9, 8, 0, {0, 1, false, 0, 0, 0}, {1, 2, false, 8, 11, 16})
+LBNR_VARIANTS(19, 8, 0, {0, 1, false, 0, 0, 0}, {1, 2, false, 4, 5, 16})
 // FP32 storage
-LBNR_VARIANTS(3, 4, 1, {1, 2, false, 8, 16}, {0, 1, true, 0, 0})
-LBNR_VARIANTS(9, 4, 1, {1, 2, false, 8, 16}, {0, 1, true, 0, 0})
-LBNR_VARIANTS(19, 4, 2, {1, 2, false, 8, 11}, {1, 2, false, 6, 9}, {0, 2, true, 0, 0})
+LBNR_VARIANTS(3, 4, 1, {1, 2, false, 8, 16, 32}, {0, 1, true, 0, 0, 0})
+LBNR_VARIANTS(9, 4, 1, {1, 2, false, 8, 11, 32}, {0, 1, true, 0, 0, 0})
+LBNR_VARIANTS(19, 4, 2, {1, 2, false, 8, 11, 16}, {1, 2, false, 8, 5, 32}, {0, 2, true, 0, 0, 0})
 // 16-bit storage
-LBNR_VARIANTS(3, 2, 1, {1, 2, false, 8, 16}, {0, 1, true, 0, 0})
-LBNR_VARIANTS(9, 2, 1, {1, 2, false, 8, 16}, {0, 1, true, 0, 0})
-LBNR_VARIANTS(19, 2, 2, {1, 2, false, 12, 20}, {1, 2, false, 8, 16}, {0, 2, true, 0, 0})
+LBNR_VARIANTS(3, 2, 1, {1, 2, false, 8, 16, 32}, {0, 1, true, 0, 0, 0})
+LBNR_VARIANTS(9, 2, 1, {1, 2, false, 8, 16, 32}, {0, 1, true, 0, 0, 0})
+LBNR_VARIANTS(19, 2, 2, {1, 2, false, 8, 11, 32}, {1, 2, false, 8, 16, 16}, {0, 2, true, 0, 0, 0})
 #undef LBNR_VARIANTS
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no
@@ -68,18 +68,18 @@ constexpr CUtensorMapDataType tma_dtype() {
 }
 
 // 2D view of a distribution buffer: x = cell (stride 1), y = plane
-// (stride pstride); boxes of kTileCells x (planes per box).
+// (stride pstride); boxes of tile_cells x (planes per box).
 template <int Q, class S>
-cudaError_t encode_planes(const void* base, int64_t pstride, CUtensorMap* map) {
+cudaError_t encode_planes(const void* base, int64_t pstride, int tile_cells, CUtensorMap* map) {
   auto fn = tensor_map_encoder();
   if (!fn) return cudaErrorNotSupported;
   const cuuint64_t dims[2] = {(cuuint64_t)pstride, (cuuint64_t)TmaShape<Q>::kPlanes};
   const cuuint64_t strides[1] = {(cuuint64_t)pstride * sizeof(S)};
-  const cuuint32_t box[2] = {(cuuint32_t)kTileCells, (cuuint32_t)TmaShape<Q>::kPlanesPerBox};
+  const cuuint32_t box[2] = {(cuuint32_t)tile_cells, (cuuint32_t)TmaShape<Q>::kPlanesPerBox};
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, tma_dtype<S>(), 2, const_cast<void*>(base), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                  CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
@@ -119,7 +119,7 @@ struct Impl {
     if (x.kind == 0)
       snprintf(buf[v], sizeof(buf[v]), "P%d%s", x.P, x.hold ? "-hold" : "-reread");
     else
-      snprintf(buf[v], sizeof(buf[v]), "tma-nc%d-ns%d", x.nc, x.ns);
+      snprintf(buf[v], sizeof(buf[v]), "tma-nc%d-ns%d-t%d", x.nc, x.ns, x.tc);
     return buf[v];
   }
 
@@ -138,15 +138,16 @@ struct Impl {
   static cudaError_t launch_tma(const LaunchCtx& L, const StepArgs<S, C>& a) {
     constexpr VariantSpec x = VT::v[VI];
     constexpr int NC = x.nc > 0 ? x.nc : 1;
-    constexpr int NS = x.ns > 0 ? x.ns : 1;
-    constexpr uint32_t smem = tma_smem_bytes(tma_stage_bytes<S>(Q), NS);
-    auto kern = k_collide_tma<Q, S, C, REP, LAYOUT, NC, NS>;
+    constexpr int NS = x.ns > 0 ? x.ns : 2;
+    constexpr int TC = x.tc > 0 ? x.tc : 16;
+    constexpr uint32_t smem = tma_smem_bytes(tma_stage_bytes<S>(Q, TC), NS);
+    auto kern = k_collide_tma<Q, S, C, REP, LAYOUT, NC, NS, TC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     CUtensorMap map;
-    e = encode_planes<Q, S>(a.fin, L.pstride, &map);
+    e = encode_planes<Q, S>(a.fin, L.pstride, TC, &map);
     if (e != cudaSuccess) return e;
-    const int64_t ntiles = L.pstride / kTileCells;
+    const int64_t ntiles = L.pstride / TC;
     const int64_t grid = ntiles < sm_count() ? ntiles : sm_count();
     kern<<<(unsigned)grid, 32 * (NC + 1), smem, L.st>>>(a, map, ntiles);
     return cudaGetLastError();

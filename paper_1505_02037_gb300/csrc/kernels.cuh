@@ -49,16 +49,25 @@ struct Codec<double> {
   __device__ static __forceinline__ double load(const double* p) { return __ldcs(p); }
   __device__ static __forceinline__ double load_keep(const double* p) { return __ldg(p); }
   __device__ static __forceinline__ double load_coh(const double* p) { return __ldcg(p); }
-  // Plain stores: the compiler predicates them (an asm store under a
-  // condition would become a branch around every store).
-  __device__ static __forceinline__ void store(double* p, double v) { *p = v; }
+  __device__ static __forceinline__ void store(double* p, double v) { __stcs(p, v); }
+  // Store under a predicate without a branch.
+  __device__ static __forceinline__ void store_if(double* p, double v, bool q) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %2, 0;\n @p st.global.cs.f64 [%0], %1;\n}\n" ::"l"(p),
+                 "d"(v), "r"((int)q)
+                 : "memory");
+  }
 };
 template <>
 struct Codec<float> {
   __device__ static __forceinline__ float load(const float* p) { return __ldcs(p); }
   __device__ static __forceinline__ float load_keep(const float* p) { return __ldg(p); }
   __device__ static __forceinline__ float load_coh(const float* p) { return __ldcg(p); }
-  __device__ static __forceinline__ void store(float* p, float v) { *p = v; }
+  __device__ static __forceinline__ void store(float* p, float v) { __stcs(p, v); }
+  __device__ static __forceinline__ void store_if(float* p, float v, bool q) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %2, 0;\n @p st.global.cs.f32 [%0], %1;\n}\n" ::"l"(p),
+                 "f"(v), "r"((int)q)
+                 : "memory");
+  }
 };
 template <>
 struct Codec<__nv_bfloat16> {
@@ -72,7 +81,13 @@ struct Codec<__nv_bfloat16> {
     return __bfloat162float(__ldcg(p));
   }
   __device__ static __forceinline__ void store(__nv_bfloat16* p, float v) {
-    *p = __float2bfloat16_rn(v);
+    __stcs(p, __float2bfloat16_rn(v));
+  }
+  __device__ static __forceinline__ void store_if(__nv_bfloat16* p, float v, bool q) {
+    const unsigned short b = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %2, 0;\n @p st.global.cs.b16 [%0], %1;\n}\n" ::"l"(p),
+                 "h"(b), "r"((int)q)
+                 : "memory");
   }
 };
 template <>
@@ -82,7 +97,13 @@ struct Codec<__half> {
     return __half2float(__ldg(p));
   }
   __device__ static __forceinline__ float load_coh(const __half* p) { return __half2float(__ldcg(p)); }
-  __device__ static __forceinline__ void store(__half* p, float v) { *p = __float2half_rn(v); }
+  __device__ static __forceinline__ void store(__half* p, float v) { __stcs(p, __float2half_rn(v)); }
+  __device__ static __forceinline__ void store_if(__half* p, float v, bool q) {
+    const unsigned short b = __half_as_ushort(__float2half_rn(v));
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %2, 0;\n @p st.global.cs.b16 [%0], %1;\n}\n" ::"l"(p),
+                 "h"(b), "r"((int)q)
+                 : "memory");
+  }
 };
 
 // Flat-space value of field F (alpha = 1, gamma = delta, K = V = 0).
@@ -384,7 +405,12 @@ __global__ void __launch_bounds__(128) k_collide(const StepArgs<S, C> a) {
         }
       }
       const C out = REP == kDEV ? fma(a.omc, v, t) : fma(a.omc, v, C(L::w(l)) * t);
-      if (valid) Codec<S>::store(ob + write_off<Q, LAYOUT>(n, ps32, l), out);
+      // Ping-pong: lanes past the last cell were clamped to it and write the
+      // same bytes as its own lanes, so every store can be unconditional.
+      if (LAYOUT == kPingPong)
+        Codec<S>::store(ob + write_off<Q, LAYOUT>(n, ps32, l), out);
+      else
+        Codec<S>::store_if(ob + write_off<Q, LAYOUT>(n, ps32, l), out, valid);
     }
   }
 }
@@ -398,16 +424,17 @@ __global__ void __launch_bounds__(256) k_aux(const S* __restrict__ f, C* __restr
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= G.cells) return;
   const Nbr n = make_nbr(G, c);
-  const uint32_t ps32 = (uint32_t)G.pstride;
-  // One field at a time: its Q loads are in flight together, and the
-  // register count stays low enough for full occupancy.
-#pragma unroll 1
+#pragma unroll
   for (int F = 0; F < 7; ++F) {
-    const S* fb = f + field_base<Q>(F, G.pstride);
     C s = C(0);
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
-      const C v = Codec<S>::load_keep(fb + read_off<Q, LAYOUT>(n, ps32, l));
+      const int64_t idx =
+          (int64_t)(F * Q + (LAYOUT == kAAOdd ? opposite(l) : l)) * G.pstride +
+          (LAYOUT == kAAOdd ? (int64_t)n.at(-Lattice<Q>::c(l, 0), -Lattice<Q>::c(l, 1),
+                                            -Lattice<Q>::c(l, 2))
+                            : (int64_t)n.c);
+      const C v = Codec<S>::load_keep(f + idx);
       s += REP == kDEV ? C(L::w(l)) * v : v;
     }
     if (F == 0) s = REP == kDEV ? log1p(s) : log(s);

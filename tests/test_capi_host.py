@@ -40,12 +40,12 @@ def test_default_opts(lib):
 @pytest.mark.parametrize("vset,shape,storage,streaming,expect", [
     (3, (128, 128, 128), 1, 1, 2 * 16 * 19 * 4 * 128 ** 3),
     (3, (128, 128, 128), 1, 2, 16 * 19 * 4 * 128 ** 3),
-    (1, (200, 1, 1), 0, 1, 2 * 16 * 3 * 8 * 208),   # planes padded to 16 cells
+    (1, (200, 1, 1), 0, 1, 2 * 16 * 3 * 8 * 224),   # planes padded to 32 cells
     (2, (64, 48, 1), 3, 2, 16 * 9 * 2 * 64 * 48),
 ])
 def test_workspace_bytes(vset, shape, storage, streaming, expect):
     """The workspace holds the distribution buffer(s) (planes padded to a
-    multiple of 16 cells for the tensor copies) plus the stencil planes, the
+    multiple of 32 cells for the tensor copies) plus the stencil planes, the
     FP64 field planes and the reduction scratch."""
     from paper_1505_02037_gb300 import lbnr
     o = lbnr.lbnr_default_opts()
