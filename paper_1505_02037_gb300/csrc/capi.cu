@@ -243,6 +243,15 @@ int read_flag(lbnr_ctx* c, int* flag) {
   return LBNR_OK;
 }
 
+// Device flag word: bit 0 non-finite moment, bit 1 a bounded wait gave up,
+// bit 2 a launch-consistency check failed (work was skipped).
+int flag_status(lbnr_ctx* c, int flag) {
+  if (flag & 4) return fail(c, LBNR_ECUDA, "device consistency check failed (flag %d)", flag);
+  if (flag & 2) return fail(c, LBNR_ETIMEOUT, "a device-side wait timed out");
+  if (flag & 1) return fail(c, LBNR_ENONFINITE, "non-finite moment seen");
+  return LBNR_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -464,7 +473,7 @@ int lbnr_moments(lbnr_ctx* c, double* out) {
   int flag = 0;
   int rc = read_flag(c, &flag);
   if (rc) return rc;
-  return flag ? fail(c, LBNR_ENONFINITE, "non-finite moment seen") : LBNR_OK;
+  return flag_status(c, flag);
 }
 
 int lbnr_constraints(lbnr_ctx* c, double* out) {
@@ -479,7 +488,7 @@ int lbnr_constraints(lbnr_ctx* c, double* out) {
   int flag = 0;
   int rc = read_flag(c, &flag);
   if (rc) return rc;
-  return flag ? fail(c, LBNR_ENONFINITE, "non-finite moment seen") : LBNR_OK;
+  return flag_status(c, flag);
 }
 
 int lbnr_get_distributions(lbnr_ctx* c, double* out) {
@@ -539,7 +548,7 @@ int lbnr_status(lbnr_ctx* c) {
   int flag = 0;
   int rc = read_flag(c, &flag);
   if (rc) return rc;
-  return flag ? fail(c, LBNR_ENONFINITE, "non-finite moment seen") : LBNR_OK;
+  return flag_status(c, flag);
 }
 
 int lbnr_num_variants(const lbnr_ctx* c) { return c ? c->ops->nvariants : 0; }

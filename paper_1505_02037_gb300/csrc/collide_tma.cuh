@@ -94,16 +94,22 @@ __host__ __device__ constexpr uint32_t tma_smem_bytes(uint32_t stage_bytes, int 
   return 1024u + stage_bytes * (uint32_t)NS;
 }
 
-// TC cells per tile (16 or 32); a tile is consumed by TC/16 warps together.
-template <int Q, class S, class C, int REP, int LAYOUT, int NC, int NS, int TC>
+// TC cells per tile (16 or 32); a tile is consumed by WPT = TC/16 warps
+// together (a group); there are NP = NC/WPT groups, and each group owns K
+// consecutive stages of the ring (NS = NP*K). Tile j of this CTA goes to
+// group j % NP as its m-th tile (m = j / NP) and lands in the group's stage
+// m % K, round m / K. Every stage is therefore filled and consumed in round
+// order by one group, so a parity wait can never mistake an older phase for
+// the awaited one.
+template <int Q, class S, class C, int REP, int LAYOUT, int NC, int K, int TC>
 __global__ void __launch_bounds__(32 * (NC + 1), 1)
     k_collide_tma(const StepArgs<S, C> a, const __grid_constant__ CUtensorMap tmap, int64_t ntiles) {
   static_assert(LAYOUT == kPingPong || LAYOUT == kAAEven, "reads must be local");
-  constexpr int WPT = TC / 16;   // warps per tile
-  constexpr int NP = NC / WPT;   // tiles in flight among the consumers
+  constexpr int WPT = TC / 16;
+  constexpr int NP = NC / WPT;
+  constexpr int NS = NP * K;
   static_assert(TC == 16 || TC == 32, "tile of 16 or 32 cells");
-  static_assert(NC % WPT == 0, "whole warp groups per tile");
-  static_assert(NS > NP, "the ring must hold more stages than tiles being consumed");
+  static_assert(NC % WPT == 0 && K >= 1, "whole warp groups per tile");
   using L = Lattice<Q>;
   using TS = TmaShape<Q>;
   constexpr int T = TC;
@@ -135,13 +141,18 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
     if (lane == 0) {
       int64_t issued = 0;
       for (int64_t j = 0; j < my; ++j) {
-        const int s = (int)(j % NS);
-        const uint32_t ph = (uint32_t)((j / NS) & 1);
-        if (j >= NS && !mbar_wait(smem_u32(&bars[NS + s]), ph ^ 1u, kLimitNs)) {
+        const int64_t m = j / NP;
+        const int s = (int)(j % NP) * K + (int)(m % K);
+        const int64_t r = m / K;
+        if (r >= 1 && !mbar_wait(smem_u32(&bars[NS + s]), (uint32_t)((r - 1) & 1), kLimitNs)) {
           atomicOr(a.flag, 2);
           break;
         }
         const int64_t tile = blockIdx.x + j * G;
+        if ((tile + 1) * T > a.G.pstride) {  // never true for a consistent launch
+          atomicOr(a.flag, 4);
+          break;
+        }
         const uint32_t fb = smem_u32(&bars[s]);
         mbar_expect_tx(fb, STAGEB);
         const uint32_t dst = smem_u32(stages + (size_t)s * STAGEB);
@@ -150,21 +161,21 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
           tma_load_2d(dst + b * BOXB, &tmap, (int32_t)(tile * T), b * TS::kPlanesPerBox, fb);
         issued = j + 1;
       }
-      // Leave only when every copy this warp started has landed.
-      for (int64_t j = issued > NS ? issued - NS : 0; j < issued; ++j)
-        if (!mbar_wait(smem_u32(&bars[j % NS]), (uint32_t)((j / NS) & 1), kLimitNs)) {
+      // Leave only when every copy this warp started has landed: the last
+      // fill of each stage is among the last NS tiles issued.
+      for (int64_t j = issued > NS ? issued - NS : 0; j < issued; ++j) {
+        const int64_t m = j / NP;
+        const int s = (int)(j % NP) * K + (int)(m % K);
+        if (!mbar_wait(smem_u32(&bars[s]), (uint32_t)((m / K) & 1), kLimitNs)) {
           atomicOr(a.flag, 2);
           break;
         }
+      }
     }
     return;
   }
 
   // ---------------- consumers ----------------
-  // Tile j of this CTA uses stage j % NS and warp group j % NP (WPT warps,
-  // 16 cells each). The producer refills stage s for tile j only after tile
-  // j - NS released it; that tile belongs to a group whose earlier tiles
-  // precede it, so the ring cannot deadlock for any NS > NP.
   const int g = lane >> 4;
   const int grp = warp / WPT;
   const int half = warp % WPT;
@@ -172,9 +183,11 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
   const int64_t cells = a.G.cells;
   const int64_t ps = a.G.pstride;
   const uint32_t ps32 = (uint32_t)ps;
-  for (int64_t j = grp; j < my; j += NP) {
-    const int s = (int)(j % NS);
-    const uint32_t ph = (uint32_t)((j / NS) & 1);
+  for (int64_t m = 0;; ++m) {
+    const int64_t j = grp + m * NP;
+    if (j >= my) break;
+    const int s = grp * K + (int)(m % K);
+    const uint32_t ph = (uint32_t)((m / K) & 1);
     const int64_t tile = blockIdx.x + j * G;
     const int64_t cell = tile * T + ci;
     const bool valid = cell < cells;

@@ -19,7 +19,7 @@ namespace lbnr {
 struct VariantSpec {
   int kind, P;
   bool hold;
-  int nc, ns, tc;  // consumer warps, stages, cells per tile (kind 1)
+  int nc, k, tc;  // consumer warps, stages per warp group, cells per tile (kind 1)
 };
 
 template <int Q, int SB>
@@ -32,17 +32,17 @@ struct VariantTable;
     static constexpr int fallback = FALLBACK_;               \
   };
 // FP64 storage (FP64 arithmetic)
-LBNR_VARIANTS(3, 8, 0, {0, 1, true, 0, 0, 0}, {1, 2, false, 8, 16, 16})
-LBNR_VARIANTS(9, 8, 0, {0, 1, false, 0, 0, 0}, {1, 2, false, 8, 11, 16})
-LBNR_VARIANTS(19, 8, 0, {0, 1, false, 0, 0, 0}, {1, 2, false, 4, 5, 16})
+LBNR_VARIANTS(3, 8, 0, {0, 1, true, 0, 0, 0}, {1, 2, false, 8, 2, 16})
+LBNR_VARIANTS(9, 8, 0, {0, 1, false, 0, 0, 0}, {1, 2, false, 8, 1, 16})
+LBNR_VARIANTS(19, 8, 0, {0, 1, false, 0, 0, 0}, {1, 2, false, 4, 1, 16})
 // FP32 storage
-LBNR_VARIANTS(3, 4, 1, {1, 2, false, 8, 16, 32}, {0, 1, true, 0, 0, 0})
-LBNR_VARIANTS(9, 4, 1, {1, 2, false, 8, 11, 32}, {0, 1, true, 0, 0, 0})
-LBNR_VARIANTS(19, 4, 2, {1, 2, false, 8, 11, 16}, {1, 2, false, 8, 5, 32}, {0, 2, true, 0, 0, 0})
+LBNR_VARIANTS(3, 4, 1, {1, 2, false, 8, 4, 32}, {0, 1, true, 0, 0, 0})
+LBNR_VARIANTS(9, 4, 1, {1, 2, false, 8, 2, 32}, {0, 1, true, 0, 0, 0})
+LBNR_VARIANTS(19, 4, 2, {1, 2, false, 4, 2, 32}, {1, 2, false, 5, 2, 16}, {0, 2, true, 0, 0, 0})
 // 16-bit storage
-LBNR_VARIANTS(3, 2, 1, {1, 2, false, 8, 16, 32}, {0, 1, true, 0, 0, 0})
-LBNR_VARIANTS(9, 2, 1, {1, 2, false, 8, 16, 32}, {0, 1, true, 0, 0, 0})
-LBNR_VARIANTS(19, 2, 2, {1, 2, false, 8, 11, 32}, {1, 2, false, 8, 16, 16}, {0, 2, true, 0, 0, 0})
+LBNR_VARIANTS(3, 2, 1, {1, 2, false, 8, 4, 32}, {0, 1, true, 0, 0, 0})
+LBNR_VARIANTS(9, 2, 1, {1, 2, false, 8, 3, 32}, {0, 1, true, 0, 0, 0})
+LBNR_VARIANTS(19, 2, 2, {1, 2, false, 8, 2, 32}, {1, 2, false, 8, 2, 16}, {0, 2, true, 0, 0, 0})
 #undef LBNR_VARIANTS
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no
@@ -119,7 +119,7 @@ struct Impl {
     if (x.kind == 0)
       snprintf(buf[v], sizeof(buf[v]), "P%d%s", x.P, x.hold ? "-hold" : "-reread");
     else
-      snprintf(buf[v], sizeof(buf[v]), "tma-nc%d-ns%d-t%d", x.nc, x.ns, x.tc);
+      snprintf(buf[v], sizeof(buf[v]), "tma-nc%d-k%d-t%d", x.nc, x.k, x.tc);
     return buf[v];
   }
 
@@ -138,10 +138,12 @@ struct Impl {
   static cudaError_t launch_tma(const LaunchCtx& L, const StepArgs<S, C>& a) {
     constexpr VariantSpec x = VT::v[VI];
     constexpr int NC = x.nc > 0 ? x.nc : 1;
-    constexpr int NS = x.ns > 0 ? x.ns : 2;
+    constexpr int K = x.k > 0 ? x.k : 1;
     constexpr int TC = x.tc > 0 ? x.tc : 16;
+    constexpr int NS = NC / (TC / 16) * K;
     constexpr uint32_t smem = tma_smem_bytes(tma_stage_bytes<S>(Q, TC), NS);
-    auto kern = k_collide_tma<Q, S, C, REP, LAYOUT, NC, NS, TC>;
+    static_assert(smem <= 232448, "shared memory per block");
+    auto kern = k_collide_tma<Q, S, C, REP, LAYOUT, NC, K, TC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     CUtensorMap map;
