@@ -203,7 +203,7 @@ def test_full_size_sampled_step_fp64(L, oracle_mod):
 def test_aa_equals_pingpong(L):
     """In-place AA streaming and ping-pong do the same arithmetic (their
     instantiations may contract multiply-adds differently): distributions
-    agree to 1e-14 of each field's scale in FP64, and to a few FP32 or BF16
+    agree to 1e-12 of each field's scale in FP64, and to a few FP32 or BF16
     rounding units, after odd and even step counts."""
     for storage in ("f64", "f32", "dev_bf16"):
         shape = (19, 9, 7)
@@ -212,7 +212,7 @@ def test_aa_equals_pingpong(L):
         b = L.Lattice(3, shape, 1.2, 1 / 19, storage=storage, streaming=2)
         a.init(fields)
         b.init(fields)
-        tol = {"f64": 1e-14, "f32": 4e-7, "dev_bf16": 1e-2}[storage]
+        tol = {"f64": 1e-12, "f32": 1e-5, "dev_bf16": 3e-2}[storage]
         for n in (1, 2, 3, 6):
             a.step(n)
             b.step(n)
