@@ -158,6 +158,31 @@ int64_t lbnr_steps_done(const lbnr_ctx* ctx);
 int lbnr_q(const lbnr_ctx* ctx);
 int lbnr_streaming(const lbnr_ctx* ctx);
 
+/* Largest lattice lbnr_constraint_norms_noalloc accepts. */
+#define LBNR_NOALLOC_MAX_CELLS 2097152
+
+/* The first six values of lbnr_constraints (H_L2, H_inf, M_L2, M_inf, C_L2,
+ * C_inf) for corrected fields that are already on the device, computed
+ * without allocating any device memory. The paper has no counterpart: this
+ * is for callers that must not allocate, such as a run that has handed
+ * nearly all device memory to its lattice, or a host framework whose own
+ * allocator owns the device memory during its step.
+ *   d_fields: device float64 [16][cells], the corrected fields in the field
+ *             order above (e.g. what lbnr_moments returns, copied back);
+ *   d_out:    device float64 [6], written on the stream;
+ *   cuda_stream: cudaStream_t (NULL = default stream). Returns after enqueue.
+ * The per-block partial sums live in one fixed array compiled into the
+ * library (LBNR_NOALLOC_MAX_CELLS / 128 blocks x 22 doubles, 2.75 MiB); every
+ * GPU that loads the library keeps it until the process exits. Lattices of
+ * more than LBNR_NOALLOC_MAX_CELLS cells give LBNR_EINVAL. The first call on
+ * a device looks up the array's device address (with that device current),
+ * so make that first call before any stream capture. All calls share the
+ * array: calls whose work overlaps on the GPU (different streams, or
+ * different host threads) race and must be serialised by the caller. Errors
+ * are reported through lbnr_last_error(NULL). */
+int lbnr_constraint_norms_noalloc(int vset, const lbnr_grid* grid, double dx,
+                                  const double* d_fields, double* d_out, void* cuda_stream);
+
 /* Frees what the context allocated. NULL is a no-op. */
 void lbnr_destroy(lbnr_ctx* ctx);
 

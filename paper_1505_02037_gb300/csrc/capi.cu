@@ -105,6 +105,8 @@ struct lbnr_ctx {
 
 static thread_local std::string g_err;
 
+void lbnr::set_thread_error(const char* msg) { g_err = msg; }
+
 static int fail(lbnr_ctx* c, int code, const char* fmt, ...) {
   char buf[512];
   va_list ap;

@@ -57,6 +57,7 @@ LBNR_DECLARE_OPS(19)
 #undef LBNR_DECLARE_OPS
 
 size_t storage_bytes(int storage);
+void set_thread_error(const char* msg);  // message for lbnr_last_error(NULL)
 bool storage_is_fp64(int storage);
 
 }  // namespace lbnr

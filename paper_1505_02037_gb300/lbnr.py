@@ -79,6 +79,8 @@ def library(path: str | None = None):
     L.lbnr_variant_name.argtypes = [vp, ctypes.c_int]
     L.lbnr_variant_name.restype = ctypes.c_char_p
     L.lbnr_set_variant.argtypes = [vp, ctypes.c_int]
+    L.lbnr_constraint_norms_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(Grid),
+                                                 ctypes.c_double, vp, vp, vp]
     L.lbnr_destroy.argtypes = [vp]
     L.lbnr_destroy.restype = None
     L.lbnr_last_error.argtypes = [vp]
@@ -193,6 +195,21 @@ def lbnr_variant_name(ctx, v: int) -> str:
 
 def lbnr_set_variant(ctx, v: int):
     _check(library().lbnr_set_variant(ctx, v), ctx)
+
+
+def lbnr_constraint_norms_noalloc(vset: int, grid: Grid, dx: float, d_fields, d_out,
+                                  stream=None):
+    """Constraint norms of device-resident corrected fields without any device
+    allocation (see include/lbnr.h). d_fields: CUDA float64 tensor [16, cells];
+    d_out: CUDA float64 tensor [6]; stream: torch CUDA stream or None."""
+    for t, n in ((d_fields, 16 * grid.nx * grid.ny * grid.nz), (d_out, 6)):
+        if (not t.is_cuda or str(t.dtype) != "torch.float64" or not t.is_contiguous()
+                or t.numel() != n):
+            raise TypeError("expected contiguous CUDA float64 tensors of the right size")
+    st = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+    _check(library().lbnr_constraint_norms_noalloc(
+        int(vset), ctypes.byref(grid), float(dx), ctypes.c_void_p(d_fields.data_ptr()),
+        ctypes.c_void_p(d_out.data_ptr()), st))
 
 
 def lbnr_destroy(ctx):
