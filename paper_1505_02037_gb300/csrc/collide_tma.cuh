@@ -94,21 +94,27 @@ __host__ __device__ constexpr uint32_t tma_smem_bytes(uint32_t stage_bytes, int 
   return 1024u + stage_bytes * (uint32_t)NS;
 }
 
-// TC cells per tile (16 or 32); a tile is consumed by WPT = TC/16 warps
-// together (a group); there are NP = NC/WPT groups, and each group owns K
+// TC cells per tile (16 or 32); P lanes per cell (P = 2: each lane owns 8
+// fields and partner lanes swap moments; P = 1: one lane per cell, all 16
+// fields). A tile is consumed by WPT = TC / (32/P) warps together (a group);
+// there are NP = NC/WPT groups, and each group owns K
 // consecutive stages of the ring (NS = NP*K). Tile j of this CTA goes to
 // group j % NP as its m-th tile (m = j / NP) and lands in the group's stage
 // m % K, round m / K. Every stage is therefore filled and consumed in round
 // order by one group, so a parity wait can never mistake an older phase for
 // the awaited one.
-template <int Q, class S, class C, int REP, int LAYOUT, int NC, int K, int TC>
+template <int Q, class S, class C, int REP, int LAYOUT, int NC, int K, int TC, int P>
 __global__ void __launch_bounds__(32 * (NC + 1), 1)
     k_collide_tma(const StepArgs<S, C> a, const __grid_constant__ CUtensorMap tmap, int64_t ntiles) {
   static_assert(LAYOUT == kPingPong || LAYOUT == kAAEven, "reads must be local");
-  constexpr int WPT = TC / 16;
+  static_assert(P == 1 || P == 2, "one or two lanes per cell");
+  constexpr int CPW = 32 / P;    // cells per consumer warp
+  constexpr int NJ = kNF / P;    // fields per lane
+  constexpr int WPT = TC / CPW;  // warps per tile
   constexpr int NP = NC / WPT;
   constexpr int NS = NP * K;
   static_assert(TC == 16 || TC == 32, "tile of 16 or 32 cells");
+  static_assert(TC % CPW == 0, "a tile holds whole warps of cells");
   static_assert(NC % WPT == 0 && K >= 1, "whole warp groups per tile");
   using L = Lattice<Q>;
   using TS = TmaShape<Q>;
@@ -176,10 +182,10 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
   }
 
   // ---------------- consumers ----------------
-  const int g = lane >> 4;
+  const int g = P == 2 ? (lane >> 4) : 0;
   const int grp = warp / WPT;
   const int half = warp % WPT;
-  const int ci = half * 16 + (lane & 15);
+  const int ci = half * CPW + (P == 2 ? (lane & 15) : lane);
   const int64_t cells = a.G.cells;
   const int64_t ps = a.G.pstride;
   const uint32_t ps32 = (uint32_t)ps;
@@ -206,11 +212,11 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
     }
     const S* st = reinterpret_cast<const S*>(stages + (size_t)s * STAGEB);
 
-    // moments of this lane's 8 fields
-    C mine[8];
+    // moments of this lane's fields
+    C mine[NJ];
 #pragma unroll
-    for (int jj = 0; jj < 8; ++jj) {
-      const int F = g ? field_of(2, 1, jj) : field_of(2, 0, jj);
+    for (int jj = 0; jj < NJ; ++jj) {
+      const int F = g ? field_of(P, 1, jj) : field_of(P, 0, jj);
       const S* row = st + (F * Q) * T + ci;
       C sum = C(0);
 #pragma unroll
@@ -222,10 +228,14 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
     }
     C rt[kNF];
 #pragma unroll
-    for (int jj = 0; jj < 8; ++jj) {
-      const C other = __shfl_xor_sync(0xffffffffu, mine[jj], 16);
-      rt[field_of(2, 0, jj)] = g ? other : mine[jj];
-      rt[field_of(2, 1, jj)] = g ? mine[jj] : other;
+    for (int jj = 0; jj < NJ; ++jj) {
+      if (P == 1) {
+        rt[jj] = mine[jj];
+      } else {
+        const C other = __shfl_xor_sync(0xffffffffu, mine[jj], 16);
+        rt[field_of(P, 0, jj)] = g ? other : mine[jj];
+        rt[field_of(P, 1, jj)] = g ? mine[jj] : other;
+      }
     }
     {
       C chk = C(0);
@@ -254,8 +264,8 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
     const C three_omega = C(3) * a.omega;
 
 #pragma unroll
-    for (int jj = 0; jj < 8; ++jj) {
-      const int F0 = field_of(2, 0, jj), F1 = field_of(2, 1, jj);
+    for (int jj = 0; jj < NJ; ++jj) {
+      const int F0 = field_of(P, 0, jj), F1 = field_of(P, 1, jj);
       const int F = g ? F1 : F0;
       const C cf = a.omega * (g ? rho[F1] : rho[F0]) + a.sigma * (g ? Sr[F1] : Sr[F0]);
       C b[3] = {C(0), C(0), C(0)};

@@ -32,17 +32,19 @@ struct VariantTable;
     static constexpr int fallback = FALLBACK_;               \
   };
 // FP64 storage (FP64 arithmetic)
-LBNR_VARIANTS(3, 8, 0, {0, 1, true, 0, 0, 0}, {1, 2, false, 8, 2, 16})
-LBNR_VARIANTS(9, 8, 0, {0, 1, false, 0, 0, 0}, {1, 2, false, 8, 1, 16})
-LBNR_VARIANTS(19, 8, 0, {0, 1, false, 0, 0, 0}, {1, 2, false, 4, 1, 16})
+LBNR_VARIANTS(3, 8, 0, {0, 1, true, 0, 0, 0}, {1, 1, false, 8, 1, 32})
+LBNR_VARIANTS(9, 8, 0, {0, 1, false, 0, 0, 0}, {1, 1, false, 4, 1, 32})
+LBNR_VARIANTS(19, 8, 0, {0, 1, false, 0, 0, 0}, {1, 1, false, 2, 1, 32})
 // FP32 storage
-LBNR_VARIANTS(3, 4, 1, {1, 2, false, 8, 4, 32}, {0, 1, true, 0, 0, 0})
-LBNR_VARIANTS(9, 4, 1, {1, 2, false, 8, 2, 32}, {0, 1, true, 0, 0, 0})
-LBNR_VARIANTS(19, 4, 2, {1, 2, false, 4, 2, 32}, {1, 2, false, 5, 2, 16}, {0, 2, true, 0, 0, 0})
+LBNR_VARIANTS(3, 4, 2, {1, 1, false, 8, 4, 32}, {1, 2, false, 8, 4, 32}, {0, 1, true, 0, 0, 0})
+LBNR_VARIANTS(9, 4, 2, {1, 1, false, 4, 2, 32}, {1, 2, false, 8, 2, 32}, {0, 1, true, 0, 0, 0})
+LBNR_VARIANTS(19, 4, 4, {1, 1, false, 4, 1, 32}, {1, 1, false, 2, 2, 32},
+              {1, 2, false, 4, 2, 32}, {1, 1, false, 5, 1, 32}, {0, 2, true, 0, 0, 0})
 // 16-bit storage
-LBNR_VARIANTS(3, 2, 1, {1, 2, false, 8, 4, 32}, {0, 1, true, 0, 0, 0})
-LBNR_VARIANTS(9, 2, 1, {1, 2, false, 8, 3, 32}, {0, 1, true, 0, 0, 0})
-LBNR_VARIANTS(19, 2, 2, {1, 2, false, 8, 2, 32}, {1, 2, false, 8, 2, 16}, {0, 2, true, 0, 0, 0})
+LBNR_VARIANTS(3, 2, 2, {1, 1, false, 8, 4, 32}, {1, 2, false, 8, 4, 32}, {0, 1, true, 0, 0, 0})
+LBNR_VARIANTS(9, 2, 2, {1, 1, false, 8, 2, 32}, {1, 2, false, 8, 3, 32}, {0, 1, true, 0, 0, 0})
+LBNR_VARIANTS(19, 2, 3, {1, 1, false, 8, 1, 32}, {1, 1, false, 4, 2, 32},
+              {1, 2, false, 8, 2, 32}, {0, 2, true, 0, 0, 0})
 #undef LBNR_VARIANTS
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no
@@ -113,13 +115,13 @@ struct Impl {
   using VT = VariantTable<Q, (int)sizeof(S)>;
 
   static const char* variant_name(int v) {
-    static char buf[8][40];
+    static char buf[8][48];
     if (v < 0 || v >= VT::n || v >= 8) return "?";
     const VariantSpec& x = VT::v[v];
     if (x.kind == 0)
       snprintf(buf[v], sizeof(buf[v]), "P%d%s", x.P, x.hold ? "-hold" : "-reread");
     else
-      snprintf(buf[v], sizeof(buf[v]), "tma-nc%d-k%d-t%d", x.nc, x.k, x.tc);
+      snprintf(buf[v], sizeof(buf[v]), "tma-p%d-nc%d-k%d-t%d", x.P, x.nc, x.k, x.tc);
     return buf[v];
   }
 
@@ -140,10 +142,11 @@ struct Impl {
     constexpr int NC = x.nc > 0 ? x.nc : 1;
     constexpr int K = x.k > 0 ? x.k : 1;
     constexpr int TC = x.tc > 0 ? x.tc : 16;
-    constexpr int NS = NC / (TC / 16) * K;
+    constexpr int P = x.P;
+    constexpr int NS = NC / (TC / (32 / P)) * K;
     constexpr uint32_t smem = tma_smem_bytes(tma_stage_bytes<S>(Q, TC), NS);
     static_assert(smem <= 232448, "shared memory per block");
-    auto kern = k_collide_tma<Q, S, C, REP, LAYOUT, NC, K, TC>;
+    auto kern = k_collide_tma<Q, S, C, REP, LAYOUT, NC, K, TC, P>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     CUtensorMap map;
@@ -169,6 +172,12 @@ struct Impl {
 
   template <int LAYOUT>
   static cudaError_t collide_layout(const LaunchCtx& L, int variant, const StepArgs<S, C>& a) {
+    if constexpr (VT::n > 4) {
+      if (variant == 4) return launch_variant<LAYOUT, 4>(L, a);
+    }
+    if constexpr (VT::n > 3) {
+      if (variant == 3) return launch_variant<LAYOUT, 3>(L, a);
+    }
     if constexpr (VT::n > 2) {
       if (variant == 2) return launch_variant<LAYOUT, 2>(L, a);
     }
