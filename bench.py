@@ -166,6 +166,18 @@ def cpu_baseline(vset, storage, direction, A, tau, seconds=12.0):
                       f"{steps} steps in {el:.1f} s on {cores} host threads"}
 
 
+def workload_config(args, streaming_name="ping-pong"):
+    vset, N, storage, direction, A = WORKLOADS[args.workload]
+    return {
+        "workload": f"3D gauge wave along {direction}, D3Q19 {N}^3 periodic, "
+                    f"{storage} storage, A={A}, tau={args.tau}, {streaming_name} streaming",
+        "workload_key": args.workload, "cells": N ** 3, "fields": 16, "velocities": 19,
+        "tau_note": "tau=0.6 of the configuration is linearly unstable for this scheme "
+                    "(blows up near step 100 at any N and A); cost per step does not "
+                    "depend on tau",
+    }
+
+
 def run_reference(args):
     """Reference arm: the FP64 oracle timed on the host cores, each step a
     bounded sample (one oracle step on a 24^3 piece of the workload)."""
@@ -191,7 +203,7 @@ def run_reference(args):
             "unit": "Mcell*var/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload, "tau": args.tau},
+            "data": "synthetic", "config": workload_config(args),
             "cpu_baseline": {"value": value, "unit": "Mcell*var/s", "cores": cores,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "Mcell*var/s", "h2d_bytes_per_step": 0,
@@ -274,18 +286,11 @@ def main():
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPE[storage], "data": "synthetic",
-        "config": {
-            "workload": f"3D gauge wave along {direction}, D3Q19 {N}^3 periodic, "
-                        f"{storage} storage, A={A}, tau={args.tau}, "
-                        f"{'ping-pong' if lat.streaming == 1 else 'AA in-place'} streaming",
-            "workload_key": args.workload, "cells": cells, "fields": 16, "velocities": Q,
-            "tau_note": "tau=0.6 of the configuration is linearly unstable for this scheme "
-                        "(blows up near step 100 at any N and A); cost per step does not "
-                        "depend on tau",
-            "l2": f"inputs larger than L2 ({lat.workspace.numel() / 1e9:.1f} GB working set)",
-            "state_finite_after_run": finite,
-            "parallelism": "replicas" if world > 1 else "single GPU",
-        },
+        "config": dict(
+            workload_config(args, "ping-pong" if lat.streaming == 1 else "AA in-place"),
+            l2=f"inputs larger than L2 ({lat.workspace.numel() / 1e9:.1f} GB working set)",
+            state_finite_after_run=finite,
+            parallelism="replicas" if world > 1 else "single GPU"),
         "roofline": {"bound": "hbm", "kernel": "k_collide (fused collide-and-stream)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": f"hbm_gbs of {peak_kind}",
@@ -296,7 +301,7 @@ def main():
         "step_algorithmic_hbm_frac": (alg_collide + alg_aux) / (ms_max / args.steps * 1e-3)
                                      / 1e9 / peak,
         "gpu_launches": 2 * args.steps,
-        "launch_form": lat.variants[lat.variant] if hasattr(lat, "variant") else None,
+        "launch_form": lat.variants[lat.variant],
         "autotune_ms_per_collide": tuning,
         "clocks": clk.summary(),
     }
