@@ -287,7 +287,7 @@ __device__ __forceinline__ void unpack(const C m[kNF], C& alpha, C g[6], C K[6],
 // k_collide: the fused step
 // ---------------------------------------------------------------------------
 template <int Q, class S, class C, int REP, int LAYOUT, int P, bool HOLD>
-__global__ void __launch_bounds__(128) k_collide(const StepArgs<S, C> a) {
+__global__ void __launch_bounds__(128, HOLD ? 1 : 3) k_collide(const StepArgs<S, C> a) {
   using L = Lattice<Q>;
   constexpr int NJ = kNF / P;
   constexpr int dim = L::kDim;
@@ -390,8 +390,9 @@ __global__ void __launch_bounds__(128) k_collide(const StepArgs<S, C> a) {
     for (int l = 0; l < Q; ++l) {
       const S* src = LAYOUT == kAAOdd ? fb + read_off<Q, LAYOUT>(n, ps32, l)
                                       : fbc + (size_t)((uint32_t)l * ps32);
+      // the second read is the last use: streaming (evict-first) load
       v_[l] = HOLD ? fv[HOLD ? j : 0][HOLD ? l : 0]
-              : LAYOUT == kPingPong ? Codec<S>::load_keep(src) : Codec<S>::load_coh(src);
+              : LAYOUT == kPingPong ? Codec<S>::load(src) : Codec<S>::load_coh(src);
     }
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
