@@ -78,14 +78,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-// Pulls a tile into L2 ahead of its shared-memory load (no completion to wait for).
-__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int32_t x, int32_t y) {
-  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
-                   reinterpret_cast<uint64_t>(map)),
-               "r"(x), "r"(y)
-               : "memory");
-}
-
 template <int Q>
 struct TmaShape {
   static constexpr int kPlanes = kNF * Q;
@@ -111,9 +103,7 @@ __host__ __device__ constexpr uint32_t tma_smem_bytes(uint32_t stage_bytes, int 
 // m % K, round m / K. Every stage is therefore filled and consumed in round
 // order by one group, so a parity wait can never mistake an older phase for
 // the awaited one.
-// PFD > 0: the producer also asks for tile j + PFD to be pulled into L2 when
-// it loads tile j, so later tensor copies hit L2 and stages turn over sooner.
-template <int Q, class S, class C, int REP, int LAYOUT, int NC, int K, int TC, int P, int PFD>
+template <int Q, class S, class C, int REP, int LAYOUT, int NC, int K, int TC, int P>
 __global__ void __launch_bounds__(32 * (NC + 1), 1)
     k_collide_tma(const StepArgs<S, C> a, const __grid_constant__ CUtensorMap tmap, int64_t ntiles) {
   static_assert(LAYOUT == kPingPong || LAYOUT == kAAEven, "reads must be local");
@@ -168,19 +158,6 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
         if ((tile + 1) * T > a.G.pstride) {  // never true for a consistent launch
           atomicOr(a.flag, 4);
           break;
-        }
-        if (PFD > 0) {
-          if (j == 0) {
-            for (int64_t q = 1; q < PFD && q < my; ++q)
-#pragma unroll
-              for (int b = 0; b < TS::kBoxes; ++b)
-                tma_prefetch_2d(&tmap, (int32_t)((blockIdx.x + q * G) * T), b * TS::kPlanesPerBox);
-          }
-          if (j + PFD < my)
-#pragma unroll
-            for (int b = 0; b < TS::kBoxes; ++b)
-              tma_prefetch_2d(&tmap, (int32_t)((blockIdx.x + (j + PFD) * G) * T),
-                              b * TS::kPlanesPerBox);
         }
         const uint32_t fb = smem_u32(&bars[s]);
         mbar_expect_tx(fb, STAGEB);

@@ -20,7 +20,6 @@ struct VariantSpec {
   int kind, P;
   bool hold;
   int nc, k, tc;  // consumer warps, stages per warp group, cells per tile (kind 1)
-  int pf;         // kind 0: L2 prefetch of the cell's values; kind 1: prefetch distance (tiles)
 };
 
 template <int Q, int SB>
@@ -33,24 +32,19 @@ struct VariantTable;
     static constexpr int fallback = FALLBACK_;               \
   };
 // FP64 storage (FP64 arithmetic)
-LBNR_VARIANTS(3, 8, 0, {0, 1, true, 0, 0, 0, 0}, {1, 1, false, 8, 1, 32, 0})
-LBNR_VARIANTS(9, 8, 0, {0, 1, false, 0, 0, 0, 0}, {1, 1, false, 4, 1, 32, 0})
-LBNR_VARIANTS(19, 8, 0, {0, 1, false, 0, 0, 0, 0}, {0, 1, false, 0, 0, 0, 1},
-              {1, 1, false, 2, 1, 32, 4})
+LBNR_VARIANTS(3, 8, 0, {0, 1, true, 0, 0, 0}, {1, 1, false, 8, 1, 32})
+LBNR_VARIANTS(9, 8, 0, {0, 1, false, 0, 0, 0}, {1, 1, false, 4, 1, 32})
+LBNR_VARIANTS(19, 8, 0, {0, 1, false, 0, 0, 0}, {1, 1, false, 2, 1, 32})
 // FP32 storage
-LBNR_VARIANTS(3, 4, 2, {1, 1, false, 8, 4, 32, 0}, {1, 2, false, 8, 4, 32, 0},
-              {0, 1, true, 0, 0, 0, 0})
-LBNR_VARIANTS(9, 4, 2, {1, 1, false, 4, 2, 32, 8}, {1, 2, false, 8, 2, 32, 8},
-              {0, 1, true, 0, 0, 0, 0})
-LBNR_VARIANTS(19, 4, 4, {1, 1, false, 5, 1, 32, 10}, {1, 1, false, 4, 1, 32, 8},
-              {0, 1, false, 0, 0, 0, 1}, {0, 2, false, 0, 0, 0, 1}, {0, 2, true, 0, 0, 0, 1})
+LBNR_VARIANTS(3, 4, 2, {1, 1, false, 8, 4, 32}, {1, 2, false, 8, 4, 32}, {0, 1, true, 0, 0, 0})
+LBNR_VARIANTS(9, 4, 2, {1, 1, false, 4, 2, 32}, {1, 2, false, 8, 2, 32}, {0, 1, true, 0, 0, 0})
+LBNR_VARIANTS(19, 4, 4, {1, 1, false, 4, 1, 32}, {1, 1, false, 5, 1, 32},
+              {0, 1, false, 0, 0, 0}, {0, 2, false, 0, 0, 0}, {0, 2, true, 0, 0, 0})
 // 16-bit storage
-LBNR_VARIANTS(3, 2, 2, {1, 1, false, 8, 4, 32, 0}, {1, 2, false, 8, 4, 32, 0},
-              {0, 1, true, 0, 0, 0, 0})
-LBNR_VARIANTS(9, 2, 2, {1, 1, false, 8, 2, 32, 8}, {1, 2, false, 8, 3, 32, 8},
-              {0, 1, true, 0, 0, 0, 0})
-LBNR_VARIANTS(19, 2, 4, {1, 2, false, 8, 2, 32, 8}, {1, 1, false, 8, 1, 32, 16},
-              {0, 1, false, 0, 0, 0, 1}, {0, 2, false, 0, 0, 0, 1}, {0, 2, true, 0, 0, 0, 1})
+LBNR_VARIANTS(3, 2, 2, {1, 1, false, 8, 4, 32}, {1, 2, false, 8, 4, 32}, {0, 1, true, 0, 0, 0})
+LBNR_VARIANTS(9, 2, 2, {1, 1, false, 8, 2, 32}, {1, 2, false, 8, 3, 32}, {0, 1, true, 0, 0, 0})
+LBNR_VARIANTS(19, 2, 4, {1, 2, false, 8, 2, 32}, {1, 1, false, 8, 1, 32},
+              {0, 1, false, 0, 0, 0}, {0, 2, false, 0, 0, 0}, {0, 2, true, 0, 0, 0})
 #undef LBNR_VARIANTS
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no
@@ -125,10 +119,9 @@ struct Impl {
     if (v < 0 || v >= VT::n || v >= 8) return "?";
     const VariantSpec& x = VT::v[v];
     if (x.kind == 0)
-      snprintf(buf[v], sizeof(buf[v]), "P%d%s%s", x.P, x.hold ? "-hold" : "-reread",
-               x.pf ? "-pf" : "");
+      snprintf(buf[v], sizeof(buf[v]), "P%d%s", x.P, x.hold ? "-hold" : "-reread");
     else
-      snprintf(buf[v], sizeof(buf[v]), "tma-p%d-nc%d-k%d-t%d-pf%d", x.P, x.nc, x.k, x.tc, x.pf);
+      snprintf(buf[v], sizeof(buf[v]), "tma-p%d-nc%d-k%d-t%d", x.P, x.nc, x.k, x.tc);
     return buf[v];
   }
 
@@ -137,10 +130,9 @@ struct Impl {
     constexpr VariantSpec x = VT::v[VI];
     constexpr int P = x.P;
     constexpr bool H = x.hold;
-    constexpr bool PF = x.pf != 0 && LAYOUT != kAAOdd;
     const int block = 128;
     const int64_t threads = P == 2 ? ((L.cells + 15) / 16) * 32 : L.cells;
-    k_collide<Q, S, C, REP, LAYOUT, P, H, PF><<<grid_for(threads, block), block, 0, L.st>>>(a);
+    k_collide<Q, S, C, REP, LAYOUT, P, H><<<grid_for(threads, block), block, 0, L.st>>>(a);
     return cudaGetLastError();
   }
 
@@ -154,8 +146,7 @@ struct Impl {
     constexpr int NS = NC / (TC / (32 / P)) * K;
     constexpr uint32_t smem = tma_smem_bytes(tma_stage_bytes<S>(Q, TC), NS);
     static_assert(smem <= 232448, "shared memory per block");
-    constexpr int PFD = x.pf;
-    auto kern = k_collide_tma<Q, S, C, REP, LAYOUT, NC, K, TC, P, PFD>;
+    auto kern = k_collide_tma<Q, S, C, REP, LAYOUT, NC, K, TC, P>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     CUtensorMap map;

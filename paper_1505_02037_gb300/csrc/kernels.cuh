@@ -286,10 +286,7 @@ __device__ __forceinline__ void unpack(const C m[kNF], C& alpha, C g[6], C K[6],
 // ---------------------------------------------------------------------------
 // k_collide: the fused step
 // ---------------------------------------------------------------------------
-// PF: before summing, every lane asks L2 for all of its cell's values
-// (prefetch.global.L2 needs no registers), so the moment pass finds them in
-// flight or in L2 instead of issuing a few DRAM loads at a time.
-template <int Q, class S, class C, int REP, int LAYOUT, int P, bool HOLD, bool PF>
+template <int Q, class S, class C, int REP, int LAYOUT, int P, bool HOLD>
 __global__ void __launch_bounds__(128, HOLD ? 1 : 3) k_collide(const StepArgs<S, C> a) {
   using L = Lattice<Q>;
   constexpr int NJ = kNF / P;
@@ -304,17 +301,6 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : 3) k_collide(const StepArgs<S,
   const int64_t ps = a.G.pstride;
   const uint32_t ps32 = (uint32_t)ps;
   const Nbr n = make_nbr(a.G, c);
-
-  if (PF) {
-#pragma unroll
-    for (int j = 0; j < NJ; ++j) {
-      const int F = g ? field_of(P, 1, j) : field_of(P, 0, j);
-      const S* fb = a.fin + field_base<Q>(F, ps);
-#pragma unroll
-      for (int l = 0; l < Q; ++l)
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(fb + read_off<Q, LAYOUT>(n, ps32, l)));
-    }
-  }
 
   // Pass 1: zeroth moments of this thread's fields (ascending l).
   C fv[HOLD ? NJ : 1][HOLD ? Q : 1];
