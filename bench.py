@@ -7,6 +7,14 @@ Boltzmann time step over the whole lattice (moment pass + fused
 collide-and-stream kernel). Metric: lattice updates/s in Mcell*var/s
 (cells x 16 fields x steps / s).
 
+Workload "batched": the ensemble configuration, 512 independent 1D/2D
+gauge-wave runs (seed 150502037; N uniform in 64..4096 for 1D and 64..512
+for 2D, tau uniform in [0.51, 2], A log-uniform in [1e-3, 0.1], FP32
+deviation storage) advanced by one persistent cooperative launch per step.
+There one "step" is one launch in which every run advances one crossing
+time (N of its steps), so 10 steps are the configuration's 10 crossings; the
+runs are re-initialised after the warm-up launches.
+
 Prints one JSON line (rank 0). Under torchrun each rank runs an independent
 replica of the workload on its own GPU (the path has no exchange step), so
 scaling is weak and value = units of all ranks / max time over ranks.
@@ -50,15 +58,24 @@ DTYPE = {"f64": "f64", "f32": "f32", "dev_f32": "f32", "dev_bf16": "f32 (bf16 st
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=1000)
-    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--steps", type=int, default=None,
+                   help="default 1000 (10 for the batched workload)")
+    p.add_argument("--warmup", type=int, default=None,
+                   help="default 10 (3 for the batched workload)")
     p.add_argument("--impl", default="lbnr", choices=["lbnr", "reference"])
-    p.add_argument("--workload", default="gauge3d-256-f32", choices=sorted(WORKLOADS))
+    p.add_argument("--workload", default="gauge3d-256-f32",
+                   choices=sorted(WORKLOADS) + ["batched"])
     p.add_argument("--tau", type=float, default=4.5)
     p.add_argument("--profile-steps", type=int, default=20)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    return p.parse_args()
+    a = p.parse_args()
+    batched = a.workload == "batched"
+    if a.steps is None:
+        a.steps = 10 if batched else 1000
+    if a.warmup is None:
+        a.warmup = 3 if batched else 10
+    return a
 
 
 def measured_peaks():
@@ -211,8 +228,215 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Batched ensemble
+# ---------------------------------------------------------------------------
+ENSEMBLE_SEED = 150502037
+
+
+def batched_config(world_rank_seed_note=""):
+    return {
+        "workload": "ensemble of 512 independent gauge-wave runs (seed 150502037): 1D D1Q3 "
+                    "N~U{64..4096} or 2D D2Q9 NxN, N~U{64..512} (x-aligned for even run id, "
+                    "(1,1) diagonal for odd), tau~U[0.51,2.0], A~logU[1e-3,0.1], 10 crossing "
+                    "times (10 N steps) per run, FP32 deviation storage, one persistent "
+                    "cooperative launch per step (graph-captured)" + world_rank_seed_note,
+        "workload_key": "batched", "runs": 512, "fields": 16,
+        "step": "one launch in which every run advances one crossing time (N of its steps); "
+                "10 steps = the whole configuration from t = 0",
+        "tau_note": "every tau in [0.51, 2] is linearly unstable for this scheme; a run whose "
+                    "moments turn non-finite stops at that step and only the steps actually "
+                    "taken are counted",
+    }
+
+
+def oracle_rate_on_ensemble(specs, seconds):
+    """FP64 oracle throughput (Mcell*var/s) on the first runs of the ensemble,
+    50 steps each (initialisation not timed), for about `seconds`."""
+    from oracle import oracle as O
+    units, timed, used = 0, 0.0, 0
+    for r in specs:
+        o = O.Oracle(r["vset"], r["shape"], r["tau"], r["dx"])
+        f = o.init(W.ensemble_fields(r))
+        n = min(r["steps"], 50)
+        ts = time.perf_counter()
+        try:
+            o.run(f, n)
+        except FloatingPointError:
+            pass
+        timed += time.perf_counter() - ts
+        units += r["shape"][0] * r["shape"][1] * 16 * n
+        used += 1
+        if timed > seconds:
+            break
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return units / timed / 1e6, cores, (
+        f"FP64 oracle on the first {used} runs of the ensemble, {50} steps each "
+        f"(initialisation untimed), {timed:.1f} s on {cores} host threads")
+
+
+def run_reference_batched(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    specs = W.ensemble(seed=ENSEMBLE_SEED)
+    per_step = 20.0 / max(args.steps + args.warmup, 1)
+    for _ in range(args.warmup):
+        oracle_rate_on_ensemble(specs, per_step)
+    vals = []
+    for _ in range(args.steps):
+        rate, cores, sample = oracle_rate_on_ensemble(specs, per_step)
+        vals.append(rate)
+    value = statistics.median(vals)
+    units_per_step = sum(r["shape"][0] * r["shape"][1] * 16 * r["N"] for r in specs)
+    line = {"impl": "reference", "metric": "lattice updates/s", "value": value,
+            "unit": "Mcell*var/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": units_per_step / (value * 1e6) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": batched_config(),
+            "cpu_baseline": {"value": value, "unit": "Mcell*var/s", "cores": cores,
+                             "kind": "oracle", "sample": "each step: " + sample},
+            "e2e": {"value": value, "unit": "Mcell*var/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main_batched(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_1505_02037_gb300 import autotune, lbnr
+
+    # each rank its own ensemble (independent problems; rank 0 = the seed above)
+    specs = W.ensemble(seed=ENSEMBLE_SEED + rank)
+    for r in specs:
+        r["steps_total"] = r["steps"]
+        r["steps"] = r["N"]  # one crossing time per launch
+    cells = [r["shape"][0] * r["shape"][1] for r in specs]
+    offs = np.concatenate([[0], np.cumsum(cells)]) * 16
+    host = torch.empty(int(offs[-1]), dtype=torch.float64).pin_memory()
+    hnp = host.numpy()
+    for i, r in enumerate(specs):
+        hnp[offs[i]:offs[i + 1]] = W.ensemble_fields(r).reshape(-1)
+    b = lbnr.Batch(specs, storage="dev_f32")
+
+    def init_all():
+        for i in range(len(specs)):
+            lbnr.lbnr_batch_init(b.b, i, host[offs[i]:offs[i + 1]])
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    init_all()
+    tuning = autotune.tune_batch(b, trial_steps=16)
+    for _ in range(args.warmup):
+        b.run()
+    b.status()
+    init_all()
+    barrier()
+    stream = b.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            b.run()
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    rc, per = b.status()
+    taken = np.array([b.steps_done(i) for i in range(len(specs))], dtype=np.int64)
+    units = float(sum(c * 16 * t for c, t in zip(cells, taken)))
+    t = torch.tensor([ms, units], device=dev, dtype=torch.float64)
+    if world > 1:
+        tm = t[:1].clone()
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        tu = t[1:].clone()
+        dist.all_reduce(tu, op=dist.ReduceOp.SUM)
+        ms_max, units_all = float(tm.item()), float(tu.item())
+    else:
+        ms_max, units_all = ms, units
+    qs = [3 if r["vset"] == 1 else 9 for r in specs]
+    alg = float(sum(c * t * (2 * 16 * q * 4 + 7 * 4) for c, t, q in zip(cells, taken, qs)))
+    peaks, peak_kind = measured_peaks()
+    peak = float(peaks["hbm_gbs"])
+    achieved = alg / (ms * 1e-3) / 1e9
+    plan = b.plan()
+    nonfinite = sum(1 for x in per if x == -4)
+    value = units_all / (ms_max * 1e-3) / 1e6
+    line = {
+        "metric": "lattice updates/s", "value": value, "unit": "Mcell*var/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (f32 deviation storage)", "data": "synthetic",
+        "config": dict(batched_config(), l2="inputs larger than L2 (%.1f GB of distributions)"
+                       % (sum(c * 16 * q * 4 * 2 for c, q in zip(cells, qs)) / 1e9),
+                       parallelism="one ensemble per GPU" if world > 1 else "single GPU",
+                       cell_steps_taken=int(taken @ np.array(cells)),
+                       cell_steps_configured=int(sum(c * r["steps_total"]
+                                                     for c, r in zip(cells, specs))),
+                       runs_nonfinite=nonfinite, runs_timed_out=sum(1 for x in per if x == -5)),
+        "roofline": {"bound": "hbm", "kernel": "k_batch (persistent ensemble kernel)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": f"hbm_gbs of {peak_kind}",
+                     "algorithmic_bytes_per_cell_step": "2*16*Q*4 + 7*4 (Q = 3 or 9)",
+                     "avg_launch_ms": ms / args.steps, "traffic": None},
+        "gpu_launches": args.steps,
+        "launch_form": f"block {plan['block']} x grid {plan['grid']}, "
+                       f"graph={'yes' if plan['graphed'] else 'no'}, "
+                       f"{sum(1 for x in plan['teams'] if x > 1)} runs on teams",
+        "autotune_ms_per_trial": {f"{k[0]}x{k[1]}": v for k, v in tuning.items()},
+        "clocks": clk.summary(),
+    }
+    if not args.no_e2e:
+        # through the public API from pinned host fields: init every run,
+        # K launches, read back every run's status and step count
+        barrier()
+        t0 = time.perf_counter()
+        init_all()
+        for _ in range(args.steps):
+            b.run()
+        rc2, per2 = b.status()
+        barrier()
+        el = time.perf_counter() - t0
+        taken2 = np.array([b.steps_done(i) for i in range(len(specs))], dtype=np.int64)
+        u2 = float(sum(c * 16 * t for c, t in zip(cells, taken2)))
+        tt = torch.tensor([el, u2], device=dev, dtype=torch.float64)
+        if world > 1:
+            a_ = tt[:1].clone()
+            dist.all_reduce(a_, op=dist.ReduceOp.MAX)
+            b_ = tt[1:].clone()
+            dist.all_reduce(b_, op=dist.ReduceOp.SUM)
+            el, u2 = float(a_.item()), float(b_.item())
+        line["e2e"] = {"value": u2 / el / 1e6, "unit": "Mcell*var/s",
+                       "h2d_bytes_per_step": host.numel() * 8 / args.steps,
+                       "d2h_bytes_per_step": len(specs) * (4 + 8) / args.steps}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, sample = oracle_rate_on_ensemble(specs, 12.0)
+        line["cpu_baseline"] = {"value": rate, "unit": "Mcell*var/s", "cores": cores,
+                                "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    b.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
+    if args.workload == "batched":
+        return run_reference_batched(args) if args.impl == "reference" else main_batched(args)
     if args.impl == "reference":
         return run_reference(args)
     import torch

@@ -183,6 +183,89 @@ int lbnr_streaming(const lbnr_ctx* ctx);
 int lbnr_constraint_norms_noalloc(int vset, const lbnr_grid* grid, double dx,
                                   const double* d_fields, double* d_out, void* cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Batched ensemble: many independent periodic 1D (D1Q3) and 2D (D2Q9)
+ * lattices, each with its own size, tau, slicing and step count, advanced by
+ * one persistent cooperative kernel launch (captured in a CUDA graph). Every
+ * run is the same step as a single context (Eq. numlb with the equilibria
+ * and sources of Eqs. (alfa)-(ekstsor), ping-pong streaming); a run of many
+ * cells is split over a team of thread blocks that meet at device-side
+ * barriers between the moment pass and the collide pass, small runs are
+ * packed onto single blocks, longest first. The paper runs one lattice at a
+ * time; the batch is for parameter scans and convergence studies.
+ * ------------------------------------------------------------------------ */
+typedef struct lbnr_batch lbnr_batch;
+
+typedef struct {
+  int32_t vset;    /* LBNR_D1Q3 or LBNR_D2Q9 */
+  int32_t slicing; /* LBNR_GEODESIC / LBNR_HARMONIC / LBNR_ONE_PLUS_LOG */
+  lbnr_grid grid;  /* nz = 1; ny = 1 for D1Q3; nx * ny < 2^28 */
+  double tau, dx;  /* tau > 1/2 (units of dt); dt = dx */
+  int64_t steps;   /* steps this run takes per lbnr_batch_run call */
+} lbnr_run_desc;
+
+typedef struct {
+  int32_t storage;      /* LBNR_F64 ... LBNR_DEV_F16, for every run */
+  int32_t block;        /* threads per block: 128 or 256 (default 256) */
+  int32_t ctas_per_sm;  /* resident blocks per SM; 0 = as many as fit */
+  int32_t sources_on;   /* 1 normally; 0 drops every source */
+  void* cuda_stream;    /* cudaStream_t; NULL = a stream of the batch's own */
+  int64_t wait_limit_ns; /* bound of every device-side barrier wait (2 s) */
+  int32_t test_drop_arrival_run; /* test hook, -1 normally: block 0 of this
+                            run's team skips its first barrier arrival so the
+                            run's waits time out */
+  int32_t reserved;
+} lbnr_batch_opts;
+
+/* Fills o with the defaults: DEV_F32, 256 threads, all resident blocks,
+ * sources on, 2 s wait limit, no dropped arrival. */
+void lbnr_default_batch_opts(lbnr_batch_opts* o);
+
+/* Validates the runs, allocates every run's two distribution buffers and
+ * stencil planes in one device allocation, and plans the block assignment
+ * (resident blocks from the occupancy calculator). runs[] is copied. */
+int lbnr_batch_create(int nruns, const lbnr_run_desc* runs, const lbnr_batch_opts* opts,
+                      lbnr_batch** out);
+
+/* Re-plans for another block size / blocks per SM (the autotuner's knobs). */
+int lbnr_batch_configure(lbnr_batch* b, int block, int ctas_per_sm);
+
+/* Initial distributions of one run from host fields [16][cells] (same rule as
+ * lbnr_init); resets the run's step count and status. Synchronises. */
+int lbnr_batch_init(lbnr_batch* b, int run, const double* fields);
+
+/* Enqueues one launch in which every run takes min(max_steps, its steps)
+ * steps (max_steps < 0: its steps). A run whose moments turn non-finite
+ * stops after the step that read them, and a run whose barrier wait timed
+ * out stops where it was; neither is stepped again until lbnr_batch_init.
+ * Returns without waiting. */
+int lbnr_batch_run(lbnr_batch* b, int64_t max_steps);
+
+/* Synchronises; per_run[r] (optional, nruns entries) receives LBNR_OK,
+ * LBNR_ENONFINITE or LBNR_ETIMEOUT for each run; returns the worst. */
+int lbnr_batch_status(lbnr_batch* b, int32_t* per_run);
+
+/* Stored distributions of one run decoded to FP64, host out[16][Q][cells]
+ * in the standard layout. Synchronises. */
+int lbnr_batch_get_distributions(lbnr_batch* b, int run, double* out);
+
+/* The current plan: blocks launched, threads per block, whether the launch is
+ * replayed from a CUDA graph (1) or launched directly (0), and the team size
+ * (blocks) of every run (team_of_run: nruns entries). Any pointer may be
+ * NULL. */
+int lbnr_batch_plan(const lbnr_batch* b, int32_t* grid, int32_t* block, int32_t* graphed,
+                    int32_t* team_of_run);
+
+/* Steps taken by one run since its lbnr_batch_init, as read back by the last
+ * lbnr_batch_status or lbnr_batch_get_distributions; -1 for a bad index. */
+int64_t lbnr_batch_steps_done(const lbnr_batch* b, int run);
+
+/* Frees the batch (synchronises first). NULL is a no-op. */
+void lbnr_batch_destroy(lbnr_batch* b);
+
+/* Last error message of the batch. */
+const char* lbnr_batch_last_error(const lbnr_batch* b);
+
 /* Frees what the context allocated. NULL is a no-op. */
 void lbnr_destroy(lbnr_ctx* ctx);
 

@@ -36,3 +36,50 @@ def tune(lat, steps_per_trial: int = 4, trials: int = 2, verbose: bool = False) 
     lat.set_variant(best)
     _cache[key] = best
     return times
+
+
+def batch_shapes(sm_resident_max: int = 4):
+    """(threads per block, blocks per SM) pairs the batched kernel accepts."""
+    shapes = [(256, 1), (256, 2), (128, 1), (128, 2), (128, 4)]
+    return [s for s in shapes if s[1] <= sm_resident_max]
+
+
+def tune_batch(batch, trial_steps: int = 64, trials: int = 2, shapes=None,
+               verbose: bool = False) -> dict:
+    """Chooses the block shape of a lbnr.Batch: for each (threads per block,
+    blocks per SM) the planner re-assigns the runs and one launch of
+    `trial_steps` steps per run is timed with CUDA events (best of `trials`).
+    Shapes the kernel cannot hold resident are skipped. The trial steps
+    advance the runs; re-initialise them afterwards for a clean start.
+    Returns {(block, per_sm): ms}."""
+    import torch
+    from .lbnr import LbnrError
+    shapes = shapes or batch_shapes()
+    times = {}
+    for block, per_sm in shapes:
+        try:
+            batch.configure(block, per_sm)
+        except LbnrError:
+            continue
+        plan = batch.plan()
+        if plan["grid"] < per_sm * torch.cuda.get_device_properties(0).multi_processor_count:
+            continue  # fewer blocks resident than asked for: same as a smaller shape
+        with torch.cuda.stream(batch.stream):
+            batch.run(trial_steps)  # first launch captures the graph
+            best = float("inf")
+            for _ in range(trials):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(batch.stream)
+                batch.run(trial_steps)
+                e1.record(batch.stream)
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+        times[(block, per_sm)] = best
+        if verbose:
+            print(f"  block {block} x {per_sm}/SM (grid {plan['grid']}): {best:.3f} ms")
+    if not times:
+        raise RuntimeError("no block shape of the batched kernel could be planned")
+    best = min(times, key=times.get)
+    batch.configure(*best)
+    return times

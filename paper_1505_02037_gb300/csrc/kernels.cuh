@@ -444,6 +444,131 @@ __global__ void __launch_bounds__(256) k_aux(const S* __restrict__ f, C* __restr
 }
 
 // ---------------------------------------------------------------------------
+// Per-cell bodies for kernels that run many steps in one launch (the batched
+// ensemble). Other thread blocks of the same launch write the buffers these
+// read, so every load is coherent (L1 bypassed). Same arithmetic, in the
+// same order, as k_aux and k_collide with one thread per cell.
+// ---------------------------------------------------------------------------
+template <int Q, class S, class C, int REP, int LAYOUT>
+__device__ __forceinline__ void aux_cell(const S* __restrict__ f, C* __restrict__ aux,
+                                         const Grid& G, int64_t c) {
+  using L = Lattice<Q>;
+  const Nbr n = make_nbr(G, c);
+  const uint32_t ps32 = (uint32_t)G.pstride;
+#pragma unroll
+  for (int F = 0; F < 7; ++F) {
+    const S* fb = f + field_base<Q>(F, G.pstride);
+    C s = C(0);
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+      const C v = Codec<S>::load_coh(fb + read_off<Q, LAYOUT>(n, ps32, l));
+      s += REP == kDEV ? C(L::w(l)) * v : v;
+    }
+    if (F == 0) s = REP == kDEV ? log1p(s) : log(s);
+    aux[(int64_t)F * G.cells + c] = s;
+  }
+}
+
+template <int Q, class C>
+__device__ __forceinline__ void derivatives_coh(const Nbr& n, int64_t cells,
+                                                const C* __restrict__ aux, C inv2dx, C inv4dx,
+                                                C A[3], C D[3][6]) {
+  constexpr int dim = Lattice<Q>::kDim;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (k < dim) {
+      const uint32_t cp = n.at(k == 0, k == 1, k == 2);
+      const uint32_t cm = n.at(-(k == 0), -(k == 1), -(k == 2));
+      A[k] = (__ldcg(aux + cp) - __ldcg(aux + cm)) * inv2dx;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        const C* plane = aux + (size_t)(1 + q) * (size_t)cells;
+        D[k][q] = (__ldcg(plane + cp) - __ldcg(plane + cm)) * inv4dx;
+      }
+    } else {
+      A[k] = C(0);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) D[k][q] = C(0);
+    }
+  }
+}
+
+template <int Q, class S, class C, int REP, int LAYOUT>
+__device__ __forceinline__ void collide_cell(const StepArgs<S, C>& a, int64_t c) {
+  using L = Lattice<Q>;
+  constexpr int dim = L::kDim;
+  const int64_t cells = a.G.cells;
+  const int64_t ps = a.G.pstride;
+  const uint32_t ps32 = (uint32_t)ps;
+  const Nbr n = make_nbr(a.G, c);
+  C rt[kNF];
+#pragma unroll
+  for (int F = 0; F < kNF; ++F) {
+    const S* fb = a.fin + field_base<Q>(F, ps);
+    C s = C(0);
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+      const C v = Codec<S>::load_coh(fb + read_off<Q, LAYOUT>(n, ps32, l));
+      s += REP == kDEV ? C(L::w(l)) * v : v;
+    }
+    rt[F] = s;
+  }
+  {
+    C chk = C(0);
+#pragma unroll
+    for (int F = 0; F < kNF; ++F) chk += rt[F];
+    if (!isfinite(chk)) atomicOr(a.flag, 1);
+  }
+  C A[3], D[3][6];
+  derivatives_coh<Q, C>(n, cells, a.aux, a.inv2dx, a.inv4dx, A, D);
+  C alpha, gm[6], K[6], V[3];
+  unpack<REP, C>(rt, alpha, gm, K, V);
+  C Sr[kNF];
+  bm_sources<C>(alpha, gm, K, V, A, D, a.slicing, Sr);
+  if (!a.sources_on) {
+#pragma unroll
+    for (int F = 0; F < kNF; ++F) Sr[F] = C(0);
+  }
+  C rho[kNF];
+#pragma unroll
+  for (int F = 0; F < kNF; ++F) rho[F] = rt[F] + a.half_dt * Sr[F];
+  C Fl[6][3];
+  {
+    C alpha2, g2[6], K2[6], V2[3];
+    unpack<REP, C>(rho, alpha2, g2, K2, V2);
+    bm_flux<C, dim>(alpha2, g2, V2, A, D, Fl);
+  }
+  const C three_omega = C(3) * a.omega;
+#pragma unroll
+  for (int F = 0; F < kNF; ++F) {
+    const C cf = a.omega * rho[F] + a.sigma * Sr[F];
+    C b[3] = {C(0), C(0), C(0)};
+    if (has_flux(F)) {
+#pragma unroll
+      for (int k = 0; k < dim; ++k) b[k] = three_omega * Fl[F - kK][k];
+    }
+    const S* fb = a.fin + field_base<Q>(F, ps);
+    S* ob = a.fout + field_base<Q>(F, ps);
+    C v_[Q];
+#pragma unroll
+    for (int l = 0; l < Q; ++l) v_[l] = Codec<S>::load_coh(fb + read_off<Q, LAYOUT>(n, ps32, l));
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+      C t = cf;
+      if (has_flux(F)) {
+#pragma unroll
+        for (int k = 0; k < dim; ++k) {
+          if (L::c(l, k) > 0) t += b[k];
+          if (L::c(l, k) < 0) t -= b[k];
+        }
+      }
+      const C out = REP == kDEV ? fma(a.omc, v_[l], t) : fma(a.omc, v_[l], C(L::w(l)) * t);
+      Codec<S>::store(ob + write_off<Q, LAYOUT>(n, ps32, l), out);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // FP64 kernels outside the hot loop: init, moments, constraints, transfers
 // ---------------------------------------------------------------------------
 template <class S>

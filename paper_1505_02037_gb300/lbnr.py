@@ -36,6 +36,18 @@ class Opts(ctypes.Structure):
                 ("dev_bytes", ctypes.c_uint64)]
 
 
+class RunDesc(ctypes.Structure):
+    _fields_ = [("vset", ctypes.c_int32), ("slicing", ctypes.c_int32), ("grid", Grid),
+                ("tau", ctypes.c_double), ("dx", ctypes.c_double), ("steps", ctypes.c_int64)]
+
+
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("storage", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("sources_on", ctypes.c_int32),
+                ("cuda_stream", ctypes.c_void_p), ("wait_limit_ns", ctypes.c_int64),
+                ("test_drop_arrival_run", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class LbnrError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"lbnr error {code} ({ERRORS.get(code, '?')}): {msg}")
@@ -81,6 +93,23 @@ def library(path: str | None = None):
     L.lbnr_set_variant.argtypes = [vp, ctypes.c_int]
     L.lbnr_constraint_norms_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(Grid),
                                                  ctypes.c_double, vp, vp, vp]
+    L.lbnr_default_batch_opts.argtypes = [ctypes.POINTER(BatchOpts)]
+    L.lbnr_default_batch_opts.restype = None
+    L.lbnr_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(RunDesc),
+                                    ctypes.POINTER(BatchOpts), ctypes.POINTER(vp)]
+    L.lbnr_batch_configure.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.lbnr_batch_init.argtypes = [vp, ctypes.c_int, dp]
+    L.lbnr_batch_run.argtypes = [vp, i64]
+    L.lbnr_batch_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
+    L.lbnr_batch_get_distributions.argtypes = [vp, ctypes.c_int, dp]
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    L.lbnr_batch_plan.argtypes = [vp, i32p, i32p, i32p, i32p]
+    L.lbnr_batch_steps_done.argtypes = [vp, ctypes.c_int]
+    L.lbnr_batch_steps_done.restype = i64
+    L.lbnr_batch_destroy.argtypes = [vp]
+    L.lbnr_batch_destroy.restype = None
+    L.lbnr_batch_last_error.argtypes = [vp]
+    L.lbnr_batch_last_error.restype = ctypes.c_char_p
     L.lbnr_destroy.argtypes = [vp]
     L.lbnr_destroy.restype = None
     L.lbnr_last_error.argtypes = [vp]
@@ -89,10 +118,13 @@ def library(path: str | None = None):
     return L
 
 
-def _check(rc, ctx=None):
+def _check(rc, ctx=None, batch=None):
     if rc == 0:
         return
-    msg = library().lbnr_last_error(ctx).decode(errors="replace")
+    if batch is not None:
+        msg = library().lbnr_batch_last_error(batch).decode(errors="replace")
+    else:
+        msg = library().lbnr_last_error(ctx).decode(errors="replace")
     if rc == -4:
         raise NonFiniteError(rc, msg)
     raise LbnrError(rc, msg)
@@ -216,6 +248,58 @@ def lbnr_destroy(ctx):
     library().lbnr_destroy(ctx)
 
 
+def lbnr_default_batch_opts() -> BatchOpts:
+    o = BatchOpts()
+    library().lbnr_default_batch_opts(ctypes.byref(o))
+    return o
+
+
+def lbnr_batch_create(runs, opts: BatchOpts):
+    arr = (RunDesc * len(runs))(*runs)
+    b = ctypes.c_void_p(0)
+    _check(library().lbnr_batch_create(len(runs), arr, ctypes.byref(opts), ctypes.byref(b)))
+    return b
+
+
+def lbnr_batch_configure(b, block: int, ctas_per_sm: int):
+    _check(library().lbnr_batch_configure(b, int(block), int(ctas_per_sm)), batch=b)
+
+
+def lbnr_batch_init(b, run: int, fields):
+    _check(library().lbnr_batch_init(b, int(run), _host_ptr(fields)), batch=b)
+
+
+def lbnr_batch_run(b, max_steps: int = -1):
+    _check(library().lbnr_batch_run(b, int(max_steps)), batch=b)
+
+
+def lbnr_batch_status(b, nruns: int):
+    """Returns (worst code, per-run codes); raises nothing."""
+    per = (ctypes.c_int32 * nruns)()
+    rc = library().lbnr_batch_status(b, per)
+    return rc, list(per)
+
+
+def lbnr_batch_get_distributions(b, run: int, out):
+    _check(library().lbnr_batch_get_distributions(b, int(run), _host_ptr(out)), batch=b)
+
+
+def lbnr_batch_plan(b, nruns: int):
+    g, blk, gr = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    teams = (ctypes.c_int32 * nruns)()
+    _check(library().lbnr_batch_plan(b, ctypes.byref(g), ctypes.byref(blk), ctypes.byref(gr),
+                                     teams))
+    return {"grid": g.value, "block": blk.value, "graphed": bool(gr.value), "teams": list(teams)}
+
+
+def lbnr_batch_steps_done(b, run: int) -> int:
+    return library().lbnr_batch_steps_done(b, int(run))
+
+
+def lbnr_batch_destroy(b):
+    library().lbnr_batch_destroy(b)
+
+
 # ---------------------------------------------------------------------------
 # Convenience wrapper: one lattice, torch-owned workspace and stream
 # ---------------------------------------------------------------------------
@@ -319,6 +403,88 @@ class Lattice:
         if getattr(self, "ctx", None) is not None and self.ctx.value:
             lbnr_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many independent 1D/2D lattices advanced by one persistent launch.
+
+    runs: sequence of dicts with keys vset (1 or 2), shape (nx, ny), tau, dx,
+    steps (per run() call) and optionally slicing. storage as for Lattice.
+    """
+
+    def __init__(self, runs, storage="dev_f32", block=256, ctas_per_sm=0, sources_on=True,
+                 wait_limit_ns=2_000_000_000, drop_arrival_run=-1, stream=None, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("lbnr needs a CUDA device; there is no CPU path")
+        self.device = torch.device(device or "cuda")
+        library()
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        if self.stream.cuda_stream == 0:
+            self.stream = torch.cuda.Stream(self.device)
+        descs = []
+        self.runs = []
+        for r in runs:
+            nx, ny = (tuple(r["shape"]) + (1,))[:2]
+            d = RunDesc(int(r["vset"]), int(r.get("slicing", LBNR_HARMONIC)),
+                        Grid(int(nx), int(ny), 1), float(r["tau"]), float(r["dx"]),
+                        int(r["steps"]))
+            descs.append(d)
+            self.runs.append(dict(r, cells=int(nx) * int(ny), Q=Q_OF[int(r["vset"])]))
+        o = lbnr_default_batch_opts()
+        o.storage = int(STORAGE_NAMES.get(storage, storage))
+        o.block = int(block)
+        o.ctas_per_sm = int(ctas_per_sm)
+        o.sources_on = int(bool(sources_on))
+        o.cuda_stream = ctypes.c_void_p(self.stream.cuda_stream)
+        o.wait_limit_ns = int(wait_limit_ns)
+        o.test_drop_arrival_run = int(drop_arrival_run)
+        self.storage = o.storage
+        self.b = lbnr_batch_create(descs, o)
+
+    def __len__(self):
+        return len(self.runs)
+
+    def init(self, run, fields):
+        a = np.ascontiguousarray(fields, dtype=np.float64).reshape(16, self.runs[run]["cells"])
+        lbnr_batch_init(self.b, run, a)
+
+    def configure(self, block, ctas_per_sm=0):
+        lbnr_batch_configure(self.b, block, ctas_per_sm)
+
+    def run(self, max_steps=-1):
+        lbnr_batch_run(self.b, max_steps)
+
+    def status(self):
+        return lbnr_batch_status(self.b, len(self.runs))
+
+    def check(self):
+        rc, per = self.status()
+        _check(rc, batch=self.b)
+        return per
+
+    def distributions(self, run):
+        r = self.runs[run]
+        out = np.empty((16, r["Q"], r["cells"]))
+        lbnr_batch_get_distributions(self.b, run, out)
+        return out
+
+    def plan(self):
+        return lbnr_batch_plan(self.b, len(self.runs))
+
+    def steps_done(self, run):
+        return lbnr_batch_steps_done(self.b, run)
+
+    def close(self):
+        if getattr(self, "b", None) is not None and self.b.value:
+            lbnr_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

@@ -169,3 +169,31 @@ def random_distributions(Q, weights, shape, seed, amp=1e-3, smooth_amp=2e-2):
         for lam in range(Q):
             f[F, lam] = w[lam] * (base[F] + sm + amp * rng.uniform(-1, 1, size=sm.shape))
     return f
+
+
+def ensemble(nruns=512, seed=150502037, n1=(64, 4096), n2=(64, 512), tau=(0.51, 2.0),
+             amp=(1e-3, 1e-1), crossings=10):
+    """Seeded parameters of an ensemble of independent gauge-wave runs on the
+    unit periodic box: each run is 1D (D1Q3, N cells) or 2D (D2Q9, N x N)
+    with equal probability, N uniform in n1 (1D) or n2 (2D), dx = dt = 1/N,
+    tau uniform in `tau`, A log-uniform in `amp`, and crossings * N steps.
+    2D runs of even id propagate along x, odd ones along the (1,1) diagonal
+    (wavelength 1/sqrt(2), so the wave is periodic on the box)."""
+    rng = np.random.default_rng(seed)
+    runs = []
+    for r in range(nruns):
+        dim = 1 + int(rng.integers(0, 2))
+        lo, hi = n1 if dim == 1 else n2
+        N = int(rng.integers(lo, hi + 1))
+        t = float(rng.uniform(tau[0], tau[1]))
+        A = float(math.exp(rng.uniform(math.log(amp[0]), math.log(amp[1]))))
+        direction = "x" if (dim == 1 or r % 2 == 0) else "xy"
+        shape = (N, 1, 1) if dim == 1 else (N, N, 1)
+        runs.append(dict(run=r, vset=dim, shape=shape, N=N, dx=1.0 / N, tau=t, A=A,
+                         direction=direction, steps=crossings * N))
+    return runs
+
+
+def ensemble_fields(spec):
+    """Initial fields [16][cells] of one ensemble run (gauge wave, t = 0)."""
+    return gauge_wave(spec["shape"], spec["dx"], spec["A"], direction=spec["direction"])

@@ -83,3 +83,45 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.lbnr_steps_done(None) == -1
     lib.lbnr_destroy(None)
     assert lib.lbnr_last_error(None)
+
+
+def test_default_batch_opts(lib):
+    from paper_1505_02037_gb300 import lbnr
+    o = lbnr.lbnr_default_batch_opts()
+    assert (o.storage, o.block, o.ctas_per_sm, o.sources_on) == (2, 256, 0, 1)
+    assert o.wait_limit_ns == 2_000_000_000 and o.test_drop_arrival_run == -1
+
+
+def _run(vset=1, shape=(64, 1, 1), tau=1.0, dx=1 / 64, steps=10, slicing=1):
+    from paper_1505_02037_gb300 import lbnr
+    return lbnr.RunDesc(vset, slicing, lbnr.Grid(*shape), tau, dx, steps)
+
+
+@pytest.mark.parametrize("bad,storage", [
+    (dict(vset=3, shape=(8, 8, 8)), 2),       # batched runs are 1D or 2D
+    (dict(vset=1, shape=(64, 2, 1)), 2),      # D1Q3 with ny > 1
+    (dict(vset=2, shape=(16, 16, 2)), 2),     # nz > 1
+    (dict(shape=(0, 1, 1)), 2),               # empty
+    (dict(tau=0.5), 2),                       # tau = 1/2
+    (dict(dx=0.0), 2),                        # dx = 0
+    (dict(steps=-1), 2),                      # negative step count
+    (dict(slicing=3), 2),                     # unknown slicing
+    (dict(vset=2, shape=(20000, 20000, 1)), 2),  # more than 2^28 cells
+    (dict(), 7),                              # unknown storage
+])
+def test_batch_create_rejects_bad_runs_before_the_device(bad, storage):
+    from paper_1505_02037_gb300 import lbnr
+    o = lbnr.lbnr_default_batch_opts()
+    o.storage = storage
+    runs = [_run(), _run(**bad)]
+    with pytest.raises(lbnr.LbnrError) as e:
+        lbnr.lbnr_batch_create(runs, o)
+    assert e.value.code == -1
+
+
+def test_null_batch_calls_fail_cleanly(lib):
+    assert lib.lbnr_batch_run(None, 1) == -1
+    assert lib.lbnr_batch_status(None, None) == -1
+    assert lib.lbnr_batch_steps_done(None, 0) == -1
+    assert lib.lbnr_batch_plan(None, None, None, None, None) == -1
+    lib.lbnr_batch_destroy(None)

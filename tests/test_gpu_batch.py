@@ -1,0 +1,193 @@
+"""GPU checks of the batched ensemble (one persistent cooperative launch that
+advances many independent 1D/2D runs): every run against the FP64 oracle,
+against the same run on its own context, team barriers, the bounded wait,
+non-finite runs stopping, and the planner's output."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1505_02037_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def L():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1505_02037_gb300 import lbnr
+    lbnr.library()
+    return lbnr
+
+
+def dist_err(g, o, kscale):
+    g = g.reshape(16, -1)
+    o = o.reshape(16, -1)
+    floor = np.array([1.0] * 7 + [kscale] * 9) / 3
+    return np.abs(g - o).max(axis=1) / np.maximum(np.abs(o).max(axis=1), floor)
+
+
+def perturbed(f, seed=0):
+    rng = np.random.default_rng(seed)
+    return f * (1 + rng.choice([-1.0, 1.0], size=f.shape) * 2.2e-16)
+
+
+def small_ensemble(n=10, seed=7, crossings=1, tau=(1.2, 2.0), n1=(33, 300), n2=(5, 40)):
+    runs = W.ensemble(nruns=n, seed=seed, n1=n1, n2=n2, tau=tau, crossings=crossings)
+    for r in runs:
+        r["slicing"] = r["run"] % 3
+    return runs
+
+
+def make_batch(L, runs, **kw):
+    b = L.Batch(runs, **kw)
+    for i, r in enumerate(runs):
+        b.init(i, W.ensemble_fields(r))
+    return b
+
+
+def test_batch_fp64_matches_oracle(L, oracle_mod):
+    """Each run of a mixed 1D/2D ensemble (uneven N, tau, A, slicing, step
+    count) equals the oracle's run to the FP64 bar (1e-12, or 4x the
+    one-ulp spread of the oracle where the method's conditioning is worse)."""
+    runs = small_ensemble()
+    b = make_batch(L, runs, storage="f64")
+    b.run()
+    rc, per = b.status()
+    assert rc == 0 and per == [0] * len(runs)
+    for i, r in enumerate(runs):
+        assert b.steps_done(i) == r["steps"]
+        o = oracle_mod.Oracle(r["vset"], r["shape"], r["tau"], r["dx"], slicing=r["slicing"])
+        f0 = o.init(W.ensemble_fields(r))
+        f = o.run(f0, r["steps"])
+        kscale = math.pi * r["A"]
+        spread = dist_err(o.run(perturbed(f0), r["steps"]), f, kscale).max()
+        err = dist_err(b.distributions(i), f, kscale).max()
+        assert err <= max(TOL64, 4 * spread), (i, r, err, spread)
+    b.close()
+
+
+def test_batch_team_runs_match_single_context(L):
+    """Large runs get a team of blocks that meet at device barriers; with one
+    block per SM the two big runs below need teams. Each run equals the same
+    run stepped on its own context (same storage), to FP32 round-off."""
+    runs = [dict(vset=2, shape=(320, 320, 1), N=320, dx=1 / 320, tau=1.6, A=0.05,
+                 direction="x", steps=24),
+            dict(vset=2, shape=(256, 256, 1), N=256, dx=1 / 256, tau=1.9, A=0.02,
+                 direction="xy", steps=24),
+            dict(vset=1, shape=(4000, 1, 1), N=4000, dx=1 / 4000, tau=1.3, A=0.1,
+                 direction="x", steps=24)]
+    runs += small_ensemble(n=6, seed=11, crossings=1, n1=(20, 80), n2=(4, 24))
+    for r in runs:
+        r["steps"] = min(r["steps"], 24)
+    b = make_batch(L, runs, storage="dev_f32", block=256, ctas_per_sm=1)
+    teams = b.plan()["teams"]
+    assert teams[0] > 1 and teams[1] > 1
+    b.run()
+    assert b.check() == [0] * len(runs)
+    for i, r in enumerate(runs):
+        lat = L.Lattice(r["vset"], r["shape"], r["tau"], r["dx"], slicing=r.get("slicing", 1),
+                        storage="dev_f32", streaming=L.LBNR_STREAM_PINGPONG)
+        lat.init(W.ensemble_fields(r))
+        lat.step(r["steps"])
+        ref = lat.distributions()
+        got = b.distributions(i)
+        err = dist_err(got, ref, math.pi * r["A"]).max()
+        assert err <= 2e-6, (i, teams[i], err)
+        lat.close()
+    b.close()
+
+
+def test_batch_chunked_launches_equal_one_launch(L):
+    """Two launches of k steps per run give the same bits as one of 2k."""
+    runs = small_ensemble(n=8, seed=5, crossings=1)
+    for r in runs:
+        r["steps"] = 20
+    b1 = make_batch(L, runs, storage="dev_f32")
+    b1.run(10)
+    b1.run(10)
+    b2 = make_batch(L, runs, storage="dev_f32")
+    b2.run()
+    assert b1.check() == b2.check() == [0] * len(runs)
+    for i in range(len(runs)):
+        assert b1.steps_done(i) == b2.steps_done(i) == 20
+        assert np.array_equal(b1.distributions(i), b2.distributions(i))
+    b1.close()
+    b2.close()
+
+
+def test_batch_block_shapes_agree(L):
+    """Every block shape the autotuner may choose gives the same bits (the
+    per-cell arithmetic does not depend on the assignment)."""
+    from paper_1505_02037_gb300 import autotune
+    runs = small_ensemble(n=6, seed=3, crossings=1, n2=(40, 96))
+    for r in runs:
+        r["steps"] = 12
+    ref = None
+    for block, per_sm in autotune.batch_shapes():
+        b = make_batch(L, runs, storage="dev_f32", block=block, ctas_per_sm=per_sm)
+        b.run()
+        assert b.check() == [0] * len(runs)
+        out = [b.distributions(i) for i in range(len(runs))]
+        if ref is None:
+            ref = out
+        else:
+            for x, y in zip(out, ref):
+                assert np.array_equal(x, y), (block, per_sm)
+        b.close()
+
+
+def test_batch_is_graph_captured(L):
+    runs = small_ensemble(n=4, seed=9)
+    b = make_batch(L, runs, storage="dev_f32")
+    b.run(2)
+    b.check()
+    p = b.plan()
+    assert p["graphed"]
+    import torch
+    assert p["grid"] % torch.cuda.get_device_properties(0).multi_processor_count == 0
+    b.close()
+
+
+def test_batch_wait_timeout_is_reported(L):
+    """A team member that never arrives (test hook: the first arrival of one
+    run's block 0 is dropped) makes the team's bounded waits run out: that run
+    reports LBNR_ETIMEOUT and stops, every other run completes normally."""
+    runs = [dict(vset=2, shape=(256, 256, 1), N=256, dx=1 / 256, tau=1.5, A=0.05,
+                 direction="x", steps=6)]
+    runs += small_ensemble(n=5, seed=13, crossings=1, n2=(4, 16))
+    for r in runs:
+        r["steps"] = min(r["steps"], 6)
+    b = make_batch(L, runs, storage="dev_f32", ctas_per_sm=1, wait_limit_ns=50_000_000,
+                   drop_arrival_run=0)
+    assert b.plan()["teams"][0] > 1
+    b.run()
+    rc, per = b.status()
+    assert rc == -5 and per[0] == -5 and per[1:] == [0] * (len(runs) - 1)
+    assert b.steps_done(0) == 0
+    for i in range(1, len(runs)):
+        assert b.steps_done(i) == runs[i]["steps"]
+    b.close()
+
+
+def test_batch_nonfinite_run_stops(L):
+    """At tau = 0.51 the scheme is linearly unstable and the run overflows
+    within a few hundred steps: it reports LBNR_ENONFINITE and stops at the
+    step that read the non-finite moments; the other runs are untouched."""
+    runs = [dict(vset=1, shape=(200, 1, 1), N=200, dx=1 / 200, tau=0.51, A=0.1,
+                 direction="x", steps=3000),
+            dict(vset=1, shape=(200, 1, 1), N=200, dx=1 / 200, tau=1.9, A=0.1,
+                 direction="x", steps=300)]
+    b = make_batch(L, runs, storage="dev_f32")
+    b.run()
+    rc, per = b.status()
+    assert per == [-4, 0] and rc == -4
+    assert 0 < b.steps_done(0) < 3000
+    assert b.steps_done(1) == 300
+    d = b.distributions(1)
+    assert np.isfinite(d).all()
+    b.close()
