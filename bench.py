@@ -69,6 +69,8 @@ def parse():
     p.add_argument("--profile-steps", type=int, default=20)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--variant", default=None,
+                   help="collide launch form by name (default: the autotuner's choice)")
     a = p.parse_args()
     batched = a.workload == "batched"
     if a.steps is None:
@@ -137,10 +139,16 @@ class ClockSampler:
                 "samples": len(self.samples)}
 
 
-def source_hash():
+# Sources the collide-and-stream kernels of the 3D lattice are built from.
+COLLIDE_SOURCES = ("collide_tma.cuh", "dispatch.h", "instantiate.cuh", "kernels.cuh",
+                   "lattice.cuh", "physics.cuh", "inst_q19_s0.cu", "inst_q19_s1.cu",
+                   "inst_q19_s2.cu", "inst_q19_s3.cu", "inst_q19_s4.cu")
+
+
+def source_hash(files=COLLIDE_SOURCES):
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1505_02037_gb300", "csrc")
-    for n in sorted(os.listdir(d)):
+    for n in sorted(files):
         with open(os.path.join(d, n), "rb") as f:
             h.update(n.encode() + f.read())
     return h.hexdigest()[:16]
@@ -242,8 +250,9 @@ def batched_config(world_rank_seed_note=""):
                     "times (10 N steps) per run, FP32 deviation storage, one persistent "
                     "cooperative launch per step (graph-captured)" + world_rank_seed_note,
         "workload_key": "batched", "runs": 512, "fields": 16,
-        "step": "one launch in which every run advances one crossing time (N of its steps); "
-                "10 steps = the whole configuration from t = 0",
+        "step": "every run advances one crossing time: 4 launches of ceil(N/4) steps each, "
+                "the work re-planned over the live runs before each launch; 10 steps = the "
+                "whole configuration from t = 0",
         "tau_note": "every tau in [0.51, 2] is linearly unstable for this scheme; a run whose "
                     "moments turn non-finite stops at that step and only the steps actually "
                     "taken are counted",
@@ -317,16 +326,17 @@ def main_batched(args):
 
     # each rank its own ensemble (independent problems; rank 0 = the seed above)
     specs = W.ensemble(seed=ENSEMBLE_SEED + rank)
+    sub = 4  # launches per crossing time
     for r in specs:
         r["steps_total"] = r["steps"]
-        r["steps"] = r["N"]  # one crossing time per launch
+        r["steps"] = -(-r["N"] // sub)
     cells = [r["shape"][0] * r["shape"][1] for r in specs]
     offs = np.concatenate([[0], np.cumsum(cells)]) * 16
     host = torch.empty(int(offs[-1]), dtype=torch.float64).pin_memory()
     hnp = host.numpy()
     for i, r in enumerate(specs):
         hnp[offs[i]:offs[i + 1]] = W.ensemble_fields(r).reshape(-1)
-    b = lbnr.Batch(specs, storage="dev_f32")
+    b = lbnr.Batch(specs, storage="dev_f32", replan=True)
 
     def init_all():
         for i in range(len(specs)):
@@ -339,9 +349,11 @@ def main_batched(args):
             torch.cuda.synchronize()
 
     init_all()
-    tuning = autotune.tune_batch(b, trial_steps=16)
+    tuning = autotune.tune_batch(b, trial_steps=16, reset=init_all)
+    init_all()
     for _ in range(args.warmup):
-        b.run()
+        for _ in range(sub):
+            b.run()
     b.status()
     init_all()
     barrier()
@@ -350,7 +362,7 @@ def main_batched(args):
     with ClockSampler(local) as clk:
         barrier()
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(args.steps * sub):
             b.run()
         e1.record(stream)
         barrier()
@@ -391,8 +403,8 @@ def main_batched(args):
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": f"hbm_gbs of {peak_kind}",
                      "algorithmic_bytes_per_cell_step": "2*16*Q*4 + 7*4 (Q = 3 or 9)",
-                     "avg_launch_ms": ms / args.steps, "traffic": None},
-        "gpu_launches": args.steps,
+                     "avg_launch_ms": ms / (args.steps * sub), "traffic": None},
+        "gpu_launches": args.steps * sub,
         "launch_form": f"block {plan['block']} x grid {plan['grid']}, "
                        f"graph={'yes' if plan['graphed'] else 'no'}, "
                        f"{sum(1 for x in plan['teams'] if x > 1)} runs on teams",
@@ -405,7 +417,7 @@ def main_batched(args):
         barrier()
         t0 = time.perf_counter()
         init_all()
-        for _ in range(args.steps):
+        for _ in range(args.steps * sub):
             b.run()
         rc2, per2 = b.status()
         barrier()
@@ -468,7 +480,11 @@ def main():
 
     # warm-up: the autotuner's trial steps, then graph capture
     from paper_1505_02037_gb300 import autotune
-    tuning = autotune.tune(lat)
+    if args.variant:
+        lat.set_variant(lat.variants.index(args.variant))
+        tuning = {}
+    else:
+        tuning = autotune.tune(lat)
     lat.step(args.warmup)
     barrier()
     stream = lat.stream
@@ -502,7 +518,7 @@ def main():
     # burst figure: the kernel is timed as one launch of a few milliseconds
     peak = float(peaks["hbm_gbs"])
     achieved = alg_collide / (col_ms * 1e-3) / 1e9
-    traffic = traffic_for(f"k_collide:{args.workload}", cells)
+    traffic = traffic_for(f"k_collide:{args.workload}:{lat.variants[lat.variant]}", cells)
 
     value = world * cells * 16 * args.steps / (ms_max * 1e-3) / 1e6
     line = {

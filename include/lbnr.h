@@ -190,8 +190,9 @@ int lbnr_constraint_norms_noalloc(int vset, const lbnr_grid* grid, double dx,
  * run is the same step as a single context (Eq. numlb with the equilibria
  * and sources of Eqs. (alfa)-(ekstsor), ping-pong streaming); a run of many
  * cells is split over a team of thread blocks that meet at device-side
- * barriers between the moment pass and the collide pass, small runs are
- * packed onto single blocks, longest first. The paper runs one lattice at a
+ * barriers between the moment pass and the collide pass; the other runs
+ * wait in a queue, longest first, from which every block without (or done
+ * with) a team run takes the next one. The paper runs one lattice at a
  * time; the batch is for parameter scans and convergence studies.
  * ------------------------------------------------------------------------ */
 typedef struct lbnr_batch lbnr_batch;
@@ -214,11 +215,13 @@ typedef struct {
   int32_t test_drop_arrival_run; /* test hook, -1 normally: block 0 of this
                             run's team skips its first barrier arrival so the
                             run's waits time out */
-  int32_t reserved;
+  int32_t replan;       /* 1: every lbnr_batch_run first calls
+                           lbnr_batch_replan (and so waits for the work
+                           before it); 0 (default): plan once */
 } lbnr_batch_opts;
 
 /* Fills o with the defaults: DEV_F32, 256 threads, all resident blocks,
- * sources on, 2 s wait limit, no dropped arrival. */
+ * sources on, 2 s wait limit, no dropped arrival, no re-planning. */
 void lbnr_default_batch_opts(lbnr_batch_opts* o);
 
 /* Validates the runs, allocates every run's two distribution buffers and
@@ -229,6 +232,12 @@ int lbnr_batch_create(int nruns, const lbnr_run_desc* runs, const lbnr_batch_opt
 
 /* Re-plans for another block size / blocks per SM (the autotuner's knobs). */
 int lbnr_batch_configure(lbnr_batch* b, int block, int ctas_per_sm);
+
+/* Synchronises and plans the work again over the runs that are still
+ * stepped (not non-finite, not timed out), so that blocks freed by stopped
+ * runs join the remaining ones. Keeps the block shape; the captured graph
+ * stays valid (the plan lives in device memory). */
+int lbnr_batch_replan(lbnr_batch* b);
 
 /* Initial distributions of one run from host fields [16][cells] (same rule as
  * lbnr_init); resets the run's step count and status. Synchronises. */
@@ -251,8 +260,9 @@ int lbnr_batch_get_distributions(lbnr_batch* b, int run, double* out);
 
 /* The current plan: blocks launched, threads per block, whether the launch is
  * replayed from a CUDA graph (1) or launched directly (0), and the team size
- * (blocks) of every run (team_of_run: nruns entries). Any pointer may be
- * NULL. */
+ * (blocks) of every run (team_of_run: nruns entries; 1 for a run stepped by
+ * a single block, 0 for a run the plan leaves out because it stopped). Any
+ * pointer may be NULL. */
 int lbnr_batch_plan(const lbnr_batch* b, int32_t* grid, int32_t* block, int32_t* graphed,
                     int32_t* team_of_run);
 

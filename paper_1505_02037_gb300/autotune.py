@@ -39,18 +39,22 @@ def tune(lat, steps_per_trial: int = 4, trials: int = 2, verbose: bool = False) 
 
 
 def batch_shapes(sm_resident_max: int = 4):
-    """(threads per block, blocks per SM) pairs the batched kernel accepts."""
-    shapes = [(256, 1), (256, 2), (128, 1), (128, 2), (128, 4)]
+    """(threads per block, blocks per SM) pairs the batched kernel accepts:
+    blocks of 256 threads at up to 255 registers (one per SM), blocks of 128
+    at up to 168 registers (one to three per SM) or at up to 128 (four)."""
+    shapes = [(256, 1), (128, 1), (128, 2), (128, 3), (128, 4)]
     return [s for s in shapes if s[1] <= sm_resident_max]
 
 
-def tune_batch(batch, trial_steps: int = 64, trials: int = 2, shapes=None,
+def tune_batch(batch, trial_steps: int = 64, trials: int = 2, shapes=None, reset=None,
                verbose: bool = False) -> dict:
     """Chooses the block shape of a lbnr.Batch: for each (threads per block,
-    blocks per SM) the planner re-assigns the runs and one launch of
-    `trial_steps` steps per run is timed with CUDA events (best of `trials`).
-    Shapes the kernel cannot hold resident are skipped. The trial steps
-    advance the runs; re-initialise them afterwards for a clean start.
+    blocks per SM) the planner re-assigns the runs and launches of
+    `trial_steps` steps per run are timed with CUDA events (best of
+    `trials`, each after `reset()` when given, so that every shape steps the
+    same states: runs that stop early would otherwise make later shapes look
+    faster). Shapes the kernel cannot hold resident are skipped. The trial
+    steps advance the runs; re-initialise them afterwards for a clean start.
     Returns {(block, per_sm): ms}."""
     import torch
     from .lbnr import LbnrError
@@ -68,6 +72,9 @@ def tune_batch(batch, trial_steps: int = 64, trials: int = 2, shapes=None,
             batch.run(trial_steps)  # first launch captures the graph
             best = float("inf")
             for _ in range(trials):
+                if reset is not None:
+                    reset()
+                    batch.replan()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(batch.stream)

@@ -7,9 +7,16 @@
 //
 // Plan (host): a run's cost is cells x steps x Q. With W resident CTAs and
 // an even share L = total / W, a run costing more than L gets a team of
-// ceil(cost / L) CTAs of its own; the other runs are packed onto the
-// remaining CTAs, longest first onto the least-loaded CTA. Every CTA walks
-// its list of (run, rank, team size) assignments.
+// ceil(cost / L) CTAs of its own. The work list holds one entry per team
+// member first, then every other run, longest first; each CTA claims the
+// next entry with an atomic counter whenever it is free. Runs that stop
+// early (non-finite) thus leave no CTA idle while work remains.
+//
+// Team members never wait on an entry nobody claims: the team entries come
+// first and number at most W - 1 when other runs exist (W otherwise), every
+// CTA makes its first claim when the launch starts, and a CTA can only claim
+// again after finishing its entry, so the counter hands out all team entries
+// while at least one CTA is free to claim.
 //
 // Kernel: for each step of a run the team's CTAs split the cells, run the
 // moment pass, meet at a team barrier, run the collide pass, and meet again.
@@ -25,7 +32,6 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
-#include <queue>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -52,8 +58,10 @@ struct Assign {
 
 struct BatchParams {
   const BatchRun* runs;
-  const Assign* assign;
-  const int* astart;  // CTA i walks assign[astart[i] .. astart[i+1])
+  const Assign* work;  // team entries, then single-CTA runs longest first
+  const int* nwork;    // entries in `work` (device memory: re-planning
+                       // rewrites the list without touching the graph)
+  unsigned* head;      // next work entry, zeroed before each launch
   int64_t* done;      // steps taken so far, per run
   unsigned* bar;      // team barrier counters, zeroed before each launch
   int* status;        // per run: bit 0 non-finite, bit 1 wait timed out
@@ -103,21 +111,28 @@ __device__ bool team_sync(const BatchParams& p, const Assign& A, int k) {
 
 template <int Q, class S, class C, int REP>
 __device__ void run_steps(const BatchParams& p, const BatchRun& R, const Assign& A) {
-  const int64_t want = p.max_steps < 0 ? R.steps : (p.max_steps < R.steps ? p.max_steps : R.steps);
+  // every field read once into registers (a runtime index into a copy of the
+  // descriptor would put it in local memory)
+  const S* const f0 = static_cast<const S*>(R.f[0]);
+  const S* const f1 = static_cast<const S*>(R.f[1]);
+  const int64_t rsteps = R.steps;
+  const int64_t want = p.max_steps < 0 ? rsteps : (p.max_steps < rsteps ? p.max_steps : rsteps);
   const int64_t start = p.done[A.run];
   StepArgs<S, C> a;
   a.aux = static_cast<const C*>(R.aux);
   a.flag = &p.status[A.run];
   a.G = R.G;
-  a.inv2dx = C(1.0 / (2.0 * R.dx));
-  a.inv4dx = C(1.0 / (4.0 * R.dx));
-  a.half_dt = C(0.5 * R.dx);
-  a.omega = C(1.0 / R.tau);
-  a.omc = C(1.0 - 1.0 / R.tau);
-  a.sigma = C(R.dx * (1.0 - 1.0 / (2.0 * R.tau)));
+  const double dx = R.dx, tau = R.tau;
+  a.inv2dx = C(1.0 / (2.0 * dx));
+  a.inv4dx = C(1.0 / (4.0 * dx));
+  a.half_dt = C(0.5 * dx);
+  a.omega = C(1.0 / tau);
+  a.omc = C(1.0 - 1.0 / tau);
+  a.sigma = C(dx * (1.0 - 1.0 / (2.0 * tau)));
   a.slicing = R.slicing;
   a.sources_on = p.sources_on;
-  const int64_t cells = R.G.cells;
+  C* const aux = static_cast<C*>(R.aux);
+  const int64_t cells = a.G.cells;
   const int64_t B = blockDim.x;
   // A run that went non-finite or timed out in an earlier launch stays where
   // it stopped. Flags are raised only in the collide phase, between two team
@@ -126,12 +141,12 @@ __device__ void run_steps(const BatchParams& p, const BatchRun& R, const Assign&
   int k = 0;
   int64_t s = 0;
   while (s < want) {
-    const int par = (int)((start + s) & 1);
-    a.fin = static_cast<const S*>(R.f[par]);
-    a.fout = static_cast<S*>(R.f[par ^ 1]);
+    const bool odd = ((start + s) & 1) != 0;
+    a.fin = odd ? f1 : f0;
+    a.fout = const_cast<S*>(odd ? f0 : f1);
     for (int64_t base = A.rank * B; base < cells; base += (int64_t)A.team * B) {
       const int64_t c = base + threadIdx.x;
-      if (c < cells) aux_cell<Q, S, C, REP, kPingPong>(a.fin, static_cast<C*>(R.aux), R.G, c);
+      if (c < cells) aux_cell<Q, S, C, REP, kPingPong>(a.fin, aux, a.G, c);
     }
     if (!team_sync(p, A, k++)) return;
     for (int64_t base = A.rank * B; base < cells; base += (int64_t)A.team * B) {
@@ -149,12 +164,38 @@ __device__ void run_steps(const BatchParams& p, const BatchRun& R, const Assign&
   }
 }
 
-template <class S, int REP>
-__global__ void __launch_bounds__(256, sizeof(S) == 4 ? 2 : 1) k_batch(const BatchParams p) {
+// Launch bounds: form 0 takes blocks of 256 threads with up to 255
+// registers a thread (one block per SM), form 1 blocks of 128 with up to 168
+// (three per SM), form 2 blocks of 128 with up to 128 (four per SM).
+template <int FORM>
+struct BatchForm;
+template <>
+struct BatchForm<0> {
+  static constexpr int kThreads = 256, kMinBlocks = 1;
+};
+template <>
+struct BatchForm<1> {
+  static constexpr int kThreads = 128, kMinBlocks = 3;
+};
+template <>
+struct BatchForm<2> {
+  static constexpr int kThreads = 128, kMinBlocks = 4;
+};
+
+template <class S, int REP, int FORM>
+__global__ void __launch_bounds__(BatchForm<FORM>::kThreads, BatchForm<FORM>::kMinBlocks)
+    k_batch(const BatchParams p) {
   using C = typename std::conditional<sizeof(S) == 8, double, float>::type;
-  for (int e = p.astart[blockIdx.x]; e < p.astart[blockIdx.x + 1]; ++e) {
-    const Assign A = p.assign[e];
-    const BatchRun R = p.runs[A.run];
+  __shared__ int next;
+  const int nwork = *p.nwork;
+  for (;;) {
+    if (threadIdx.x == 0) next = (int)atomicAdd(p.head, 1u);
+    __syncthreads();
+    const int i = next;
+    __syncthreads();  // all have read `next` before thread 0 writes it again
+    if (i >= nwork) break;
+    const Assign A = p.work[i];
+    const BatchRun& R = p.runs[A.run];
     if (R.q == 3)
       run_steps<3, S, C, REP>(p, R, A);
     else
@@ -162,15 +203,28 @@ __global__ void __launch_bounds__(256, sizeof(S) == 4 ? 2 : 1) k_batch(const Bat
   }
 }
 
-void* batch_kernel(int storage) {
+template <int FORM>
+void* batch_kernel_form(int storage) {
   switch (storage) {
-    case LBNR_F64: return (void*)k_batch<double, kABS>;
-    case LBNR_F32: return (void*)k_batch<float, kABS>;
-    case LBNR_DEV_F32: return (void*)k_batch<float, kDEV>;
-    case LBNR_DEV_BF16: return (void*)k_batch<__nv_bfloat16, kDEV>;
-    case LBNR_DEV_F16: return (void*)k_batch<__half, kDEV>;
+    case LBNR_F64: return (void*)k_batch<double, kABS, FORM>;
+    case LBNR_F32: return (void*)k_batch<float, kABS, FORM>;
+    case LBNR_DEV_F32: return (void*)k_batch<float, kDEV, FORM>;
+    case LBNR_DEV_BF16: return (void*)k_batch<__nv_bfloat16, kDEV, FORM>;
+    case LBNR_DEV_F16: return (void*)k_batch<__half, kDEV, FORM>;
     default: return nullptr;
   }
+}
+
+// Form for a block size and a requested number of blocks per SM (0: the
+// form's own maximum).
+int form_for(int block, int per_sm) {
+  if (block == 256) return 0;
+  return per_sm == 4 ? 2 : 1;
+}
+
+void* batch_kernel(int storage, int form) {
+  return form == 0 ? batch_kernel_form<0>(storage)
+                   : form == 1 ? batch_kernel_form<1>(storage) : batch_kernel_form<2>(storage);
 }
 
 int qv(int vset) { return vset == LBNR_D1Q3 ? 3 : vset == LBNR_D2Q9 ? 9 : 0; }
@@ -196,17 +250,20 @@ struct lbnr_batch {
   void* base = nullptr;
   size_t bytes = 0;
   BatchRun* d_runs = nullptr;
-  Assign* d_assign = nullptr;
-  int* d_astart = nullptr;
+  Assign* d_work = nullptr;  // work list (capacity work_cap)
   int64_t* d_done = nullptr;
   unsigned* d_bar = nullptr;
   int* d_status = nullptr;
   int* d_flag = nullptr;
   double* d_stage = nullptr;  // 16 x max cells FP64 (init, transfers)
   int64_t max_cells = 0;
-  int grid = 0, block = 256;
-  std::vector<Assign> assign;
-  std::vector<int> astart;
+  int grid = 0, block = 256, form = 0;
+  std::vector<Assign> work;
+  std::vector<int> team;   // blocks per run in the current plan (0: not stepped)
+  size_t work_cap = 0;
+  Assign* h_work = nullptr;  // pinned staging of the work list
+  int* h_nwork = nullptr;
+  int* d_nwork = nullptr;
   cudaGraphExec_t graph = nullptr;
   int64_t graph_steps = -2;
   bool graphed = true;  // false when the runtime refused to capture the launch
@@ -227,15 +284,18 @@ int bfail(lbnr_batch* b, int code, const char* msg) {
     if (e_ != cudaSuccess) return bfail((b), LBNR_ECUDA, cudaGetErrorString(e_)); \
   } while (0)
 
-// Builds the CTA assignments for `workers` resident CTAs.
-void make_plan(lbnr_batch* b, int workers) {
+// Builds the work list for `workers` resident CTAs over the runs marked
+// live (all when `live` is empty).
+void make_plan(lbnr_batch* b, int workers, const std::vector<char>& live) {
   const int R = (int)b->runs.size();
   std::vector<double> cost(R);
   double total = 0;
   for (int r = 0; r < R; ++r) {
     const lbnr_run_desc& d = b->runs[r];
-    cost[r] = (double)(d.grid.nx * d.grid.ny * d.grid.nz) * (double)std::max<int64_t>(d.steps, 1) *
-              qv(d.vset);
+    const bool on = live.empty() || live[r];
+    cost[r] = on ? (double)(d.grid.nx * d.grid.ny * d.grid.nz) *
+                       (double)std::max<int64_t>(d.steps, 1) * qv(d.vset)
+                 : 0.0;
     total += cost[r];
   }
   const double share = total / std::max(workers, 1);
@@ -243,6 +303,10 @@ void make_plan(lbnr_batch* b, int workers) {
   int big = 0;
   bool any_small = false;
   for (int r = 0; r < R; ++r) {
+    if (cost[r] == 0.0) {
+      team[r] = 0;  // not stepped
+      continue;
+    }
     const int64_t cells = b->runs[r].grid.nx * b->runs[r].grid.ny * b->runs[r].grid.nz;
     const int64_t max_team = std::max<int64_t>(1, (cells + b->block - 1) / b->block);
     int t = (int)std::min<double>(std::ceil(cost[r] / std::max(share, 1.0)), (double)max_team);
@@ -261,56 +325,51 @@ void make_plan(lbnr_batch* b, int workers) {
     --big;
     if (team[rmax] == 1) any_small = true;
   }
-  std::vector<std::vector<Assign>> per(workers);
-  int next = 0;
+  b->work.clear();
   for (int r = 0; r < R; ++r)
     if (team[r] > 1)
-      for (int k = 0; k < team[r]; ++k) per[next++].push_back(Assign{r, k, team[r]});
-  // longest first onto the least-loaded of the remaining CTAs
-  std::vector<int> small;
+      for (int k = 0; k < team[r]; ++k) b->work.push_back(Assign{r, k, team[r]});
+  std::vector<int> single;
   for (int r = 0; r < R; ++r)
-    if (team[r] == 1) small.push_back(r);
-  std::sort(small.begin(), small.end(), [&](int x, int y) { return cost[x] > cost[y]; });
-  typedef std::pair<double, int> Load;
-  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
-  for (int w = next; w < workers; ++w) heap.push(Load(0.0, w));
-  if (heap.empty() && !small.empty()) heap.push(Load(0.0, 0));
-  for (int r : small) {
-    Load l = heap.top();
-    heap.pop();
-    per[l.second].push_back(Assign{r, 0, 1});
-    heap.push(Load(l.first + cost[r], l.second));
-  }
-  b->assign.clear();
-  b->astart.assign(1, 0);
-  for (int w = 0; w < workers; ++w) {
-    for (const Assign& a : per[w]) b->assign.push_back(a);
-    b->astart.push_back((int)b->assign.size());
-  }
+    if (team[r] == 1) single.push_back(r);
+  b->team = team;
+  std::stable_sort(single.begin(), single.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  for (int r : single) b->work.push_back(Assign{r, 0, 1});
   b->grid = workers;
 }
 
+// Copies the work list and its length to the device (stream-ordered, from
+// pinned staging; callers have synchronised the stream, so the staging is
+// free).
 int upload_plan(lbnr_batch* b) {
-  if (b->d_assign) cudaFree(b->d_assign);
-  if (b->d_astart) cudaFree(b->d_astart);
-  b->d_assign = nullptr;
-  b->d_astart = nullptr;
-  BTRY(b, cudaMalloc(&b->d_assign, sizeof(Assign) * std::max<size_t>(1, b->assign.size())));
-  BTRY(b, cudaMalloc(&b->d_astart, sizeof(int) * b->astart.size()));
-  BTRY(b, cudaMemcpy(b->d_assign, b->assign.data(), sizeof(Assign) * b->assign.size(),
-                     cudaMemcpyHostToDevice));
-  BTRY(b, cudaMemcpy(b->d_astart, b->astart.data(), sizeof(int) * b->astart.size(),
-                     cudaMemcpyHostToDevice));
-  if (b->graph) {
-    cudaGraphExecDestroy(b->graph);
-    b->graph = nullptr;
-  }
+  const size_t n = b->work.size();
+  if (n > b->work_cap) return bfail(b, LBNR_ECUDA, "work list larger than its buffer");
+  memcpy(b->h_work, b->work.data(), sizeof(Assign) * n);
+  *b->h_nwork = (int)n;
+  if (n) BTRY(b, cudaMemcpyAsync(b->d_work, b->h_work, sizeof(Assign) * n, cudaMemcpyHostToDevice, b->st));
+  BTRY(b, cudaMemcpyAsync(b->d_nwork, b->h_nwork, sizeof(int), cudaMemcpyHostToDevice, b->st));
+  return LBNR_OK;
+}
+
+// Runs still to be stepped: neither non-finite nor timed out.
+int live_runs(lbnr_batch* b, std::vector<char>& live) {
+  std::vector<int> st(b->runs.size());
+  BTRY(b, cudaMemcpyAsync(st.data(), b->d_status, sizeof(int) * st.size(), cudaMemcpyDeviceToHost,
+                          b->st));
+  BTRY(b, cudaStreamSynchronize(b->st));
+  live.resize(st.size());
+  for (size_t r = 0; r < st.size(); ++r) live[r] = (st[r] & 3) == 0;
   return LBNR_OK;
 }
 
 int configure(lbnr_batch* b, int block, int ctas_per_sm) {
   if (block != 128 && block != 256) return bfail(b, LBNR_EINVAL, "block must be 128 or 256");
-  void* kern = batch_kernel(b->opts.storage);
+  if (ctas_per_sm < 0 || ctas_per_sm > 4) return bfail(b, LBNR_EINVAL, "ctas_per_sm must be 0..4");
+  const int form = form_for(block, ctas_per_sm);
+  void* kern = batch_kernel(b->opts.storage, form);
+  // the kernel uses no shared memory to speak of: give the SM's unified
+  // cache to L1
+  BTRY(b, cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
   int occ = 0;
   BTRY(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, 0));
   if (occ < 1) return bfail(b, LBNR_ECUDA, "batched kernel cannot be resident");
@@ -318,14 +377,37 @@ int configure(lbnr_batch* b, int block, int ctas_per_sm) {
   BTRY(b, cudaGetDevice(&dev));
   BTRY(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ) : occ;
+  const int workers = sms * per_sm;
+  // work list buffers: at most one entry per CTA for team members plus one
+  // per run
+  const size_t cap = b->runs.size() + (size_t)workers;
+  if (cap > b->work_cap) {
+    cudaFree(b->d_work);
+    cudaFreeHost(b->h_work);
+    b->d_work = nullptr;
+    b->h_work = nullptr;
+    b->work_cap = 0;
+    BTRY(b, cudaMalloc(&b->d_work, sizeof(Assign) * cap));
+    BTRY(b, cudaMallocHost(&b->h_work, sizeof(Assign) * cap));
+    b->work_cap = cap;
+  }
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
   b->block = block;
-  make_plan(b, sms * per_sm);
+  b->form = form;
+  std::vector<char> live;
+  int rc = live_runs(b, live);
+  if (rc) return rc;
+  make_plan(b, workers, live);
   return upload_plan(b);
 }
 
 // Barrier reset and the cooperative launch, on the batch's stream.
 cudaError_t enqueue_batch(lbnr_batch* b, BatchParams& p) {
-  cudaError_t e = cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned) * b->runs.size(), b->st);
+  // team barrier counters and the work-list head
+  cudaError_t e = cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned) * (b->runs.size() + 1), b->st);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg;
   memset(&cfg, 0, sizeof(cfg));
@@ -338,7 +420,7 @@ cudaError_t enqueue_batch(lbnr_batch* b, BatchParams& p) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   void* args[] = {&p};
-  return cudaLaunchKernelExC(&cfg, batch_kernel(b->opts.storage), args);
+  return cudaLaunchKernelExC(&cfg, batch_kernel(b->opts.storage, b->form), args);
 }
 
 }  // namespace
@@ -360,7 +442,7 @@ int lbnr_batch_create(int nruns, const lbnr_run_desc* runs, const lbnr_batch_opt
                       lbnr_batch** out) {
   if (!out || !runs || !opts || nruns < 1) return bfail(nullptr, LBNR_EINVAL, "bad argument");
   *out = nullptr;
-  if (!batch_kernel(opts->storage)) return bfail(nullptr, LBNR_EINVAL, "unknown storage");
+  if (!batch_kernel(opts->storage, 0)) return bfail(nullptr, LBNR_EINVAL, "unknown storage");
   for (int r = 0; r < nruns; ++r) {
     const lbnr_run_desc& d = runs[r];
     if (qv(d.vset) == 0) return bfail(nullptr, LBNR_EINVAL, "batched runs are D1Q3 or D2Q9");
@@ -424,9 +506,11 @@ int lbnr_batch_create(int nruns, const lbnr_run_desc* runs, const lbnr_batch_opt
     e = cudaMemcpy(b->d_runs, b->hruns.data(), sizeof(BatchRun) * nruns, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_done, sizeof(int64_t) * nruns);
   if (e == cudaSuccess) e = cudaMemset(b->d_done, 0, sizeof(int64_t) * nruns);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_bar, sizeof(unsigned) * nruns);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_bar, sizeof(unsigned) * (nruns + 1));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(int) * nruns);
   if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int) * nruns);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_nwork, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&b->h_nwork, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_flag, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(b->d_flag, 0, sizeof(int));
   if (e == cudaSuccess && opts->cuda_stream) {
@@ -484,16 +568,31 @@ int lbnr_batch_init(lbnr_batch* b, int run, const double* fields) {
   BTRY(b, cudaMemsetAsync(b->d_done + run, 0, sizeof(int64_t), b->st));
   BTRY(b, cudaStreamSynchronize(b->st));
   b->done[run] = 0;
+  if (b->team[run] == 0) return lbnr_batch_replan(b);  // stopped run restarted
   return LBNR_OK;
+}
+
+int lbnr_batch_replan(lbnr_batch* b) {
+  if (!b) return bfail(b, LBNR_EINVAL, "null batch");
+  std::vector<char> live;
+  int rc = live_runs(b, live);  // synchronises
+  if (rc) return rc;
+  make_plan(b, b->grid, live);
+  return upload_plan(b);
 }
 
 int lbnr_batch_run(lbnr_batch* b, int64_t max_steps) {
   if (!b) return bfail(b, LBNR_EINVAL, "null batch");
   if (max_steps < 0) max_steps = -1;
+  if (b->opts.replan) {
+    int rc = lbnr_batch_replan(b);
+    if (rc) return rc;
+  }
   BatchParams p;
   p.runs = b->d_runs;
-  p.assign = b->d_assign;
-  p.astart = b->d_astart;
+  p.work = b->d_work;
+  p.nwork = b->d_nwork;
+  p.head = b->d_bar + b->runs.size();
   p.done = b->d_done;
   p.bar = b->d_bar;
   p.status = b->d_status;
@@ -583,8 +682,7 @@ int lbnr_batch_plan(const lbnr_batch* b, int32_t* grid, int32_t* block, int32_t*
   if (block) *block = b->block;
   if (graphed) *graphed = b->graphed ? 1 : 0;
   if (team_of_run) {
-    for (size_t r = 0; r < b->runs.size(); ++r) team_of_run[r] = 1;
-    for (const Assign& a : b->assign) team_of_run[a.run] = a.team;
+    for (size_t r = 0; r < b->runs.size(); ++r) team_of_run[r] = b->team[r];
   }
   return LBNR_OK;
 }
@@ -597,8 +695,10 @@ void lbnr_batch_destroy(lbnr_batch* b) {
   if (!b) return;
   if (b->st) cudaStreamSynchronize(b->st);
   if (b->graph) cudaGraphExecDestroy(b->graph);
-  cudaFree(b->d_assign);
-  cudaFree(b->d_astart);
+  cudaFree(b->d_work);
+  cudaFree(b->d_nwork);
+  cudaFreeHost(b->h_work);
+  cudaFreeHost(b->h_nwork);
   cudaFree(b->d_runs);
   cudaFree(b->d_done);
   cudaFree(b->d_bar);

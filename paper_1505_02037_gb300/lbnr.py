@@ -45,7 +45,7 @@ class BatchOpts(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("sources_on", ctypes.c_int32),
                 ("cuda_stream", ctypes.c_void_p), ("wait_limit_ns", ctypes.c_int64),
-                ("test_drop_arrival_run", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("test_drop_arrival_run", ctypes.c_int32), ("replan", ctypes.c_int32)]
 
 
 class LbnrError(RuntimeError):
@@ -100,6 +100,7 @@ def library(path: str | None = None):
     L.lbnr_batch_configure.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.lbnr_batch_init.argtypes = [vp, ctypes.c_int, dp]
     L.lbnr_batch_run.argtypes = [vp, i64]
+    L.lbnr_batch_replan.argtypes = [vp]
     L.lbnr_batch_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
     L.lbnr_batch_get_distributions.argtypes = [vp, ctypes.c_int, dp]
     i32p = ctypes.POINTER(ctypes.c_int32)
@@ -273,6 +274,10 @@ def lbnr_batch_run(b, max_steps: int = -1):
     _check(library().lbnr_batch_run(b, int(max_steps)), batch=b)
 
 
+def lbnr_batch_replan(b):
+    _check(library().lbnr_batch_replan(b), batch=b)
+
+
 def lbnr_batch_status(b, nruns: int):
     """Returns (worst code, per-run codes); raises nothing."""
     per = (ctypes.c_int32 * nruns)()
@@ -419,7 +424,8 @@ class Batch:
     """
 
     def __init__(self, runs, storage="dev_f32", block=256, ctas_per_sm=0, sources_on=True,
-                 wait_limit_ns=2_000_000_000, drop_arrival_run=-1, stream=None, device=None):
+                 wait_limit_ns=2_000_000_000, drop_arrival_run=-1, replan=False, stream=None,
+                 device=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("lbnr needs a CUDA device; there is no CPU path")
@@ -445,6 +451,7 @@ class Batch:
         o.cuda_stream = ctypes.c_void_p(self.stream.cuda_stream)
         o.wait_limit_ns = int(wait_limit_ns)
         o.test_drop_arrival_run = int(drop_arrival_run)
+        o.replan = int(bool(replan))
         self.storage = o.storage
         self.b = lbnr_batch_create(descs, o)
 
@@ -460,6 +467,9 @@ class Batch:
 
     def run(self, max_steps=-1):
         lbnr_batch_run(self.b, max_steps)
+
+    def replan(self):
+        lbnr_batch_replan(self.b)
 
     def status(self):
         return lbnr_batch_status(self.b, len(self.runs))
