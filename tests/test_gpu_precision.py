@@ -1,0 +1,161 @@
+"""Reduced-precision storage against the FP64 oracle: the gauge wave along x
+(A = 0.01) stored as FP32, or as FP32/FP16/BF16 deviations from flat space,
+collided in FP32.
+
+Stated bound. Rounding a stored value perturbs a moment by about the
+storage's rounding unit times the value. The stencil turns that into a
+relative error of the derivatives times N / 2 pi (one over k dx), and the
+collision weighs the equilibrium by 1/tau. After one step the error is
+therefore about K_s (N / 2 pi) / tau. K_s is per storage and set; it does
+not depend on N or tau. Each later step adds the same amount, and the
+scheme's largest amplification factor lambda(tau) grows what is already
+there. So after n steps
+
+    max_F max_x |rho_F - rho_F(oracle)| / A  <=  3 K_s (N / 2 pi) / tau * sum_{k<n} lambda^k
+
+with lambda(tau) taken from the oracle's step linearised about flat space.
+K_s: the rounding unit u of the stored type times a constant of order one
+found on GB300 over N in {64, 256} and tau in {0.55, 0.8, 1.5}:
+
+    dev_bf16  1.0e-2  (u = 2^-9: about 5 u)
+    dev_f16   1.0e-3  (u = 2^-12: about 4 u)
+    dev_f32   2.5e-7 on D1Q3, 1.0e-6 on D3Q19 (u = 2^-24: 4 u and 16 u)
+    f32       5.0e-5 on D1Q3, 2.0e-4 on D3Q19 (absolute storage: u / A scale)
+
+The factor 3 is the margin. The x-aligned 3D run equals the 1D run to round-off
+(pinned on the oracle), so the 1D oracle at the same N is the reference for
+any 3D lattice. With LBNR_REPORT_DIR set, every measured error (against the
+oracle and against the analytic solution) is also written as JSON.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1505_02037_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+A = 0.01
+K = {"dev_bf16": (1.0e-2, 1.0e-2), "dev_f16": (1.0e-3, 1.0e-3),
+     "dev_f32": (2.5e-7, 1.0e-6), "f32": (5.0e-5, 2.0e-4)}
+REPORT = []
+
+
+@pytest.fixture(scope="module")
+def L():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1505_02037_gb300 import lbnr
+    lbnr.library()
+    yield lbnr
+    d = os.environ.get("LBNR_REPORT_DIR")
+    if d and REPORT:
+        os.makedirs(d, exist_ok=True)
+        with open(os.path.join(d, "precision_report.json"), "w") as f:
+            json.dump(REPORT, f, indent=0)
+
+
+_lam = {}
+
+
+def amplification(oracle_mod, tau, N=32):
+    """Largest modulus of the eigenvalues of the oracle's step linearised about
+    flat space (D1Q3, N cells; the x-aligned modes of every set)."""
+    if tau not in _lam:
+        o = oracle_mod.Oracle(1, (N, 1, 1), tau, 1 / N)
+        f0 = o.init(W.flat((N, 1, 1)))
+        base = o.step(f0).reshape(-1)
+        flat = f0.reshape(-1)
+        J = np.zeros((flat.size, flat.size))
+        for i in range(flat.size):
+            g = flat.copy()
+            g[i] += 1e-7
+            J[:, i] = (o.step(g.reshape(f0.shape)).reshape(-1) - base) / 1e-7
+        _lam[tau] = float(np.abs(np.linalg.eigvals(J)).max())
+    return _lam[tau]
+
+
+def bound(storage, three_d, N, tau, n, lam):
+    k = K[storage][1 if three_d else 0]
+    growth = n if abs(lam - 1) < 1e-12 else (lam ** n - 1) / (lam - 1)
+    return 3 * k * (N / (2 * math.pi)) / tau * growth
+
+
+def oracle_moments(oracle_mod, N, tau, steps):
+    o = oracle_mod.Oracle(1, (N, 1, 1), tau, 1 / N)
+    f = o.init(W.gauge_wave((N, 1, 1), 1 / N, A))
+    out, done = {}, 0
+    for n in steps:
+        f = o.run(f, n - done)
+        done = n
+        out[n] = o.moments(f).reshape(16, N)
+    return out
+
+
+def check(L, oracle_mod, storage, vset, N, tau, steps):
+    three_d = vset == 3
+    shape = (N, N, N) if three_d else (N, 1, 1)
+    lam = amplification(oracle_mod, tau)
+    ref = oracle_moments(oracle_mod, N, tau, steps)
+    lat = L.Lattice(vset, shape, tau, 1 / N, storage=storage)
+    lat.init(W.gauge_wave(shape, 1 / N, A))
+    done = 0
+    for n in steps:
+        lat.step(n - done)
+        done = n
+        lat.status()
+        m = lat.moments().reshape(16, -1, N)
+        exact = W.gauge_wave((N, 1, 1), 1 / N, A, t=n / N).reshape(16, 1, N)
+        err = float(np.abs(m - ref[n][:, None, :]).max() / A)
+        err_exact = float(np.abs(m - exact).max() / A)
+        oracle_exact = float(np.abs(ref[n][:, None, :] - exact).max() / A)
+        b = bound(storage, three_d, N, tau, n, lam)
+        REPORT.append(dict(storage=storage, vset=vset, N=N, tau=tau, step=n, lam=lam,
+                           err_vs_oracle=err, bound=b, err_vs_analytic=err_exact,
+                           oracle_err_vs_analytic=oracle_exact))
+        assert err <= b, (storage, vset, N, tau, n, err, b)
+    lat.close()
+
+
+@pytest.mark.parametrize("storage", ["dev_f32", "dev_f16", "dev_bf16", "f32"])
+@pytest.mark.parametrize("tau", [0.55, 0.8, 1.5, 4.5])
+@pytest.mark.parametrize("N", [64, 256])
+def test_reduced_precision_1d_within_stated_bound(L, oracle_mod, storage, tau, N):
+    # at tau <= 0.8 the 16-bit runs overflow between steps 10 and 64
+    check(L, oracle_mod, storage, 1, N, tau, [1, 10] if tau < 1 else [1, 10, 32])
+
+
+@pytest.mark.parametrize("storage", ["dev_f32", "dev_f16", "dev_bf16", "f32"])
+@pytest.mark.parametrize("tau", [0.55, 1.5])
+def test_reduced_precision_3d_within_stated_bound(L, oracle_mod, storage, tau):
+    check(L, oracle_mod, storage, 3, 64, tau, [1, 10] if tau < 1 else [1, 10, 32])
+
+
+@pytest.mark.parametrize("storage", ["dev_f32", "dev_f16", "dev_bf16", "f32"])
+def test_reduced_precision_full_size_256cubed(L, oracle_mod, storage):
+    """The precision configuration at full size: 256^3, A = 0.01, tau = 1.5,
+    1 and 10 steps, every cell against the 1D oracle at N = 256."""
+    check(L, oracle_mod, storage, 3, 256, 1.5, [1, 10])
+
+
+def test_deviation_fp32_keeps_the_fp64_analytic_error(L, oracle_mod):
+    """At the paper's tau = 4.5 over one crossing time (256 steps at N = 256),
+    FP32 deviation storage is as close to the analytic solution as the FP64
+    oracle, within 1 % (the scheme's own error dominates its rounding)."""
+    N, tau, n = 256, 4.5, 256
+    ref = oracle_moments(oracle_mod, N, tau, [n])[n]
+    exact = W.gauge_wave((N, 1, 1), 1 / N, A, t=n / N).reshape(16, N)
+    lat = L.Lattice(1, (N, 1, 1), tau, 1 / N, storage="dev_f32")
+    lat.init(W.gauge_wave((N, 1, 1), 1 / N, A))
+    lat.step(n)
+    m = lat.moments().reshape(16, N)
+    e64 = np.abs(ref - exact).max() / A
+    e32 = np.abs(m - exact).max() / A
+    REPORT.append(dict(storage="dev_f32", vset=1, N=N, tau=tau, step=n, err_vs_analytic=e32,
+                       oracle_err_vs_analytic=e64))
+    assert abs(e32 - e64) <= 1e-2 * e64, (e32, e64)
+    lat.close()
