@@ -42,14 +42,33 @@ sys.path.insert(0, ROOT)
 from paper_1505_02037_gb300 import workloads as W  # noqa: E402
 
 WORKLOADS = {
-    # name: (vset, N, storage, direction, A)
+    # name: (vset, N, storage, direction, A[, wave, streaming])
     "gauge3d-256-f32": (3, 256, "f32", "x", 0.1),
     "gauge3d-256-dev_bf16": (3, 256, "dev_bf16", "x", 0.1),
     "gauge3d-256-dev_f16": (3, 256, "dev_f16", "x", 0.1),
     "gauge3d-256-dev_f32": (3, 256, "dev_f32", "x", 0.1),
+    "gauge3d-256-f64": (3, 256, "f64", "x", 0.1),
     "gauge3d-128-f64": (3, 128, "f64", "x", 0.1),
     "gauge3d-128-f64-diag": (3, 128, "f64", "xyz", 0.1),
+    # the largest configuration's lattice: 384^3, one 68.9 GB buffer, in place
+    "linear3d-384-dev_f32-aa": (3, 384, "dev_f32", "xyz", 1e-6, "linear", "aa"),
 }
+
+
+def workload(name):
+    t = WORKLOADS[name]
+    vset, N, storage, direction, A = t[:5]
+    wave = t[5] if len(t) > 5 else "gauge"
+    streaming = t[6] if len(t) > 6 else "auto"
+    return vset, N, storage, direction, A, wave, streaming
+
+
+def fields_for(wave, shape, dx, A, direction):
+    if wave == "linear":
+        return W.linear_wave(shape, dx, A, direction=direction)
+    return W.gauge_wave(shape, dx, A, direction=direction)
+
+
 BYTES = {"f64": 8, "f32": 4, "dev_f32": 4, "dev_bf16": 2, "dev_f16": 2}
 DTYPE = {"f64": "f64", "f32": "f32", "dev_f32": "f32", "dev_bf16": "f32 (bf16 storage)",
          "dev_f16": "f32 (f16 storage)"}
@@ -168,14 +187,14 @@ def traffic_for(kernel_key, cells):
     return e["dram_bytes_per_cell"] * cells
 
 
-def cpu_baseline(vset, storage, direction, A, tau, seconds=12.0):
+def cpu_baseline(vset, storage, direction, A, tau, wave="gauge", seconds=12.0):
     """The FP64 oracle as it stands, on this host's cores, on a bounded sample
     of the same workload (a 48^3 periodic piece of the same wave, same tau)."""
     from oracle import oracle as O
     n = 48
     shape = (n, n, n) if vset == 3 else (n, n, 1)
-    o = O.Oracle(vset, shape, tau, 1 / n)
-    f = o.init(W.gauge_wave(shape, 1 / n, A, direction=direction))
+    o = O.Oracle(vset, shape, tau, 1 / n, slicing=0 if wave == "linear" else 1)
+    f = o.init(fields_for(wave, shape, 1 / n, A, direction))
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     steps, t0 = 0, time.perf_counter()
     while True:
@@ -187,14 +206,14 @@ def cpu_baseline(vset, storage, direction, A, tau, seconds=12.0):
     cells = n ** 3 if vset == 3 else n * n
     return {"value": cells * 16 * steps / el / 1e6, "unit": "Mcell*var/s", "cores": cores,
             "kind": "oracle",
-            "sample": f"FP64 oracle, D3Q19 {n}^3 periodic gauge wave (A={A}, tau={tau}), "
+            "sample": f"FP64 oracle, D3Q19 {n}^3 periodic {wave} wave (A={A}, tau={tau}), "
                       f"{steps} steps in {el:.1f} s on {cores} host threads"}
 
 
 def workload_config(args, streaming_name="ping-pong"):
-    vset, N, storage, direction, A = WORKLOADS[args.workload]
+    vset, N, storage, direction, A, wave, _ = workload(args.workload)
     return {
-        "workload": f"3D gauge wave along {direction}, D3Q19 {N}^3 periodic, "
+        "workload": f"3D {wave} wave along {direction}, D3Q19 {N}^3 periodic, "
                     f"{storage} storage, A={A}, tau={args.tau}, {streaming_name} streaming",
         "workload_key": args.workload, "cells": N ** 3, "fields": 16, "velocities": 19,
         "tau_note": "tau=0.6 of the configuration is linearly unstable for this scheme "
@@ -206,14 +225,14 @@ def workload_config(args, streaming_name="ping-pong"):
 def run_reference(args):
     """Reference arm: the FP64 oracle timed on the host cores, each step a
     bounded sample (one oracle step on a 24^3 piece of the workload)."""
-    vset, N, storage, direction, A = WORKLOADS[args.workload]
+    vset, N, storage, direction, A, wave, _ = workload(args.workload)
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from oracle import oracle as O
     n = 24
-    o = O.Oracle(vset, (n, n, n), args.tau, 1 / n)
-    f = o.init(W.gauge_wave((n, n, n), 1 / n, A, direction=direction))
+    o = O.Oracle(vset, (n, n, n), args.tau, 1 / n, slicing=0 if wave == "linear" else 1)
+    f = o.init(fields_for(wave, (n, n, n), 1 / n, A, direction))
     for _ in range(args.warmup):
         f = o.step(f)
     t0 = time.perf_counter()
@@ -464,12 +483,15 @@ def main():
     torch.cuda.set_device(dev)
     from paper_1505_02037_gb300 import lbnr
 
-    vset, N, storage, direction, A = WORKLOADS[args.workload]
+    vset, N, storage, direction, A, wave, streaming = workload(args.workload)
     shape = (N, N, N)
     cells = N ** 3
     Q = 19
-    fields = W.gauge_wave(shape, 1 / N, A, direction=direction).reshape(16, cells)
-    lat = lbnr.Lattice(vset, shape, args.tau, 1 / N, storage=storage)
+    fields = fields_for(wave, shape, 1 / N, A, direction).reshape(16, cells)
+    lat = lbnr.Lattice(vset, shape, args.tau, 1 / N, storage=storage,
+                       slicing=lbnr.LBNR_GEODESIC if wave == "linear" else lbnr.LBNR_HARMONIC,
+                       streaming={"auto": lbnr.LBNR_STREAM_AUTO,
+                                  "aa": lbnr.LBNR_STREAM_AA}[streaming])
     lat.init(fields)
 
     def barrier():
@@ -572,7 +594,7 @@ def main():
                        "steps_per_transfer": k}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(vset, storage, direction, A, args.tau)
+        line["cpu_baseline"] = cpu_baseline(vset, storage, direction, A, args.tau, wave)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
