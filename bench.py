@@ -99,6 +99,20 @@ def parse():
     return a
 
 
+def over_ranks(elapsed, units, world, device):
+    """Whole-job totals of a timed region: the largest elapsed time over
+    ranks and the sum of the units every rank processed (one all-reduce
+    each; a no-op on one rank). Returns (elapsed_max, units_sum)."""
+    import torch
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -389,15 +403,7 @@ def main_batched(args):
     rc, per = b.status()
     taken = np.array([b.steps_done(i) for i in range(len(specs))], dtype=np.int64)
     units = float(sum(c * 16 * t for c, t in zip(cells, taken)))
-    t = torch.tensor([ms, units], device=dev, dtype=torch.float64)
-    if world > 1:
-        tm = t[:1].clone()
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        tu = t[1:].clone()
-        dist.all_reduce(tu, op=dist.ReduceOp.SUM)
-        ms_max, units_all = float(tm.item()), float(tu.item())
-    else:
-        ms_max, units_all = ms, units
+    ms_max, units_all = over_ranks(ms, units, world, dev)
     qs = [3 if r["vset"] == 1 else 9 for r in specs]
     alg = float(sum(c * t * (2 * 16 * q * 4 + 7 * 4) for c, t, q in zip(cells, taken, qs)))
     peaks, peak_kind = measured_peaks()
@@ -443,13 +449,7 @@ def main_batched(args):
         el = time.perf_counter() - t0
         taken2 = np.array([b.steps_done(i) for i in range(len(specs))], dtype=np.int64)
         u2 = float(sum(c * 16 * t for c, t in zip(cells, taken2)))
-        tt = torch.tensor([el, u2], device=dev, dtype=torch.float64)
-        if world > 1:
-            a_ = tt[:1].clone()
-            dist.all_reduce(a_, op=dist.ReduceOp.MAX)
-            b_ = tt[1:].clone()
-            dist.all_reduce(b_, op=dist.ReduceOp.SUM)
-            el, u2 = float(a_.item()), float(b_.item())
+        el, u2 = over_ranks(el, u2, world, dev)
         line["e2e"] = {"value": u2 / el / 1e6, "unit": "Mcell*var/s",
                        "h2d_bytes_per_step": host.numel() * 8 / args.steps,
                        "d2h_bytes_per_step": len(specs) * (4 + 8) / args.steps}
@@ -518,10 +518,7 @@ def main():
         e1.record(stream)
         barrier()
     ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max, units_all = over_ranks(ms, cells * 16 * args.steps, world, dev)
     finite = True
     try:
         lat.status()
@@ -542,7 +539,7 @@ def main():
     achieved = alg_collide / (col_ms * 1e-3) / 1e9
     traffic = traffic_for(f"k_collide:{args.workload}:{lat.variants[lat.variant]}", cells)
 
-    value = world * cells * 16 * args.steps / (ms_max * 1e-3) / 1e6
+    value = units_all / (ms_max * 1e-3) / 1e6
     line = {
         "metric": "lattice updates/s", "value": value, "unit": "Mcell*var/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -584,11 +581,8 @@ def main():
             pass
         barrier()
         el = time.perf_counter() - t0
-        tt = torch.tensor([el], device=dev)
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        el = float(tt.item())
-        line["e2e"] = {"value": world * cells * 16 * k / el / 1e6, "unit": "Mcell*var/s",
+        el, u_e2e = over_ranks(el, cells * 16 * k, world, dev)
+        line["e2e"] = {"value": u_e2e / el / 1e6, "unit": "Mcell*var/s",
                        "h2d_bytes_per_step": hf.numel() * 8 / k,
                        "d2h_bytes_per_step": hout.numel() * 8 / k,
                        "steps_per_transfer": k}
