@@ -29,6 +29,7 @@ struct VariantTable;
   struct VariantTable<Q_, SB_> {                             \
     static constexpr VariantSpec v[] = {__VA_ARGS__};        \
     static constexpr int n = sizeof(v) / sizeof(v[0]);       \
+    static_assert(n <= 8, "at most 8 launch forms");         \
     static constexpr int fallback = FALLBACK_;               \
   };
 // FP64 storage (FP64 arithmetic)
@@ -176,6 +177,15 @@ struct Impl {
 
   template <int LAYOUT>
   static cudaError_t collide_layout(const LaunchCtx& L, int variant, const StepArgs<S, C>& a) {
+    if constexpr (VT::n > 7) {
+      if (variant == 7) return launch_variant<LAYOUT, 7>(L, a);
+    }
+    if constexpr (VT::n > 6) {
+      if (variant == 6) return launch_variant<LAYOUT, 6>(L, a);
+    }
+    if constexpr (VT::n > 5) {
+      if (variant == 5) return launch_variant<LAYOUT, 5>(L, a);
+    }
     if constexpr (VT::n > 4) {
       if (variant == 4) return launch_variant<LAYOUT, 4>(L, a);
     }

@@ -2,9 +2,13 @@
 
   python -m paper_1505_02037_gb300.profile_step --storage f32 --n 128 \
       --variant 3 --steps 4 [--vset 3] [--tau 4.5] [--streaming 1]
+  python -m paper_1505_02037_gb300.profile_step --batch 16 --vset 2 --n 256 \
+      --storage dev_f32 --steps 16 [--block 256 --per-sm 1]
 
 Prints the per-kernel milliseconds of the timed steps (CUDA events). Used to
-capture ncu reports of a single kernel on a small case.
+capture ncu reports of a single kernel on a small case. With --batch R the
+batched ensemble kernel advances R copies of the wave (tau 2.0) by --steps
+steps in each of four launches.
 """
 from __future__ import annotations
 
@@ -24,7 +28,12 @@ def main(argv=None):
     p.add_argument("--vset", type=int, default=3)
     p.add_argument("--tau", type=float, default=4.5)
     p.add_argument("--streaming", type=int, default=1)
+    p.add_argument("--batch", type=int, default=0)
+    p.add_argument("--block", type=int, default=256)
+    p.add_argument("--per-sm", type=int, default=1)
     a = p.parse_args(argv)
+    if a.batch:
+        return batch_main(a)
     n = a.n
     shape = (n, n, n) if a.vset == 3 else ((n, n, 1) if a.vset == 2 else (n, 1, 1))
     lat = lbnr.Lattice(a.vset, shape, a.tau, 1 / n, storage=a.storage, streaming=a.streaming)
@@ -38,6 +47,33 @@ def main(argv=None):
     ms = lat.step_timed(4)
     print(f"{a.storage} n={n} vset={a.vset} {lat.variants[a.variant]}: "
           f"ms per step aux {ms[0] / 4:.4f} collide {ms[1] / 4:.4f}")
+    return 0
+
+
+def batch_main(a):
+    import torch
+    n = a.n
+    shape = (n, n, 1) if a.vset == 2 else (n, 1, 1)
+    runs = [dict(vset=a.vset, shape=shape, tau=2.0, dx=1 / n, steps=a.steps)
+            for _ in range(a.batch)]
+    b = lbnr.Batch(runs, storage=a.storage, block=a.block, ctas_per_sm=a.per_sm)
+    f = W.gauge_wave(shape, 1 / n, 0.01)
+    for i in range(a.batch):
+        b.init(i, f)
+    times = []
+    with torch.cuda.stream(b.stream):
+        for _ in range(4):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(b.stream)
+            b.run()
+            e1.record(b.stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+    b.check()
+    p = b.plan()
+    print(f"batch {a.batch} x {shape} {a.storage}: grid {p['grid']} x {p['block']}, "
+          f"ms per launch of {a.steps} steps: " + " ".join(f"{t:.3f}" for t in times))
     return 0
 
 
