@@ -266,3 +266,33 @@ def test_batch_replan_drops_stopped_runs_and_keeps_bits(L):
     assert b1.plan()["teams"][0] == 1
     b1.close()
     b2.close()
+
+
+def test_ensemble_configuration_first_16_runs(L, oracle_mod):
+    """The ensemble configuration itself (seed 150502037): its first 16 runs,
+    24 steps each. In FP64 every run equals the oracle's run to the FP64 bar;
+    in FP32 deviation storage (the configuration's storage) every run equals,
+    bit for bit, the same run stepped on its own context in the
+    one-thread-per-cell form."""
+    runs = W.ensemble(seed=150502037)[:16]
+    for r in runs:
+        r["steps"] = 24
+    b64 = make_batch(L, runs, storage="f64")
+    b64.run()
+    b32 = make_batch(L, runs, storage="dev_f32")
+    b32.run()
+    assert b64.check() == [0] * 16 and b32.check() == [0] * 16
+    for i, r in enumerate(runs):
+        o = oracle_mod.Oracle(r["vset"], r["shape"], r["tau"], r["dx"])
+        f0 = o.init(W.ensemble_fields(r))
+        f = o.run(f0, 24)
+        kscale = math.pi * r["A"]
+        spread = dist_err(o.run(perturbed(f0), 24), f, kscale).max()
+        err = dist_err(b64.distributions(i), f, kscale).max()
+        assert err <= max(TOL64, 4 * spread), (i, r["shape"], r["tau"], err, spread)
+        lat = single_context(L, r, "dev_f32", variant=("P1-reread", "P1-hold"))
+        lat.step(24)
+        assert np.array_equal(b32.distributions(i), lat.distributions()), i
+        lat.close()
+    b64.close()
+    b32.close()
