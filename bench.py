@@ -187,6 +187,19 @@ def source_hash(files=COLLIDE_SOURCES):
     return h.hexdigest()[:16]
 
 
+def profile_entry(kernel_key, field):
+    """A per-cell figure from the committed ncu summaries, if it was taken on
+    the current kernel sources (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            e = json.load(f).get(kernel_key)
+    except OSError:
+        return None
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get(field)
+
+
 def traffic_for(kernel_key, cells):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel sources (else None)."""
@@ -537,7 +550,24 @@ def main():
     # burst figure: the kernel is timed as one launch of a few milliseconds
     peak = float(peaks["hbm_gbs"])
     achieved = alg_collide / (col_ms * 1e-3) / 1e9
-    traffic = traffic_for(f"k_collide:{args.workload}:{lat.variants[lat.variant]}", cells)
+    tkey = f"k_collide:{args.workload}:{lat.variants[lat.variant]}"
+    traffic = traffic_for(tkey, cells)
+    hbm_roofline = {"bound": "hbm", "kernel": "k_collide (fused collide-and-stream)",
+                    "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "peak_source": f"hbm_gbs of {peak_kind}",
+                    "algorithmic_bytes_per_cell": alg_collide / cells,
+                    "avg_launch_ms": col_ms, "traffic": traffic}
+    roofline = hbm_roofline
+    flops = profile_entry(tkey, "fp64_flops_per_cell") if storage == "f64" else None
+    if flops is not None:
+        # FP64 is bound by the FP64 pipes: 152 SMs x 2 FP64 FMA per clock x
+        # 2 flops x 2.07 GHz = 1.26 TFLOP/s nominal
+        fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12
+        ach = flops * cells / (col_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "kernel": "k_collide (fused collide-and-stream, FP64)",
+                    "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
+                    "peak_source": "FP64 units x clock (nominal)", "flops_per_cell": flops,
+                    "avg_launch_ms": col_ms, "traffic": traffic, "hbm": hbm_roofline}
 
     value = units_all / (ms_max * 1e-3) / 1e6
     line = {
@@ -550,11 +580,7 @@ def main():
             l2=f"inputs larger than L2 ({lat.workspace.numel() / 1e9:.1f} GB working set)",
             state_finite_after_run=finite,
             parallelism="replicas" if world > 1 else "single GPU"),
-        "roofline": {"bound": "hbm", "kernel": "k_collide (fused collide-and-stream)",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_source": f"hbm_gbs of {peak_kind}",
-                     "algorithmic_bytes_per_cell": alg_collide / cells,
-                     "avg_launch_ms": col_ms, "traffic": traffic},
+        "roofline": roofline,
         "kernels_ms_per_step": {"k_aux": aux_ms, "k_collide": col_ms,
                                 "k_aux_frac_of_peak": alg_aux / (aux_ms * 1e-3) / 1e9 / peak},
         "step_algorithmic_hbm_frac": (alg_collide + alg_aux) / (ms_max / args.steps * 1e-3)
