@@ -538,6 +538,15 @@ def main():
     except lbnr.NonFiniteError:
         finite = False
 
+    # constraint monitor (FP64 moments, corrections, H/M/C norms and the 16
+    # lattice sums), a call made every m steps outside the step itself
+    lat.constraints()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        lat.constraints()
+    monitor_ms = (time.perf_counter() - t0) / 3 * 1e3
+
     # per-kernel durations (same steps, one launch at a time, events around each)
     ms_aux, ms_col = lat.step_timed(args.profile_steps)
     col_ms = ms_col / args.profile_steps
@@ -585,6 +594,7 @@ def main():
                                 "k_aux_frac_of_peak": alg_aux / (aux_ms * 1e-3) / 1e9 / peak},
         "step_algorithmic_hbm_frac": (alg_collide + alg_aux) / (ms_max / args.steps * 1e-3)
                                      / 1e9 / peak,
+        "constraint_monitor_ms_per_call": monitor_ms,
         "gpu_launches": 2 * args.steps,
         "launch_form": lat.variants[lat.variant],
         "autotune_ms_per_collide": tuning,
