@@ -159,3 +159,28 @@ def test_deviation_fp32_keeps_the_fp64_analytic_error(L, oracle_mod):
                        oracle_err_vs_analytic=e64))
     assert abs(e32 - e64) <= 1e-2 * e64, (e32, e64)
     lat.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "dev_f32"])
+def test_every_launch_form_at_full_size(L, oracle_mod, storage):
+    """The benchmark's 256^3 lattice in every launch form the autotuner may
+    pick (so whichever one a bench run times is covered): 2 steps from the
+    gauge wave, every cell against the 1D oracle at N = 256, within the stated
+    bound."""
+    N, tau, n = 256, 4.5, 2
+    lam = amplification(oracle_mod, tau)
+    ref = oracle_moments(oracle_mod, N, tau, [n])[n]
+    b = bound(storage, True, N, tau, n, lam)
+    fields = W.gauge_wave((N, N, N), 1 / N, A)
+    lat = L.Lattice(3, (N, N, N), tau, 1 / N, storage=storage, streaming=L.LBNR_STREAM_PINGPONG)
+    for v, name in enumerate(lat.variants):
+        lat.set_variant(v)
+        lat.init(fields)
+        lat.step(n)
+        lat.status()
+        m = lat.moments().reshape(16, -1, N)
+        err = float(np.abs(m - ref[:, None, :]).max() / A)
+        REPORT.append(dict(storage=storage, vset=3, N=N, tau=tau, step=n, form=name,
+                           err_vs_oracle=err, bound=b))
+        assert err <= b, (name, err, b)
+    lat.close()
