@@ -63,6 +63,14 @@ typedef struct {
   int32_t pad;
   int64_t nx, ny, nz;
   double dx, dt, tau;
+  /* Matter (Sec. "Expansion of flat universe"): a perfect fluid at rest in
+   * the slice frame with energy density rho(t) = fluid_rho0 (fluid_t0/t)^2
+   * and pressure P = fluid_w rho, prescribed, not evolved. t is the time of
+   * the state a call reads (the caller advances it). fluid_on = 0: vacuum. */
+  double t;
+  int32_t fluid_on;
+  int32_t pad2;
+  double fluid_rho0, fluid_w, fluid_t0;
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -184,8 +192,9 @@ static double kdelta(int a, int b) { return a == b ? 1.0 : 0.0; }
 
 /* Evaluates lambda^k_ij, S_ij, Omega_k and the lapse and metric sources at
  * one point, following the paper's equations term by term, with zero shift
- * and vacuum (reading R7). */
-static void bm_point(const bm_state* s, int slicing, bm_rhs* r) {
+ * (reading R7). Matter: a perfect fluid at rest in the slice frame with
+ * energy density rho and pressure P (both 0 in vacuum). */
+static void bm_point(const bm_state* s, int slicing, double rho, double P, bm_rhs* r) {
   double gi[3][3];
   inverse3(s->g, gi);
   const double a = s->alpha;
@@ -298,12 +307,24 @@ static void bm_point(const bm_state* s, int slicing, bm_rhs* r) {
   for (int k = 0; k < 3; ++k) DD += Dtr1[k] * Dtr1up[k];
   double VA = 0; /* V^k A_k */
   for (int k = 0; k < 3; ++k) VA += Vup[k] * s->A[k];
-  const double bracket = -DG + DD - 2 * VA + trK2 - trK * trK;
+  /* Matter (Sec. "Expansion of flat universe"): G_ij = P gamma_ij,
+   * G_00 = rho alpha^2 (so alpha^2 G^00 = rho), G^0_k = 0 for a fluid at
+   * rest; R^(4)_ij = G_ij - gamma_ij/2 (-alpha^2 G^00 + tr G). */
+  double Gdn[3][3], trG = 0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) Gdn[i][j] = P * s->g[i][j];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) trG += gi[i][j] * Gdn[i][j];
+  const double G00up = rho / (a * a);
+  double R4[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) R4[i][j] = Gdn[i][j] - 0.5 * s->g[i][j] * (-a * a * G00up + trG);
+  const double bracket = -DG + DD - 2 * VA + trK2 - trK * trK + 2 * a * a * G00up;
 
   /* S_ij. */
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
-      double t = 0;
+      double t = -R4[i][j];
       /* -2 K_i^k K_kj + tr K K_ij (K_i^k = K_im g^{mk} = Kmix[k][i]) */
       for (int k = 0; k < 3; ++k) t += -2 * Kmix[k][i] * s->K[k][j];
       t += trK * s->K[i][j];
@@ -329,7 +350,7 @@ static void bm_point(const bm_state* s, int slicing, bm_rhs* r) {
       r->S_K[i][j] = a * t;
     }
 
-  /* Omega_k (Eq. Vsor), zero shift and vacuum:
+  /* Omega_k (Eq. Vsor), zero shift, fluid at rest (alpha^2 G^0_k = 0):
    * alpha [ A_r (K^r_k - trK delta^r_k) + (D_kr^s - 2 D_rk^s) K^r_s
    *         - K^r_k (D_rs^s - 2 D^j_jr) ]. */
   for (int k = 0; k < 3; ++k) {
@@ -355,8 +376,8 @@ static void bm_point(const bm_state* s, int slicing, bm_rhs* r) {
  * K[6], V[3], A[3], D[3][6] (stored pairs); outputs lam[3][6] (lambda^k_ij),
  * Sij[6] (S_ij without alpha), Omega[3], and the lapse source. */
 void orc_bm_point(double alpha, const double* g6, const double* K6, const double* V3,
-                  const double* A3, const double* D18, int slicing, double* lam18,
-                  double* S6, double* Om3, double* S_alpha) {
+                  const double* A3, const double* D18, int slicing, double rho, double P,
+                  double* lam18, double* S6, double* Om3, double* S_alpha) {
   bm_state s;
   bm_rhs r;
   s.alpha = alpha;
@@ -370,7 +391,7 @@ void orc_bm_point(double alpha, const double* g6, const double* K6, const double
     s.V[k] = V3[k];
     s.A[k] = A3[k];
   }
-  bm_point(&s, slicing, &r);
+  bm_point(&s, slicing, rho, P, &r);
   for (int k = 0; k < 3; ++k)
     for (int p = 0; p < 6; ++p) lam18[6 * k + p] = r.lam[k][PAIR_I[p]][PAIR_J[p]];
   for (int p = 0; p < 6; ++p) S6[p] = r.S_ij[PAIR_I[p]][PAIR_J[p]];
@@ -403,6 +424,7 @@ static int check_params(const orc_params* p, vset_t* vs) {
   if (p->vset == 1 && (p->ny != 1 || p->nz != 1)) return -1;
   if (p->vset == 2 && p->nz != 1) return -1;
   if (!(p->tau > 0.5) || !(p->dx > 0) || !(p->dt > 0)) return -1;
+  if (p->fluid_on && (!(p->t > 0) || !(p->fluid_t0 > 0))) return -1;
   return 0;
 }
 
@@ -429,6 +451,16 @@ static void derivatives(const orc_params* p, const double* rho, int64_t cells,
         D[k][i][j] = (rho[(F_G + q) * cells + cp] - rho[(F_G + q) * cells + cm]) / (4 * p->dx);
       }
   }
+}
+
+/* Fluid density and pressure at the time of the state a call reads. */
+static void matter_now(const orc_params* p, double* rho, double* P) {
+  *rho = 0;
+  *P = 0;
+  if (!p->fluid_on) return;
+  const double q = p->fluid_t0 / p->t;
+  *rho = p->fluid_rho0 * q * q;
+  *P = p->fluid_w * *rho;
 }
 
 /* Unpacks the 16 stored values into a bm_state (derivatives added apart). */
@@ -467,6 +499,8 @@ static void pack_fluxes(const bm_rhs* r, double alpha, double Fl[ORC_NF][3]) {
 static void cell_macro(const orc_params* p, const double* mom, int64_t cells, int64_t c,
                        double rt[ORC_NF], double S[ORC_NF], double rho[ORC_NF],
                        double Fl[ORC_NF][3]) {
+  double mrho, mP;
+  matter_now(p, &mrho, &mP);
   int64_t x, y, z;
   cell_coords(p, c, &x, &y, &z);
   for (int F = 0; F < ORC_NF; ++F) rt[F] = mom[F * cells + c];
@@ -474,7 +508,7 @@ static void cell_macro(const orc_params* p, const double* mom, int64_t cells, in
   bm_rhs r;
   derivatives(p, mom, cells, x, y, z, s.A, s.D);
   unpack_fields(rt, &s);
-  bm_point(&s, p->slicing, &r);
+  bm_point(&s, p->slicing, mrho, mP, &r);
   pack_sources(&r, S);
   if (!p->sources_on)
     for (int F = 0; F < ORC_NF; ++F) S[F] = 0;
@@ -482,7 +516,7 @@ static void cell_macro(const orc_params* p, const double* mom, int64_t cells, in
   for (int F = 0; F < ORC_NF; ++F) rho[F] = rt[F] + 0.5 * p->dt * S[F];
   /* Flux at the corrected moments with the same derivatives (R5). */
   unpack_fields(rho, &s);
-  bm_point(&s, p->slicing, &r);
+  bm_point(&s, p->slicing, mrho, mP, &r);
   pack_fluxes(&r, rho[F_ALPHA], Fl);
 }
 
@@ -507,6 +541,8 @@ static void all_moments(const vset_t* vs, int64_t cells, const double* f, double
 int orc_init(const orc_params* p, const double* fields, double* f_out) {
   vset_t vs;
   if (check_params(p, &vs)) return -1;
+  double mrho, mP;
+  matter_now(p, &mrho, &mP);
   const int64_t cells = p->nx * p->ny * p->nz;
   int bad = 0;
 #pragma omp parallel for schedule(static) reduction(| : bad)
@@ -519,7 +555,7 @@ int orc_init(const orc_params* p, const double* fields, double* f_out) {
     bm_rhs r;
     derivatives(p, fields, cells, x, y, z, s.A, s.D);
     unpack_fields(v, &s);
-    bm_point(&s, p->slicing, &r);
+    bm_point(&s, p->slicing, mrho, mP, &r);
     pack_sources(&r, S);
     if (!p->sources_on)
       for (int F = 0; F < ORC_NF; ++F) S[F] = 0;
@@ -579,10 +615,13 @@ int orc_step(const orc_params* p, const double* f_in, double* f_out) {
   return bad ? -4 : 0;
 }
 
-/* n steps, alternating two caller-owned buffers; the result ends in f_io. */
+/* n steps, alternating two caller-owned buffers; the result ends in f_io.
+ * The state's time advances by dt per step from p->t. */
 int orc_run(const orc_params* p, double* f_io, double* scratch, int64_t n) {
+  orc_params q = *p;
   for (int64_t i = 0; i < n; ++i) {
-    int rc = orc_step(p, f_io, scratch);
+    int rc = orc_step(&q, f_io, scratch);
+    q.t += q.dt;
     if (rc) return rc;
     vset_t vs;
     get_vset(p->vset, &vs);
@@ -617,6 +656,8 @@ int orc_step_cells(const orc_params* p, const double* f_in, int64_t n, const int
                    double* out) {
   vset_t vs;
   if (check_params(p, &vs)) return -1;
+  double mrho, mP;
+  matter_now(p, &mrho, &mP);
   const int64_t cells = p->nx * p->ny * p->nz;
   int bad = 0;
 #pragma omp parallel for schedule(dynamic) reduction(| : bad)
@@ -652,13 +693,13 @@ int orc_step_cells(const orc_params* p, const double* f_in, int64_t n, const int
           }
       }
       unpack_fields(rt, &s);
-      bm_point(&s, p->slicing, &r);
+      bm_point(&s, p->slicing, mrho, mP, &r);
       pack_sources(&r, S);
       if (!p->sources_on)
         for (int F = 0; F < ORC_NF; ++F) S[F] = 0;
       for (int F = 0; F < ORC_NF; ++F) rho[F] = rt[F] + 0.5 * p->dt * S[F];
       unpack_fields(rho, &s);
-      bm_point(&s, p->slicing, &r);
+      bm_point(&s, p->slicing, mrho, mP, &r);
       pack_fluxes(&r, rho[F_ALPHA], Fl);
       const double src_fac = 1.0 - 1.0 / (2.0 * p->tau);
       for (int F = 0; F < ORC_NF; ++F) {

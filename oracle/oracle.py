@@ -44,6 +44,12 @@ class Params(ctypes.Structure):
         ("dx", ctypes.c_double),
         ("dt", ctypes.c_double),
         ("tau", ctypes.c_double),
+        ("t", ctypes.c_double),
+        ("fluid_on", ctypes.c_int32),
+        ("pad2", ctypes.c_int32),
+        ("fluid_rho0", ctypes.c_double),
+        ("fluid_w", ctypes.c_double),
+        ("fluid_t0", ctypes.c_double),
     ]
 
 
@@ -72,7 +78,7 @@ def lib():
             L.orc_vset.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp]
             L.orc_vset.restype = ctypes.c_int
             L.orc_bm_point.argtypes = [ctypes.c_double, dp, dp, dp, dp, dp, ctypes.c_int,
-                                       dp, dp, dp, dp]
+                                       ctypes.c_double, ctypes.c_double, dp, dp, dp, dp]
             L.orc_bm_point.restype = None
             for name in ("orc_init", "orc_step", "orc_moments"):
                 getattr(L, name).argtypes = [pp, dp, dp]
@@ -116,8 +122,9 @@ def velocity_set(vset: int):
     return np.array(c[: 3 * Q]).reshape(Q, 3), w[:Q].copy()
 
 
-def bm_point(alpha, g6, K6, V3, A3, D18, slicing=1):
-    """Pointwise lambda^k_ij [3,6], S_ij [6], Omega_k [3], lapse source."""
+def bm_point(alpha, g6, K6, V3, A3, D18, slicing=1, rho=0.0, P=0.0):
+    """Pointwise lambda^k_ij [3,6], S_ij [6], Omega_k [3], lapse source; rho
+    and P are the density and pressure of a fluid at rest (0: vacuum)."""
     g6, K6, V3, A3, D18 = (np.ascontiguousarray(np.asarray(v, dtype=np.float64))
                            for v in (g6, K6, V3, A3, D18))
     lam = np.zeros(18)
@@ -125,15 +132,21 @@ def bm_point(alpha, g6, K6, V3, A3, D18, slicing=1):
     Om = np.zeros(3)
     Sa = ctypes.c_double(0)
     lib().orc_bm_point(float(alpha), _dp(g6), _dp(K6), _dp(V3), _dp(A3), _dp(D18.reshape(-1)),
-                       int(slicing), _dp(lam), _dp(S), _dp(Om), ctypes.byref(Sa))
+                       int(slicing), float(rho), float(P), _dp(lam), _dp(S), _dp(Om),
+                       ctypes.byref(Sa))
     return lam.reshape(3, 6), S, Om, Sa.value
 
 
 class Oracle:
     """One lattice configuration: vset 1/2/3, grid (nx, ny, nz), tau (the
-    dimensionless tau/dt), dx = dt, slicing 0/1/2, sources on/off."""
+    dimensionless tau/dt), dx = dt, slicing 0/1/2, sources on/off.
 
-    def __init__(self, vset, shape, tau, dx, dt=None, slicing=1, sources_on=True):
+    fluid = (rho0, w, t0): a perfect fluid at rest with density
+    rho0 (t0/t)^2 and pressure w rho (Sec. "Expansion of flat universe"). The
+    calls then take the time t of the state they read (default t0; run()
+    advances it by dt per step)."""
+
+    def __init__(self, vset, shape, tau, dx, dt=None, slicing=1, sources_on=True, fluid=None):
         nx, ny, nz = shape
         self.vset = int(vset)
         self.Q = Q_OF[self.vset]
@@ -141,35 +154,49 @@ class Oracle:
         self.cells = nx * ny * nz
         self.p = Params(self.vset, int(slicing), int(bool(sources_on)), 0, nx, ny, nz,
                         float(dx), float(dx if dt is None else dt), float(tau))
+        self.t0 = 1.0
+        if fluid is not None:
+            rho0, w, t0 = fluid
+            self.p.fluid_on, self.p.fluid_rho0, self.p.fluid_w = 1, float(rho0), float(w)
+            self.p.fluid_t0 = self.t0 = float(t0)
+        self.p.t = self.t0
+
+    def _at(self, t):
+        self.p.t = self.t0 if t is None else float(t)
 
     def _f_shape(self):
         return (NF, self.Q, self.cells)
 
-    def init(self, fields: np.ndarray) -> np.ndarray:
+    def init(self, fields: np.ndarray, t=None) -> np.ndarray:
+        self._at(t)
         fields = np.ascontiguousarray(fields, dtype=np.float64).reshape(NF, self.cells)
         f = np.zeros(self._f_shape())
         _check(lib().orc_init(ctypes.byref(self.p), _dp(fields), _dp(f)), "init")
         return f
 
-    def step(self, f: np.ndarray) -> np.ndarray:
+    def step(self, f: np.ndarray, t=None) -> np.ndarray:
+        self._at(t)
         f = np.ascontiguousarray(f, dtype=np.float64)
         out = np.zeros(self._f_shape())
         _check(lib().orc_step(ctypes.byref(self.p), _dp(f), _dp(out)), "step")
         return out
 
-    def run(self, f: np.ndarray, n: int) -> np.ndarray:
+    def run(self, f: np.ndarray, n: int, t=None) -> np.ndarray:
+        self._at(t)
         f = np.array(f, dtype=np.float64, order="C", copy=True)
         scratch = np.zeros_like(f)
         _check(lib().orc_run(ctypes.byref(self.p), _dp(f), _dp(scratch), int(n)), "run")
         return f
 
-    def moments(self, f: np.ndarray) -> np.ndarray:
+    def moments(self, f: np.ndarray, t=None) -> np.ndarray:
+        self._at(t)
         f = np.ascontiguousarray(f, dtype=np.float64)
         out = np.zeros((NF, self.cells))
         _check(lib().orc_moments(ctypes.byref(self.p), _dp(f), _dp(out)), "moments")
         return out
 
-    def step_cells(self, f: np.ndarray, cells) -> np.ndarray:
+    def step_cells(self, f: np.ndarray, cells, t=None) -> np.ndarray:
+        self._at(t)
         f = np.ascontiguousarray(f, dtype=np.float64)
         idx = np.ascontiguousarray(np.asarray(cells, dtype=np.int64))
         out = np.zeros((len(idx), NF, self.Q))

@@ -197,3 +197,33 @@ def ensemble(nruns=512, seed=150502037, n1=(64, 4096), n2=(64, 512), tau=(0.51, 
 def ensemble_fields(spec):
     """Initial fields [16][cells] of one ensemble run (gauge wave, t = 0)."""
     return gauge_wave(spec["shape"], spec["dx"], spec["A"], direction=spec["direction"])
+
+
+def flrw_exponent(w):
+    """a(t) ~ t^q for a flat universe filled with a perfect fluid P = w rho
+    (c^2 = 8 pi G = 1): q = 2 / (3 (1 + w))."""
+    return 2.0 / (3.0 * (1.0 + w))
+
+
+def flrw_density(t, w=1.0):
+    """Energy density of that universe at time t: rho = 3 (q / t)^2 (for
+    w = 1, 1 / (3 t^2) as in Sec. "Expansion of flat universe")."""
+    q = flrw_exponent(w)
+    return 3.0 * q * q / (t * t)
+
+
+def flrw(shape, t=1.0, w=1.0):
+    """Flat expanding universe in comoving coordinates, geodesic slicing:
+    alpha = 1, gamma_ij = t^(2q) delta_ij (= t^(2/3) delta for w = 1, equal
+    to delta at t = 1), K_ij = -(1/2) d_t gamma_ij = -q t^(2q-1) delta_ij,
+    V = 0."""
+    q = flrw_exponent(w)
+    cells = int(np.prod(shape))
+    out = np.zeros((NF, cells))
+    out[0] = 1.0
+    g = t ** (2 * q)
+    k = -q * t ** (2 * q - 1)
+    for qq in (0, 3, 5):  # xx, yy, zz
+        out[1 + qq] = g
+        out[7 + qq] = k
+    return out
