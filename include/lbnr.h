@@ -145,6 +145,18 @@ int lbnr_set_distributions(lbnr_ctx* ctx, const double* in);
  * non-finite moment, else LBNR_OK. */
 int lbnr_status(lbnr_ctx* ctx);
 
+/* Matter (Sec. "Expansion of flat universe"): a homogeneous perfect fluid at
+ * rest in the slice frame, energy density rho(t) = rho0 (t0 / t)^2 (the
+ * density of a flat FLRW universe, for any equation of state) and pressure
+ * P = w rho, prescribed rather than evolved, as in the paper's test. The
+ * state after n steps is at t = t0 + n dt. It enters S_ij through
+ * -R^(4)_ij + (gamma_ij / 4) 2 alpha^2 G^00 with G_ij = P gamma_ij and
+ * alpha^2 G^00 = rho, which is (P / 2) gamma_ij; Omega_k is unchanged
+ * (G^0_k = 0). rho0 = 0 returns to vacuum. Call before lbnr_init (which
+ * evaluates the initial sources at t0); later calls take the current step
+ * as n. Errors: LBNR_EINVAL for rho0 < 0, t0 <= 0 or non-finite values. */
+int lbnr_set_fluid(lbnr_ctx* ctx, double rho0, double w, double t0);
+
 /* Thread-to-cell layouts of the collide kernel available for this context's
  * set and storage (all give the same results): their number, a short name,
  * and the selection (default 0). Used by the autotuner. */

@@ -100,8 +100,19 @@ struct lbnr_ctx {
   bool initialised = false;
   int64_t steps = 0;
   cudaGraphExec_t cycle[2] = {nullptr, nullptr};  // two-step cycle from even / odd step
+  double fluid_rho0 = 0, fluid_w = 0, fluid_t0 = 1;  // perfect fluid (rho0 = 0: vacuum)
   std::string err;
 };
+
+// Advances the device step counter that the fluid's time is read from.
+static __global__ void k_tick(int64_t* clock) { *clock += 1; }
+
+// Fluid pressure at the current state's time t0 + steps dt (0 in vacuum).
+static double fluid_pressure_now(const lbnr_ctx* c) {
+  if (!c->L.clock) return 0.0;
+  const double r = c->fluid_t0 / (c->fluid_t0 + (double)c->steps * c->dt);
+  return c->fluid_w * c->fluid_rho0 * r * r;
+}
 
 static thread_local std::string g_err;
 
@@ -211,7 +222,12 @@ cudaError_t enqueue_step(lbnr_ctx* c, int64_t parity) {
   }
   cudaError_t e = c->ops->aux(c->L, layout, fin);
   if (e != cudaSuccess) return e;
-  return c->ops->step(c->L, layout, c->variant, fin, fout);
+  e = c->ops->step(c->L, layout, c->variant, fin, fout);
+  if (e == cudaSuccess && c->L.clock) {
+    k_tick<<<1, 1, 0, c->st>>>(const_cast<int64_t*>(c->L.clock));
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 void drop_graphs(lbnr_ctx* c) {
@@ -374,6 +390,8 @@ int lbnr_create(const lbnr_grid* grid, int vset, double tau, double dx, double d
   L.stage = b + Ly.stage;
   L.st = c->st;
   L.block = 128;
+  L.clock = nullptr;
+  L.fluid_P0 = L.fluid_t0 = L.fluid_P_now = 0;
   // zero everything once: the plane padding must hold finite values
   cudaError_t e = cudaMemsetAsync(c->base, 0, Ly.total, c->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
@@ -390,6 +408,8 @@ int lbnr_init(lbnr_ctx* c, const double* fields) {
   const size_t nb = sizeof(double) * 16 * (size_t)c->L.cells;
   CUDA_TRY(c, cudaMemcpyAsync(c->L.macro, fields, nb, cudaMemcpyHostToDevice, c->st));
   CUDA_TRY(c, cudaMemsetAsync(c->L.flag, 0, sizeof(int), c->st));
+  if (c->L.clock)
+    CUDA_TRY(c, cudaMemsetAsync(const_cast<int64_t*>(c->L.clock), 0, sizeof(int64_t), c->st));
   CUDA_TRY(c, c->ops->init(c->L, c->f[0]));
   // the host array may be released as soon as we return
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
@@ -446,6 +466,10 @@ int lbnr_step_timed(lbnr_ctx* c, int64_t n, double* ms_out) {
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->st);
     if (e == cudaSuccess) e = c->ops->step(c->L, layout, c->variant, fin, fout);
     if (e == cudaSuccess) e = cudaEventRecord(ev[2], c->st);
+    if (e == cudaSuccess && c->L.clock) {
+      k_tick<<<1, 1, 0, c->st>>>(const_cast<int64_t*>(c->L.clock));
+      e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
     float a = 0, b = 0;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&a, ev[0], ev[1]);
@@ -468,6 +492,7 @@ int lbnr_moments(lbnr_ctx* c, double* out) {
   if (!c || !out) return fail(c, LBNR_EINVAL, "null argument");
   if (!c->initialised) return fail(c, LBNR_ESTATE, "moments before init");
   int64_t nb = 0;
+  c->L.fluid_P_now = fluid_pressure_now(c);
   CUDA_TRY(c, c->ops->sum64(c->L, layout_now(c), state_now(c), &nb));
   CUDA_TRY(c, c->ops->correct64(c->L));
   CUDA_TRY(c, cudaMemcpyAsync(out, c->L.macro, sizeof(double) * 16 * (size_t)c->L.cells,
@@ -482,6 +507,7 @@ int lbnr_constraints(lbnr_ctx* c, double* out) {
   if (!c || !out) return fail(c, LBNR_EINVAL, "null argument");
   if (!c->initialised) return fail(c, LBNR_ESTATE, "constraints before init");
   int64_t nbs = 0, nbc = 0;
+  c->L.fluid_P_now = fluid_pressure_now(c);
   CUDA_TRY(c, c->ops->sum64(c->L, layout_now(c), state_now(c), &nbs));
   CUDA_TRY(c, c->ops->correct64(c->L));
   CUDA_TRY(c, c->ops->constraints64(c->L, &nbc));
@@ -557,6 +583,28 @@ int lbnr_num_variants(const lbnr_ctx* c) { return c ? c->ops->nvariants : 0; }
 
 const char* lbnr_variant_name(const lbnr_ctx* c, int v) {
   return (c && v >= 0 && v < c->ops->nvariants) ? c->ops->variant_name(v) : "";
+}
+
+int lbnr_set_fluid(lbnr_ctx* c, double rho0, double w, double t0) {
+  if (!c) return fail(c, LBNR_EINVAL, "null context");
+  if (!std::isfinite(rho0) || !std::isfinite(w) || !(t0 > 0) || !std::isfinite(t0) || rho0 < 0)
+    return fail(c, LBNR_EINVAL, "fluid needs rho0 >= 0, finite w and t0 > 0");
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  c->fluid_rho0 = rho0;
+  c->fluid_w = w;
+  c->fluid_t0 = t0;
+  if (rho0 == 0) {
+    c->L.clock = nullptr;
+  } else {
+    int64_t* clock = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(c->L.flag) + 64);
+    const int64_t n = c->steps;
+    CUDA_TRY(c, cudaMemcpy(clock, &n, sizeof(n), cudaMemcpyHostToDevice));
+    c->L.clock = clock;
+  }
+  c->L.fluid_P0 = w * rho0;
+  c->L.fluid_t0 = t0;
+  drop_graphs(c);  // the captured steps carry the old parameters
+  return LBNR_OK;
 }
 
 int lbnr_set_variant(lbnr_ctx* c, int v) {

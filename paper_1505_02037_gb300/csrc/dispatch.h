@@ -25,6 +25,11 @@ struct LaunchCtx {
   int* flag;        // non-finite flag
   cudaStream_t st;
   int block;        // threads per block of the collide kernel
+  // Matter (perfect fluid at rest): pressure P0 (t0/t)^2 at t = t0 + n dt;
+  // clock points at the device step counter n (nullptr: vacuum), P_now is
+  // the pressure at the state the FP64 moment calls read.
+  const int64_t* clock;
+  double fluid_P0, fluid_t0, fluid_P_now;
 };
 
 // layout: 0 ping-pong, 1 AA at even step, 2 AA at odd step

@@ -216,6 +216,10 @@ struct Impl {
     a.sigma = C(L.dt * (1.0 - 1.0 / (2.0 * L.tau)));
     a.slicing = L.slicing;
     a.sources_on = L.sources_on;
+    a.clock = L.clock;
+    a.fluid_P0 = L.fluid_P0;
+    a.fluid_t0 = L.fluid_t0;
+    a.fluid_dt = L.dt;
     if (layout == kPingPong) return collide_layout<kPingPong>(L, variant, a);
     if (layout == kAAEven) return collide_layout<kAAEven>(L, variant, a);
     return collide_layout<kAAOdd>(L, variant, a);
@@ -243,6 +247,7 @@ struct Impl {
     a.half_dt = 0.5 * L.dt;
     a.slicing = L.slicing;
     a.sources_on = L.sources_on;
+    a.fluidP = L.clock ? L.fluid_P0 : 0.0;  // the initial state is at t0
     k_init<Q, S, REP><<<grid_for(L.cells, 128), 128, 0, L.st>>>(a);
     return cudaGetLastError();
   }
@@ -265,7 +270,7 @@ struct Impl {
     const Grid G = make_grid(L.nx, L.ny, L.nz, L.cells, L.pstride);
     k_correct64<Q><<<grid_for(L.cells, 128), 128, 0, L.st>>>(
         L.macro, L.aux64, G, 1.0 / (2.0 * L.dx), 1.0 / (4.0 * L.dx), 0.5 * L.dt, L.slicing,
-        L.sources_on);
+        L.sources_on, L.clock ? L.fluid_P_now : 0.0);
     return cudaGetLastError();
   }
 

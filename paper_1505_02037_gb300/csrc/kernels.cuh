@@ -242,7 +242,20 @@ struct StepArgs {
   C half_dt, omega, omc, sigma;  // dt/2, 1/tau, 1 - 1/tau, dt (1 - 1/(2 tau))
   int slicing;
   int sources_on;
+  // Matter: pressure P(t) = P0 (t0/t)^2 of a fluid at rest, t = t0 + n dt at
+  // step n, n read from *clock (device memory, advanced after every step);
+  // clock == nullptr is vacuum.
+  const int64_t* clock;
+  double fluid_P0, fluid_t0, fluid_dt;
 };
+
+// Pressure of the fluid at the step being taken (0 without matter).
+template <class S, class C>
+__device__ __forceinline__ C fluid_pressure(const StepArgs<S, C>& a) {
+  if (a.clock == nullptr) return C(0);
+  const double r = a.fluid_t0 / (a.fluid_t0 + (double)(*a.clock) * a.fluid_dt);
+  return C(a.fluid_P0 * r * r);
+}
 
 // A_k and D_kij by central differences of the aux planes (reading: second
 // order differences of ln alpha and gamma_ij / 2).
@@ -348,7 +361,7 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : 3) k_collide(const StepArgs<S,
   C alpha, gm[6], K[6], V[3];
   unpack<REP, C>(rt, alpha, gm, K, V);
   C Sr[kNF];
-  bm_sources<C>(alpha, gm, K, V, A, D, a.slicing, Sr);
+  bm_sources<C>(alpha, gm, K, V, A, D, a.slicing, Sr, fluid_pressure(a));
   if (!a.sources_on) {
 #pragma unroll
     for (int F = 0; F < kNF; ++F) Sr[F] = C(0);
@@ -524,7 +537,7 @@ __device__ __forceinline__ void collide_cell(const StepArgs<S, C>& a, int64_t c)
   C alpha, gm[6], K[6], V[3];
   unpack<REP, C>(rt, alpha, gm, K, V);
   C Sr[kNF];
-  bm_sources<C>(alpha, gm, K, V, A, D, a.slicing, Sr);
+  bm_sources<C>(alpha, gm, K, V, A, D, a.slicing, Sr, fluid_pressure(a));
   if (!a.sources_on) {
 #pragma unroll
     for (int F = 0; F < kNF; ++F) Sr[F] = C(0);
@@ -579,6 +592,7 @@ struct Init64Args {
   Grid G;
   double inv2dx, inv4dx, half_dt;
   int slicing, sources_on;
+  double fluidP;  // fluid pressure at the initial time (0: vacuum)
 };
 
 // Shifted equilibrium: f = f_eq(rho0) - (dt/2) w_l S(rho0), A and D from rho0.
@@ -613,7 +627,7 @@ __global__ void __launch_bounds__(128) k_init(const Init64Args<S> a) {
   double alpha, gm[6], K[6], V[3];
   unpack<kABS, double>(r, alpha, gm, K, V);
   double Sr[kNF];
-  bm_sources<double>(alpha, gm, K, V, A, D, a.slicing, Sr);
+  bm_sources<double>(alpha, gm, K, V, A, D, a.slicing, Sr, a.fluidP);
   if (!a.sources_on)
     for (int F = 0; F < kNF; ++F) Sr[F] = 0;
   double Fl[6][3];
@@ -690,7 +704,7 @@ template <int Q>
 __global__ void __launch_bounds__(128) k_correct64(double* __restrict__ macro,
                                                    const double* __restrict__ aux64, Grid G,
                                                    double inv2dx, double inv4dx, double half_dt,
-                                                   int slicing, int sources_on) {
+                                                   int slicing, int sources_on, double fluidP) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= G.cells || !sources_on) return;
   const Nbr n = make_nbr(G, c);
@@ -702,7 +716,7 @@ __global__ void __launch_bounds__(128) k_correct64(double* __restrict__ macro,
   double alpha, gm[6], K[6], V[3];
   unpack<kABS, double>(r, alpha, gm, K, V);
   double S[kNF];
-  bm_sources<double>(alpha, gm, K, V, A, D, slicing, S);
+  bm_sources<double>(alpha, gm, K, V, A, D, slicing, S, fluidP);
 #pragma unroll
   for (int F = 0; F < kNF; ++F) macro[(int64_t)F * G.cells + c] = r[F] + half_dt * S[F];
 }

@@ -45,10 +45,18 @@ enum : int { kAlpha = 0, kG = 1, kK = 7, kV = 13, kNF = 16 };
 
 // Sources S_F of all 16 fields (d_t of each field less its flux divergence)
 // at the state (alpha, gamma, K, V) with derivatives A_k, D_kij.
+//
+// Matter (Sec. "Expansion of flat universe"): a perfect fluid at rest in the
+// slice frame, with energy density rho = alpha^2 G^00 and pressure P:
+// G_ij = P gamma_ij, tr G = 3P, G^0_k = 0. S_ij gains -R^(4)_ij +
+// (gamma_ij / 4) 2 alpha^2 G^00 with R^(4)_ij = G_ij - (gamma_ij / 2)
+// (-alpha^2 G^00 + tr G) = (rho - P) gamma_ij / 2, so the sum is
+// (P / 2) gamma_ij and rho drops out; Omega_k gains alpha^2 G^0_k = 0.
+// fluidP = 0 is vacuum.
 template <class T>
 __device__ __forceinline__ void bm_sources(const T alpha, const T g[6], const T K[6],
                                            const T V[3], const T A[3], const T D[3][6],
-                                           int slicing, T S[kNF]) {
+                                           int slicing, T S[kNF], T fluidP = T(0)) {
   T gi[6];
   invert_sym3(g, gi);
 
@@ -165,6 +173,7 @@ __device__ __forceinline__ void bm_sources(const T alpha, const T g[6], const T 
       // A_i (V_j - D_jk^k / 2) + A_j (V_i - D_ik^k / 2)
       t += A[i] * (V[j] - T(0.5) * tr1[j]) + A[j] * (V[i] - T(0.5) * tr1[i]);
       t += T(0.25) * g[q] * bracket;
+      t += T(0.5) * fluidP * g[q];
       S[kK + q] = alpha * t;
     }
 

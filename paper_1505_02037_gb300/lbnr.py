@@ -91,6 +91,7 @@ def library(path: str | None = None):
     L.lbnr_variant_name.argtypes = [vp, ctypes.c_int]
     L.lbnr_variant_name.restype = ctypes.c_char_p
     L.lbnr_set_variant.argtypes = [vp, ctypes.c_int]
+    L.lbnr_set_fluid.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     L.lbnr_constraint_norms_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(Grid),
                                                  ctypes.c_double, vp, vp, vp]
     L.lbnr_default_batch_opts.argtypes = [ctypes.POINTER(BatchOpts)]
@@ -228,6 +229,10 @@ def lbnr_variant_name(ctx, v: int) -> str:
 
 def lbnr_set_variant(ctx, v: int):
     _check(library().lbnr_set_variant(ctx, v), ctx)
+
+
+def lbnr_set_fluid(ctx, rho0: float, w: float, t0: float):
+    _check(library().lbnr_set_fluid(ctx, float(rho0), float(w), float(t0)), ctx)
 
 
 def lbnr_constraint_norms_noalloc(vset: int, grid: Grid, dx: float, d_fields, d_out,
@@ -370,6 +375,11 @@ class Lattice:
     def set_variant(self, v):
         lbnr_set_variant(self.ctx, v)
         self.variant = v
+
+    def set_fluid(self, rho0, w, t0=1.0):
+        """Perfect fluid at rest: density rho0 (t0/t)^2, pressure w rho, the
+        state after n steps at t = t0 + n dt (call before init)."""
+        lbnr_set_fluid(self.ctx, rho0, w, t0)
 
     def step_timed(self, n=1):
         return lbnr_step_timed(self.ctx, n)

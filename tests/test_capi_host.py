@@ -125,3 +125,7 @@ def test_null_batch_calls_fail_cleanly(lib):
     assert lib.lbnr_batch_steps_done(None, 0) == -1
     assert lib.lbnr_batch_plan(None, None, None, None, None) == -1
     lib.lbnr_batch_destroy(None)
+
+
+def test_set_fluid_rejects_bad_arguments(lib):
+    assert lib.lbnr_set_fluid(None, 0.1, 1.0, 1.0) == -1
