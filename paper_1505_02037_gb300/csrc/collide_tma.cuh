@@ -247,7 +247,8 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
     C alpha, gm[6], K[6], V[3];
     unpack<REP, C>(rt, alpha, gm, K, V);
     C Sr[kNF];
-    bm_sources<C>(alpha, gm, K, V, A, D, a.slicing, Sr, fluid_pressure(a));
+    bm_sources<C>(alpha, gm, K, V, A, D, a.slicing, Sr);
+    add_fluid(a, alpha, gm, Sr);
     if (!a.sources_on) {
 #pragma unroll
       for (int F = 0; F < kNF; ++F) Sr[F] = C(0);

@@ -249,12 +249,17 @@ struct StepArgs {
   double fluid_P0, fluid_t0, fluid_dt;
 };
 
-// Pressure of the fluid at the step being taken (0 without matter).
+// Adds the fluid's term (P/2) gamma_ij to the sources of K_ij (alpha S_ij),
+// with P at the step being taken; nothing without matter. Kept apart from
+// bm_sources so that vacuum launches carry no extra live values.
 template <class S, class C>
-__device__ __forceinline__ C fluid_pressure(const StepArgs<S, C>& a) {
-  if (a.clock == nullptr) return C(0);
+__device__ __forceinline__ void add_fluid(const StepArgs<S, C>& a, C alpha, const C g[6],
+                                          C Sr[kNF]) {
+  if (a.clock == nullptr) return;
   const double r = a.fluid_t0 / (a.fluid_t0 + (double)(*a.clock) * a.fluid_dt);
-  return C(a.fluid_P0 * r * r);
+  const C half_p = C(0.5 * a.fluid_P0 * r * r);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) Sr[kK + q] += alpha * half_p * g[q];
 }
 
 // A_k and D_kij by central differences of the aux planes (reading: second
@@ -361,7 +366,8 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : 3) k_collide(const StepArgs<S,
   C alpha, gm[6], K[6], V[3];
   unpack<REP, C>(rt, alpha, gm, K, V);
   C Sr[kNF];
-  bm_sources<C>(alpha, gm, K, V, A, D, a.slicing, Sr, fluid_pressure(a));
+  bm_sources<C>(alpha, gm, K, V, A, D, a.slicing, Sr);
+  add_fluid(a, alpha, gm, Sr);
   if (!a.sources_on) {
 #pragma unroll
     for (int F = 0; F < kNF; ++F) Sr[F] = C(0);
@@ -537,7 +543,8 @@ __device__ __forceinline__ void collide_cell(const StepArgs<S, C>& a, int64_t c)
   C alpha, gm[6], K[6], V[3];
   unpack<REP, C>(rt, alpha, gm, K, V);
   C Sr[kNF];
-  bm_sources<C>(alpha, gm, K, V, A, D, a.slicing, Sr, fluid_pressure(a));
+  bm_sources<C>(alpha, gm, K, V, A, D, a.slicing, Sr);
+  add_fluid(a, alpha, gm, Sr);
   if (!a.sources_on) {
 #pragma unroll
     for (int F = 0; F < kNF; ++F) Sr[F] = C(0);
