@@ -41,14 +41,14 @@ LBNR_VARIANTS(3, 4, 2, {1, 1, false, 8, 4, 32}, {1, 2, false, 8, 4, 32}, {0, 1, 
               {0, 1, false, 0, 0, 0})
 LBNR_VARIANTS(9, 4, 2, {1, 1, false, 4, 2, 32}, {1, 2, false, 8, 2, 32}, {0, 1, true, 0, 0, 0},
               {0, 1, false, 0, 0, 0})
-LBNR_VARIANTS(19, 4, 4, {1, 1, false, 4, 1, 32}, {1, 1, false, 5, 1, 32},
+LBNR_VARIANTS(19, 4, 2, {1, 1, false, 4, 1, 32}, {1, 1, false, 5, 1, 32},
               {0, 1, false, 0, 0, 0}, {0, 2, false, 0, 0, 0}, {0, 2, true, 0, 0, 0})
 // 16-bit storage
 LBNR_VARIANTS(3, 2, 2, {1, 1, false, 8, 4, 32}, {1, 2, false, 8, 4, 32}, {0, 1, true, 0, 0, 0},
               {0, 1, false, 0, 0, 0})
 LBNR_VARIANTS(9, 2, 2, {1, 1, false, 8, 2, 32}, {1, 2, false, 8, 3, 32}, {0, 1, true, 0, 0, 0},
               {0, 1, false, 0, 0, 0})
-LBNR_VARIANTS(19, 2, 4, {1, 2, false, 8, 2, 32}, {1, 1, false, 8, 1, 32},
+LBNR_VARIANTS(19, 2, 2, {1, 2, false, 8, 2, 32}, {1, 1, false, 8, 1, 32},
               {0, 1, false, 0, 0, 0}, {0, 2, false, 0, 0, 0}, {0, 2, true, 0, 0, 0})
 #undef LBNR_VARIANTS
 
