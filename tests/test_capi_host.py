@@ -129,3 +129,34 @@ def test_null_batch_calls_fail_cleanly(lib):
 
 def test_set_fluid_rejects_bad_arguments(lib):
     assert lib.lbnr_set_fluid(None, 0.1, 1.0, 1.0) == -1
+
+
+@pytest.mark.parametrize("vset,shape", [
+    (3, (1291, 1291, 1291)),   # 2.15e9 cells: past the 2^31 cell limit
+    (3, (610, 610, 610)),      # 19 planes x 227M cells: plane offsets past 2^32
+    (2, (65536, 32768, 1)),    # 2^31 cells on the 2D lattice
+    (1, (2 ** 31, 1, 1)),      # and on the 1D lattice
+])
+def test_create_rejects_lattices_beyond_the_index_limits(vset, shape):
+    """All in-block offsets are 32-bit: lattices with 2^31 cells or more, or
+    with Q x (cells padded to 32) of 2^32 or more, are refused before any
+    device memory is touched."""
+    from paper_1505_02037_gb300 import lbnr
+    o = lbnr.lbnr_default_opts()
+    o.streaming = lbnr.LBNR_STREAM_PINGPONG
+    with pytest.raises(lbnr.LbnrError) as e:
+        lbnr.lbnr_workspace_bytes(lbnr.Grid(*shape), vset, o)
+    assert e.value.code == -1
+    with pytest.raises(lbnr.LbnrError) as e:
+        lbnr.lbnr_create(lbnr.Grid(*shape), vset, 1.0, 0.1, 0.1, o)
+    assert e.value.code == -1
+
+
+def test_largest_accepted_lattice_has_a_workspace_size():
+    """Just inside the limits the workspace size is computed (no device
+    needed): 600^3 D3Q19 in one AA buffer."""
+    from paper_1505_02037_gb300 import lbnr
+    o = lbnr.lbnr_default_opts()
+    o.storage, o.streaming = 1, lbnr.LBNR_STREAM_AA
+    n = lbnr.lbnr_workspace_bytes(lbnr.Grid(600, 600, 600), 3, o)
+    assert n >= 16 * 19 * 4 * 600 ** 3
