@@ -71,6 +71,10 @@ typedef struct {
   int32_t fluid_on;
   int32_t pad2;
   double fluid_rho0, fluid_w, fluid_t0;
+  /* Shift (Sec. "Bona-Masso evolution equations"): a constant, uniform
+   * beta^i, so B_k^i = d_k beta^i / 2 = 0, s_ij = 0, and with Q_i = 0 beta
+   * stays constant. Zero: the zero-shift system of the paper's tests. */
+  double beta[3];
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -156,6 +160,7 @@ enum { F_ALPHA = 0, F_G = 1, F_K = 7, F_V = 13 };
 
 typedef struct {
   double alpha;
+  double beta[3];     /* constant shift beta^i (B = 0) */
   double g[3][3];     /* gamma_ij */
   double K[3][3];     /* K_ij */
   double V[3];        /* V_k */
@@ -363,13 +368,20 @@ static void bm_point(const bm_state* s, int slicing, double rho, double P, bm_rh
     r->S_V[k] = a * t;
   }
 
-  /* Lapse (Eq. alfan with beta = 0) and metric (beta = 0, s_ij = 0). */
+  /* Lapse (Eq. alfan): alpha (beta^r A_r - alpha Q); metric:
+   * 2 beta^r D_rij - 2 alpha (K_ij - s_ij) with s_ij = 0 (B = 0). */
   double Qg = 0;
   if (slicing == 1) Qg = trK;
   else if (slicing == 2) Qg = trK / a;
-  r->S_alpha = -a * a * Qg;
+  double bA = 0;
+  for (int rr = 0; rr < 3; ++rr) bA += s->beta[rr] * s->A[rr];
+  r->S_alpha = a * bA - a * a * Qg;
   for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) r->S_g[i][j] = -2 * a * s->K[i][j];
+    for (int j = 0; j < 3; ++j) {
+      double bD = 0;
+      for (int rr = 0; rr < 3; ++rr) bD += s->beta[rr] * s->D[rr][i][j];
+      r->S_g[i][j] = 2 * bD - 2 * a * s->K[i][j];
+    }
 }
 
 /* Exported pointwise evaluation for the tests: inputs alpha, gamma[6],
@@ -381,6 +393,7 @@ void orc_bm_point(double alpha, const double* g6, const double* K6, const double
   bm_state s;
   bm_rhs r;
   s.alpha = alpha;
+  s.beta[0] = s.beta[1] = s.beta[2] = 0;
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
       s.g[i][j] = g6[pair_of(i, j)];
@@ -463,9 +476,11 @@ static void matter_now(const orc_params* p, double* rho, double* P) {
   *P = p->fluid_w * *rho;
 }
 
-/* Unpacks the 16 stored values into a bm_state (derivatives added apart). */
-static void unpack_fields(const double v[ORC_NF], bm_state* s) {
+/* Unpacks the 16 stored values and the shift into a bm_state (derivatives
+ * added apart). */
+static void unpack_fields(const orc_params* p, const double v[ORC_NF], bm_state* s) {
   s->alpha = v[F_ALPHA];
+  for (int k = 0; k < 3; ++k) s->beta[k] = p->beta[k];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
       s->g[i][j] = v[F_G + pair_of(i, j)];
@@ -484,13 +499,19 @@ static void pack_sources(const bm_rhs* r, double S[ORC_NF]) {
   for (int k = 0; k < 3; ++k) S[F_V + k] = r->S_V[k];
 }
 
-/* Macroscopic flux of every field along each axis: alpha lambda^k_ij for
- * K_ij (the only field with a flux at zero shift), zero otherwise. */
-static void pack_fluxes(const bm_rhs* r, double alpha, double Fl[ORC_NF][3]) {
+/* Macroscopic flux of every field along each axis, read off the
+ * equilibria's first moments: -beta^k K_ij + alpha lambda^k_ij for K_ij,
+ * -beta^k V_i for V_i, zero for alpha and gamma_ij (their shift terms are
+ * sources). s holds the fields the flux is taken at. */
+static void pack_fluxes(const bm_rhs* r, const bm_state* s, double Fl[ORC_NF][3]) {
   for (int F = 0; F < ORC_NF; ++F)
     for (int k = 0; k < 3; ++k) Fl[F][k] = 0;
   for (int q = 0; q < 6; ++q)
-    for (int k = 0; k < 3; ++k) Fl[F_K + q][k] = alpha * r->lam[k][PAIR_I[q]][PAIR_J[q]];
+    for (int k = 0; k < 3; ++k)
+      Fl[F_K + q][k] = s->alpha * r->lam[k][PAIR_I[q]][PAIR_J[q]] -
+                       s->beta[k] * s->K[PAIR_I[q]][PAIR_J[q]];
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 3; ++k) Fl[F_V + i][k] = -s->beta[k] * s->V[i];
 }
 
 /* Steps 1-5 at one cell: given the uncorrected moments rho~ of all cells
@@ -507,7 +528,7 @@ static void cell_macro(const orc_params* p, const double* mom, int64_t cells, in
   bm_state s;
   bm_rhs r;
   derivatives(p, mom, cells, x, y, z, s.A, s.D);
-  unpack_fields(rt, &s);
+  unpack_fields(p, rt, &s);
   bm_point(&s, p->slicing, mrho, mP, &r);
   pack_sources(&r, S);
   if (!p->sources_on)
@@ -515,12 +536,12 @@ static void cell_macro(const orc_params* p, const double* mom, int64_t cells, in
   /* rho = sum_l f + dt S / 2 (Sec. LBM, macroscopic variables). */
   for (int F = 0; F < ORC_NF; ++F) rho[F] = rt[F] + 0.5 * p->dt * S[F];
   /* Flux at the corrected moments with the same derivatives (R5). */
-  unpack_fields(rho, &s);
+  unpack_fields(p, rho, &s);
   bm_point(&s, p->slicing, mrho, mP, &r);
-  pack_fluxes(&r, rho[F_ALPHA], Fl);
+  pack_fluxes(&r, &s, Fl);
 }
 
-/* Equilibrium (Eqs. alfa .. ekst at zero shift): w_l [rho + c_l . Flux / c_s^2]. */
+/* Equilibrium (Eqs. alfa .. ekst): w_l [rho + c_l . Flux / c_s^2]. */
 static double feq(const vset_t* vs, int l, double rho, const double Fl[3]) {
   double cf = 0;
   for (int k = 0; k < 3; ++k) cf += vs->c[l][k] * Fl[k];
@@ -554,12 +575,12 @@ int orc_init(const orc_params* p, const double* fields, double* f_out) {
     bm_state s;
     bm_rhs r;
     derivatives(p, fields, cells, x, y, z, s.A, s.D);
-    unpack_fields(v, &s);
+    unpack_fields(p, v, &s);
     bm_point(&s, p->slicing, mrho, mP, &r);
     pack_sources(&r, S);
     if (!p->sources_on)
       for (int F = 0; F < ORC_NF; ++F) S[F] = 0;
-    pack_fluxes(&r, v[F_ALPHA], Fl);
+    pack_fluxes(&r, &s, Fl);
     for (int F = 0; F < ORC_NF; ++F)
       for (int l = 0; l < vs.Q; ++l) {
         double val = feq(&vs, l, v[F], Fl[F]) - 0.5 * p->dt * vs.w[l] * S[F];
@@ -692,15 +713,15 @@ int orc_step_cells(const orc_params* p, const double* f_in, int64_t n, const int
                             moment0(&vs, cells, f_in, F_G + q, cm)) / (4 * p->dx);
           }
       }
-      unpack_fields(rt, &s);
+      unpack_fields(p, rt, &s);
       bm_point(&s, p->slicing, mrho, mP, &r);
       pack_sources(&r, S);
       if (!p->sources_on)
         for (int F = 0; F < ORC_NF; ++F) S[F] = 0;
       for (int F = 0; F < ORC_NF; ++F) rho[F] = rt[F] + 0.5 * p->dt * S[F];
-      unpack_fields(rho, &s);
+      unpack_fields(p, rho, &s);
       bm_point(&s, p->slicing, mrho, mP, &r);
-      pack_fluxes(&r, rho[F_ALPHA], Fl);
+      pack_fluxes(&r, &s, Fl);
       const double src_fac = 1.0 - 1.0 / (2.0 * p->tau);
       for (int F = 0; F < ORC_NF; ++F) {
         double fl = f_in[((int64_t)F * vs.Q + l) * cells + nb[0]];

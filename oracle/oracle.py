@@ -50,6 +50,7 @@ class Params(ctypes.Structure):
         ("fluid_rho0", ctypes.c_double),
         ("fluid_w", ctypes.c_double),
         ("fluid_t0", ctypes.c_double),
+        ("beta", ctypes.c_double * 3),
     ]
 
 
@@ -144,9 +145,13 @@ class Oracle:
     fluid = (rho0, w, t0): a perfect fluid at rest with density
     rho0 (t0/t)^2 and pressure w rho (Sec. "Expansion of flat universe"). The
     calls then take the time t of the state they read (default t0; run()
-    advances it by dt per step)."""
+    advances it by dt per step).
 
-    def __init__(self, vset, shape, tau, dx, dt=None, slicing=1, sources_on=True, fluid=None):
+    shift = (bx, by, bz): a constant, uniform shift beta^i (Sec. "Bona-Masso
+    evolution equations" with B = 0); default zero."""
+
+    def __init__(self, vset, shape, tau, dx, dt=None, slicing=1, sources_on=True, fluid=None,
+                 shift=None):
         nx, ny, nz = shape
         self.vset = int(vset)
         self.Q = Q_OF[self.vset]
@@ -160,6 +165,9 @@ class Oracle:
             self.p.fluid_on, self.p.fluid_rho0, self.p.fluid_w = 1, float(rho0), float(w)
             self.p.fluid_t0 = self.t0 = float(t0)
         self.p.t = self.t0
+        if shift is not None:
+            for k in range(3):
+                self.p.beta[k] = float(shift[k])
 
     def _at(self, t):
         self.p.t = self.t0 if t is None else float(t)

@@ -64,14 +64,23 @@ def _pack(alpha, g, K, V, shape):
     return out
 
 
-def gauge_wave(shape, dx, A, t=0.0, direction="x"):
+def _shifted_u(n, shape, dx, t, beta):
+    """u = n.(x + beta t): a zero-shift solution seen from coordinates that
+    move with the constant velocity -beta. In them the shift is beta^i, the
+    lapse, metric and extrinsic curvature keep their values, and the fields
+    at x are the zero-shift fields at x + beta t."""
+    X, Y, Z = coords(shape, dx)
+    b = (0.0, 0.0, 0.0) if beta is None else tuple(float(v) for v in beta)
+    return n[0] * (X + b[0] * t) + n[1] * (Y + b[1] * t) + n[2] * (Z + b[2] * t)
+
+
+def gauge_wave(shape, dx, A, t=0.0, direction="x", beta=None):
     """Gauge wave (Sec. "Gauge Wave"): ds^2 = -H dt^2 + H du^2 + (transverse),
     H = 1 - A sin(2 pi (u - t)/d), u = n.x; alpha = sqrt(H),
     gamma = delta + (H - 1) n n, K = -(pi A/d) cos(phase)/sqrt(H) n n, V = 0.
-    Harmonic slicing."""
+    Harmonic slicing. beta: a constant shift (u = n.(x + beta t))."""
     n, d = _direction(direction, shape, dx)
-    X, Y, Z = coords(shape, dx)
-    u = n[0] * X + n[1] * Y + n[2] * Z
+    u = _shifted_u(n, shape, dx, t, beta)
     ph = 2 * math.pi * (u - t) / d
     H = 1 - A * np.sin(ph)
     Knn = -(math.pi * A / d) * np.cos(ph) / np.sqrt(H)
@@ -92,16 +101,16 @@ def _polarisation(direction):
     raise ValueError(direction)
 
 
-def linear_wave(shape, dx, A, t=0.0, direction="x"):
+def linear_wave(shape, dx, A, t=0.0, direction="x", beta=None):
     """Linear (gravitational) wave (Sec. "Linear Wave"): alpha = 1,
     gamma = delta + b (e1 e1 - e2 e2), b = A sin(2 pi (u - t)/d),
     K = (pi A/d) cos(phase) (e1 e1 - e2 e2). Geodesic slicing.
     V_k = -b b' n_k / (1 - b^2) is V's defining combination of the closed-form
-    metric derivatives, with b' = db/du."""
+    metric derivatives, with b' = db/du. beta: a constant shift
+    (u = n.(x + beta t))."""
     n, d = _direction(direction, shape, dx)
     e1, e2 = _polarisation(direction)
-    X, Y, Z = coords(shape, dx)
-    u = n[0] * X + n[1] * Y + n[2] * Z
+    u = _shifted_u(n, shape, dx, t, beta)
     ph = 2 * math.pi * (u - t) / d
     b = A * np.sin(ph)
     bp = (2 * math.pi * A / d) * np.cos(ph)
@@ -123,6 +132,29 @@ def kasner(shape, p=(-1 / 3, 2 / 3, 2 / 3), t=1.0):
     K = [[(-p[i] * t ** (2 * p[i] - 1) * one if i == j else 0 * one) for j in range(3)]
          for i in range(3)]
     return _pack(one, g, K, [0 * one] * 3, shape)
+
+
+def smooth_modes(shape, dx, amp, seed, modes=2):
+    """Flat space plus, in every one of the 16 fields, a few smooth periodic
+    Fourier modes of amplitude amp (seeded): generic initial data for the
+    evolution system, constraints not imposed. Modes run along the lattice's
+    axes of extent > 1, wave numbers 1..modes per box length."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = shape
+    X, Y, Z = coords(shape, dx)
+    L = (nx * dx, ny * dx, nz * dx)
+    out = flat(shape).copy()
+    live = [a for a, n in enumerate(shape) if n > 1]
+    for F in range(NF):
+        for _ in range(modes):
+            k = np.zeros(3)
+            for a in live:
+                k[a] = rng.integers(-modes, modes + 1) / L[a]
+            if not k.any():
+                k[live[0]] = 1.0 / L[live[0]]
+            ph = 2 * math.pi * (k[0] * X + k[1] * Y + k[2] * Z) + rng.uniform(0, 2 * math.pi)
+            out[F] += amp * rng.uniform(0.5, 1.0) * np.sin(ph)
+    return out
 
 
 def flat(shape):
