@@ -157,6 +157,18 @@ int lbnr_status(lbnr_ctx* ctx);
  * as n. Errors: LBNR_EINVAL for rho0 < 0, t0 <= 0 or non-finite values. */
 int lbnr_set_fluid(lbnr_ctx* ctx, double rho0, double w, double t0);
 
+/* Shift (Sec. "Bona-Masso evolution equations"): a constant, uniform shift
+ * vector beta^i = (bx, by, bz) in lattice units of dr/dt, so B_k^i = 0 and
+ * s_ij = 0. Adds alpha beta^r A_r to the lapse source and 2 beta^r D_rij to
+ * the metric source, and the factor 1 - c_l.beta / c_s^2 to the equilibria
+ * of K_ij and V_i (fluxes -beta^k K_ij and -beta^k V_i). The collide step
+ * then runs in its one shift-carrying launch form (one thread per cell,
+ * distributions re-read; any streaming pattern), whatever lbnr_set_variant
+ * chose; (0, 0, 0) returns to the zero-shift forms. Call before lbnr_init
+ * (the initial equilibria carry the shift); takes effect at the next step.
+ * Errors: LBNR_EINVAL for a null context or non-finite values. */
+int lbnr_set_shift(lbnr_ctx* ctx, double bx, double by, double bz);
+
 /* Thread-to-cell layouts of the collide kernel available for this context's
  * set and storage (all give the same results): their number, a short name,
  * and the selection (default 0). Used by the autotuner. */

@@ -131,8 +131,9 @@ __device__ void run_steps(const BatchParams& p, const BatchRun& R, const Assign&
   a.sigma = C(dx * (1.0 - 1.0 / (2.0 * tau)));
   a.slicing = R.slicing;
   a.sources_on = p.sources_on;
-  a.clock = nullptr;  // batched runs are vacuum
+  a.clock = nullptr;  // batched runs are vacuum, zero shift
   a.fluid_P0 = a.fluid_t0 = a.fluid_dt = 0;
+  a.beta[0] = a.beta[1] = a.beta[2] = C(0);
   C* const aux = static_cast<C*>(R.aux);
   const int64_t cells = a.G.cells;
   const int64_t B = blockDim.x;

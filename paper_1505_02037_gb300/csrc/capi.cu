@@ -392,6 +392,8 @@ int lbnr_create(const lbnr_grid* grid, int vset, double tau, double dx, double d
   L.block = 128;
   L.clock = nullptr;
   L.fluid_P0 = L.fluid_t0 = L.fluid_P_now = 0;
+  L.beta[0] = L.beta[1] = L.beta[2] = 0;
+  L.shift_on = 0;
   // zero everything once: the plane padding must hold finite values
   cudaError_t e = cudaMemsetAsync(c->base, 0, Ly.total, c->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
@@ -603,6 +605,19 @@ int lbnr_set_fluid(lbnr_ctx* c, double rho0, double w, double t0) {
   }
   c->L.fluid_P0 = w * rho0;
   c->L.fluid_t0 = t0;
+  drop_graphs(c);  // the captured steps carry the old parameters
+  return LBNR_OK;
+}
+
+int lbnr_set_shift(lbnr_ctx* c, double bx, double by, double bz) {
+  if (!c) return fail(c, LBNR_EINVAL, "null context");
+  if (!std::isfinite(bx) || !std::isfinite(by) || !std::isfinite(bz))
+    return fail(c, LBNR_EINVAL, "shift must be finite");
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  c->L.beta[0] = bx;
+  c->L.beta[1] = by;
+  c->L.beta[2] = bz;
+  c->L.shift_on = (bx != 0.0 || by != 0.0 || bz != 0.0) ? 1 : 0;
   drop_graphs(c);  // the captured steps carry the old parameters
   return LBNR_OK;
 }

@@ -141,6 +141,13 @@ struct Impl {
     return cudaGetLastError();
   }
 
+  template <int LAYOUT>
+  static cudaError_t launch_shifted(const LaunchCtx& L, const StepArgs<S, C>& a) {
+    const int block = 128;
+    k_collide<Q, S, C, REP, LAYOUT, 1, false, true><<<grid_for(L.cells, block), block, 0, L.st>>>(a);
+    return cudaGetLastError();
+  }
+
   template <int LAYOUT, int VI>
   static cudaError_t launch_tma(const LaunchCtx& L, const StepArgs<S, C>& a) {
     constexpr VariantSpec x = VT::v[VI];
@@ -220,6 +227,13 @@ struct Impl {
     a.fluid_P0 = L.fluid_P0;
     a.fluid_t0 = L.fluid_t0;
     a.fluid_dt = L.dt;
+    for (int k = 0; k < 3; ++k) a.beta[k] = C(L.beta[k]);
+    if (L.shift_on) {
+      // One launch form carries the shift terms: P1-reread, any layout.
+      if (layout == kPingPong) return launch_shifted<kPingPong>(L, a);
+      if (layout == kAAEven) return launch_shifted<kAAEven>(L, a);
+      return launch_shifted<kAAOdd>(L, a);
+    }
     if (layout == kPingPong) return collide_layout<kPingPong>(L, variant, a);
     if (layout == kAAEven) return collide_layout<kAAEven>(L, variant, a);
     return collide_layout<kAAOdd>(L, variant, a);
@@ -248,6 +262,8 @@ struct Impl {
     a.slicing = L.slicing;
     a.sources_on = L.sources_on;
     a.fluidP = L.clock ? L.fluid_P0 : 0.0;  // the initial state is at t0
+    for (int k = 0; k < 3; ++k) a.beta[k] = L.beta[k];
+    a.shift_on = L.shift_on;
     k_init<Q, S, REP><<<grid_for(L.cells, 128), 128, 0, L.st>>>(a);
     return cudaGetLastError();
   }
@@ -270,7 +286,8 @@ struct Impl {
     const Grid G = make_grid(L.nx, L.ny, L.nz, L.cells, L.pstride);
     k_correct64<Q><<<grid_for(L.cells, 128), 128, 0, L.st>>>(
         L.macro, L.aux64, G, 1.0 / (2.0 * L.dx), 1.0 / (4.0 * L.dx), 0.5 * L.dt, L.slicing,
-        L.sources_on, L.clock ? L.fluid_P_now : 0.0);
+        L.sources_on, L.clock ? L.fluid_P_now : 0.0, L.shift_on ? L.beta[0] : 0.0,
+        L.shift_on ? L.beta[1] : 0.0, L.shift_on ? L.beta[2] : 0.0);
     return cudaGetLastError();
   }
 

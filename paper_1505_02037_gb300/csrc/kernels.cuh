@@ -111,6 +111,8 @@ __host__ __device__ constexpr double flat_value(int F) {
   return (F == 0 || F == 1 || F == 4 || F == 6) ? 1.0 : 0.0;
 }
 __host__ __device__ constexpr bool has_flux(int F) { return F >= kK && F < kV; }
+// V_i: a flux (-beta^k V_i) only under a shift.
+__host__ __device__ constexpr bool is_v(int F) { return F >= kV && F < kNF; }
 
 // ---------------------------------------------------------------------------
 // Geometry of one cell and its neighbours (periodic)
@@ -247,6 +249,8 @@ struct StepArgs {
   // clock == nullptr is vacuum.
   const int64_t* clock;
   double fluid_P0, fluid_t0, fluid_dt;
+  // Constant shift beta^i (B = 0), read by the forms compiled with SHIFT.
+  C beta[3];
 };
 
 // Adds the fluid's term (P/2) gamma_ij to the sources of K_ij (alpha S_ij),
@@ -260,6 +264,27 @@ __device__ __forceinline__ void add_fluid(const StepArgs<S, C>& a, C alpha, cons
   const C half_p = C(0.5 * a.fluid_P0 * r * r);
 #pragma unroll
   for (int q = 0; q < 6; ++q) Sr[kK + q] += alpha * half_p * g[q];
+}
+
+// Shift sources (Sec. "Bona-Masso evolution equations", constant beta):
+// alpha beta^r A_r to the lapse, 2 beta^r D_rij to the metric.
+template <class C>
+__device__ __forceinline__ void shift_sources(const C beta[3], C alpha, const C A[3],
+                                              const C D[3][6], C Sr[kNF]) {
+  Sr[0] += alpha * (beta[0] * A[0] + beta[1] * A[1] + beta[2] * A[2]);
+#pragma unroll
+  for (int q = 0; q < 6; ++q)
+    Sr[kG + q] += C(2) * (beta[0] * D[0][q] + beta[1] * D[1][q] + beta[2] * D[2][q]);
+}
+
+// Shift part of the K fluxes: -beta^k K_ij (the K equilibria's factor
+// 1 - c.beta / c_s^2), K at the corrected moments.
+template <class C, int dim>
+__device__ __forceinline__ void shift_flux_k(const C beta[3], const C K[6], C Fl[6][3]) {
+#pragma unroll
+  for (int k = 0; k < dim; ++k)
+#pragma unroll
+    for (int q = 0; q < 6; ++q) Fl[q][k] -= beta[k] * K[q];
 }
 
 // A_k and D_kij by central differences of the aux planes (reading: second
@@ -304,7 +329,9 @@ __device__ __forceinline__ void unpack(const C m[kNF], C& alpha, C g[6], C K[6],
 // ---------------------------------------------------------------------------
 // k_collide: the fused step
 // ---------------------------------------------------------------------------
-template <int Q, class S, class C, int REP, int LAYOUT, int P, bool HOLD>
+// SHIFT: the shift terms are compiled in (a.beta); the zero-shift forms keep
+// none of their code or registers.
+template <int Q, class S, class C, int REP, int LAYOUT, int P, bool HOLD, bool SHIFT = false>
 __global__ void __launch_bounds__(128, HOLD ? 1 : 3) k_collide(const StepArgs<S, C> a) {
   using L = Lattice<Q>;
   constexpr int NJ = kNF / P;
@@ -368,6 +395,7 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : 3) k_collide(const StepArgs<S,
   C Sr[kNF];
   bm_sources<C>(alpha, gm, K, V, A, D, a.slicing, Sr);
   add_fluid(a, alpha, gm, Sr);
+  if (SHIFT) shift_sources<C>(a.beta, alpha, A, D, Sr);
   if (!a.sources_on) {
 #pragma unroll
     for (int F = 0; F < kNF; ++F) Sr[F] = C(0);
@@ -380,6 +408,7 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : 3) k_collide(const StepArgs<S,
     C alpha2, g2[6], K2[6], V2[3];
     unpack<REP, C>(rho, alpha2, g2, K2, V2);
     bm_flux<C, dim>(alpha2, g2, V2, A, D, Fl);
+    if (SHIFT) shift_flux_k<C, dim>(a.beta, K2, Fl);
   }
   // Per-field coefficients: coef = omega rho + sigma S; flux scaled by 3 omega.
   C coef[kNF];
@@ -399,6 +428,9 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : 3) k_collide(const StepArgs<S,
       for (int k = 0; k < dim; ++k)
         b[k] = three_omega * (g ? Fl[F1 - kK][k] : Fl[F0 - kK][k]);
     }
+    // Under a shift the V fields (and, with two threads per cell, the field
+    // paired with V_x) take the flux -beta^k V_i; b stays zero for the other.
+    const bool vflux = SHIFT && (is_v(F0) || is_v(F1));
     // All Q values of this field are read before any is written: in place
     // (AA) the field's reads and writes touch the same Q locations.
     const S* fb = a.fin + field_base<Q>(F, ps);
@@ -413,11 +445,22 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : 3) k_collide(const StepArgs<S,
       v_[l] = HOLD ? fv[HOLD ? j : 0][HOLD ? l : 0]
               : LAYOUT == kPingPong ? Codec<S>::load(src) : Codec<S>::load_coh(src);
     }
+    if (vflux) {
+      // V_i at the corrected moments, recovered from this field's own values
+      // rather than kept live since pass 1: coef = omega rho~ + dt S (as
+      // omega dt/2 + sigma = dt), so rho = rho~ + (coef - omega rho~) / 2.
+      C s = C(0);
+#pragma unroll
+      for (int l = 0; l < Q; ++l) s += REP == kDEV ? C(L::w(l)) * v_[l] : v_[l];
+      const C mv = is_v(F) ? -three_omega * (s + C(0.5) * (cf - a.omega * s)) : C(0);
+#pragma unroll
+      for (int k = 0; k < dim; ++k) b[k] = mv * a.beta[k];
+    }
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
       const C v = v_[l];
       C t = cf;
-      if (has_flux(F0)) {
+      if (has_flux(F0) || vflux) {
 #pragma unroll
         for (int k = 0; k < dim; ++k) {
           if (L::c(l, k) > 0) t += b[k];
@@ -600,6 +643,8 @@ struct Init64Args {
   double inv2dx, inv4dx, half_dt;
   int slicing, sources_on;
   double fluidP;  // fluid pressure at the initial time (0: vacuum)
+  double beta[3];  // constant shift
+  int shift_on;
 };
 
 // Shifted equilibrium: f = f_eq(rho0) - (dt/2) w_l S(rho0), A and D from rho0.
@@ -635,10 +680,12 @@ __global__ void __launch_bounds__(128) k_init(const Init64Args<S> a) {
   unpack<kABS, double>(r, alpha, gm, K, V);
   double Sr[kNF];
   bm_sources<double>(alpha, gm, K, V, A, D, a.slicing, Sr, a.fluidP);
+  if (a.shift_on) shift_sources<double>(a.beta, alpha, A, D, Sr);
   if (!a.sources_on)
     for (int F = 0; F < kNF; ++F) Sr[F] = 0;
   double Fl[6][3];
   bm_flux<double, dim>(alpha, gm, V, A, D, Fl);
+  if (a.shift_on) shift_flux_k<double, dim>(a.beta, K, Fl);
   bool bad = false;
 #pragma unroll
   for (int F = 0; F < kNF; ++F) {
@@ -648,6 +695,10 @@ __global__ void __launch_bounds__(128) k_init(const Init64Args<S> a) {
       if (has_flux(F)) {
 #pragma unroll
         for (int k = 0; k < dim; ++k) cf += L::c(l, k) * Fl[F - kK][k];
+      }
+      if (is_v(F) && a.shift_on) {
+#pragma unroll
+        for (int k = 0; k < dim; ++k) cf += L::c(l, k) * (-a.beta[k] * r[F]);
       }
       // f = w (rho + 3 c.F) - (dt/2) w S
       double v;
@@ -711,7 +762,8 @@ template <int Q>
 __global__ void __launch_bounds__(128) k_correct64(double* __restrict__ macro,
                                                    const double* __restrict__ aux64, Grid G,
                                                    double inv2dx, double inv4dx, double half_dt,
-                                                   int slicing, int sources_on, double fluidP) {
+                                                   int slicing, int sources_on, double fluidP,
+                                                   double bx, double by, double bz) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= G.cells || !sources_on) return;
   const Nbr n = make_nbr(G, c);
@@ -724,6 +776,10 @@ __global__ void __launch_bounds__(128) k_correct64(double* __restrict__ macro,
   unpack<kABS, double>(r, alpha, gm, K, V);
   double S[kNF];
   bm_sources<double>(alpha, gm, K, V, A, D, slicing, S, fluidP);
+  if (bx != 0.0 || by != 0.0 || bz != 0.0) {
+    const double beta[3] = {bx, by, bz};
+    shift_sources<double>(beta, alpha, A, D, S);
+  }
 #pragma unroll
   for (int F = 0; F < kNF; ++F) macro[(int64_t)F * G.cells + c] = r[F] + half_dt * S[F];
 }

@@ -92,6 +92,7 @@ def library(path: str | None = None):
     L.lbnr_variant_name.restype = ctypes.c_char_p
     L.lbnr_set_variant.argtypes = [vp, ctypes.c_int]
     L.lbnr_set_fluid.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    L.lbnr_set_shift.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     L.lbnr_constraint_norms_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(Grid),
                                                  ctypes.c_double, vp, vp, vp]
     L.lbnr_default_batch_opts.argtypes = [ctypes.POINTER(BatchOpts)]
@@ -233,6 +234,10 @@ def lbnr_set_variant(ctx, v: int):
 
 def lbnr_set_fluid(ctx, rho0: float, w: float, t0: float):
     _check(library().lbnr_set_fluid(ctx, float(rho0), float(w), float(t0)), ctx)
+
+
+def lbnr_set_shift(ctx, bx: float, by: float, bz: float):
+    _check(library().lbnr_set_shift(ctx, float(bx), float(by), float(bz)), ctx)
 
 
 def lbnr_constraint_norms_noalloc(vset: int, grid: Grid, dx: float, d_fields, d_out,
@@ -380,6 +385,11 @@ class Lattice:
         """Perfect fluid at rest: density rho0 (t0/t)^2, pressure w rho, the
         state after n steps at t = t0 + n dt (call before init)."""
         lbnr_set_fluid(self.ctx, rho0, w, t0)
+
+    def set_shift(self, beta):
+        """Constant shift beta^i = (bx, by, bz) (call before init)."""
+        bx, by, bz = (float(v) for v in beta)
+        lbnr_set_shift(self.ctx, bx, by, bz)
 
     def step_timed(self, n=1):
         return lbnr_step_timed(self.ctx, n)

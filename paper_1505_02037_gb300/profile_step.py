@@ -1,14 +1,15 @@
 """Runs a few lattice Boltzmann steps of one launch form, for profilers.
 
   python -m paper_1505_02037_gb300.profile_step --storage f32 --n 128 \
-      --variant 3 --steps 4 [--vset 3] [--tau 4.5] [--streaming 1]
+      --variant 3 --steps 4 [--vset 3] [--tau 4.5] [--streaming 1] [--shift 0.25,0.1,-0.2]
   python -m paper_1505_02037_gb300.profile_step --batch 16 --vset 2 --n 256 \
       --storage dev_f32 --steps 16 [--block 256 --per-sm 1]
 
 Prints the per-kernel milliseconds of the timed steps (CUDA events). Used to
 capture ncu reports of a single kernel on a small case. With --batch R the
 batched ensemble kernel advances R copies of the wave (tau 2.0) by --steps
-steps in each of four launches.
+steps in each of four launches. With --shift the lattice carries that
+constant shift and runs the shift-carrying launch form (--variant is ignored).
 """
 from __future__ import annotations
 
@@ -31,6 +32,7 @@ def main(argv=None):
     p.add_argument("--batch", type=int, default=0)
     p.add_argument("--block", type=int, default=256)
     p.add_argument("--per-sm", type=int, default=1)
+    p.add_argument("--shift", default=None, help="bx,by,bz")
     a = p.parse_args(argv)
     if a.batch:
         return batch_main(a)
@@ -41,11 +43,15 @@ def main(argv=None):
         print(f"no launch form {a.variant}; have {lat.variants}")
         return 2
     lat.set_variant(a.variant)
-    lat.init(W.gauge_wave(shape, 1 / n, 0.1))
+    beta = tuple(float(v) for v in a.shift.split(",")) if a.shift else None
+    if beta:
+        lat.set_shift(beta)
+    lat.init(W.gauge_wave(shape, 1 / n, 0.1, beta=beta))
     lat.step(a.steps)
     lat.status()
     ms = lat.step_timed(4)
-    print(f"{a.storage} n={n} vset={a.vset} {lat.variants[a.variant]}: "
+    form = "P1-reread-shift" if beta else lat.variants[a.variant]
+    print(f"{a.storage} n={n} vset={a.vset} {form}: "
           f"ms per step aux {ms[0] / 4:.4f} collide {ms[1] / 4:.4f}")
     return 0
 

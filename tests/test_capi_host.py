@@ -131,6 +131,11 @@ def test_set_fluid_rejects_bad_arguments(lib):
     assert lib.lbnr_set_fluid(None, 0.1, 1.0, 1.0) == -1
 
 
+def test_set_shift_rejects_a_null_context(lib):
+    assert lib.lbnr_set_shift(None, 0.1, 0.0, 0.0) == -1
+    assert lib.lbnr_set_shift(None, float("nan"), 0.0, 0.0) == -1
+
+
 @pytest.mark.parametrize("vset,shape", [
     (3, (1291, 1291, 1291)),   # 2.15e9 cells: past the 2^31 cell limit
     (3, (610, 610, 610)),      # 19 planes x 227M cells: plane offsets past 2^32
