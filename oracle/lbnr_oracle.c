@@ -75,6 +75,10 @@ typedef struct {
    * beta^i, so B_k^i = d_k beta^i / 2 = 0, s_ij = 0, and with Q_i = 0 beta
    * stays constant. Zero: the zero-shift system of the paper's tests. */
   double beta[3];
+  /* Shift field (reading R15): a prescribed, static beta^i(x), [3][cells],
+   * added to beta; B_k^i = d_k beta^i / 2 from its central differences.
+   * NULL: no field. */
+  const double* beta_field;
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -160,7 +164,8 @@ enum { F_ALPHA = 0, F_G = 1, F_K = 7, F_V = 13 };
 
 typedef struct {
   double alpha;
-  double beta[3];     /* constant shift beta^i (B = 0) */
+  double beta[3];     /* shift beta^i at the point */
+  double B[3][3];     /* B_k^i = d_k beta^i / 2, index [k][i] */
   double g[3][3];     /* gamma_ij */
   double K[3][3];     /* K_ij */
   double V[3];        /* V_k */
@@ -175,6 +180,7 @@ typedef struct {
   double S_V[3];       /* Omega_k (Eq. Vsor) */
   double lam[3][3][3]; /* lambda^k_ij, index [k][i][j] */
   double S_ij[3][3];   /* S_ij itself (without the factor alpha) */
+  double VB[3][3];     /* B part of the flux of V_k along r: B^r_k - B_k^r, [k][r] */
 } bm_rhs;
 
 static double inverse3(const double g[3][3], double gi[3][3]) {
@@ -368,6 +374,45 @@ static void bm_point(const bm_state* s, int slicing, double rho, double P, bm_rh
     r->S_V[k] = a * t;
   }
 
+  /* Shift-derivative terms (Sec. "Bona-Masso evolution equations"), all
+   * zero for a constant shift: B_ij = B_i^m gamma_mj (second index
+   * lowered), B^r_s = g^{rl} B_ls (first raised), tr B = B_r^r. */
+  double Bl[3][3], Bul[3][3], trB = 0;
+  for (int i = 0; i < 3; ++i) {
+    trB += s->B[i][i];
+    for (int j = 0; j < 3; ++j) {
+      double t = 0;
+      for (int m = 0; m < 3; ++m) t += s->B[i][m] * s->g[m][j];
+      Bl[i][j] = t;
+    }
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double t = 0;
+      for (int m = 0; m < 3; ++m) t += gi[i][m] * Bl[m][j];
+      Bul[i][j] = t;
+    }
+  /* S_ij += (2 / alpha)(K_ir B_j^r + K_jr B_i^r - K_ij tr B) */
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double t = -s->K[i][j] * trB;
+      for (int rr = 0; rr < 3; ++rr) t += s->K[i][rr] * s->B[j][rr] + s->K[j][rr] * s->B[i][rr];
+      r->S_ij[i][j] += (2 / a) * t;
+      r->S_K[i][j] = a * r->S_ij[i][j];
+    }
+  /* Omega_k += 2 (B_k^r - delta_k^r tr B) V_r + 2 (D_rk^s - delta^s_k D^j_jr) B^r_s */
+  for (int k = 0; k < 3; ++k) {
+    double t = 0;
+    for (int rr = 0; rr < 3; ++rr) t += (s->B[k][rr] - trB * kdelta(k, rr)) * s->V[rr];
+    for (int rr = 0; rr < 3; ++rr)
+      for (int ss = 0; ss < 3; ++ss)
+        t += (Dl2u[rr][k][ss] - kdelta(ss, k) * Dtr2[rr]) * Bul[rr][ss];
+    r->S_V[k] += 2 * t;
+  }
+  /* V flux (reading R15): B^r_k - B_k^r along r */
+  for (int k = 0; k < 3; ++k)
+    for (int rr = 0; rr < 3; ++rr) r->VB[k][rr] = Bul[rr][k] - s->B[k][rr];
+
   /* Lapse (Eq. alfan): alpha (beta^r A_r - alpha Q); metric:
    * 2 beta^r D_rij - 2 alpha (K_ij - s_ij) with s_ij = 0 (B = 0). */
   double Qg = 0;
@@ -380,7 +425,7 @@ static void bm_point(const bm_state* s, int slicing, double rho, double P, bm_rh
     for (int j = 0; j < 3; ++j) {
       double bD = 0;
       for (int rr = 0; rr < 3; ++rr) bD += s->beta[rr] * s->D[rr][i][j];
-      r->S_g[i][j] = 2 * bD - 2 * a * s->K[i][j];
+      r->S_g[i][j] = 2 * bD - 2 * a * s->K[i][j] + 2 * (Bl[i][j] + Bl[j][i]);
     }
 }
 
@@ -393,7 +438,8 @@ void orc_bm_point(double alpha, const double* g6, const double* K6, const double
   bm_state s;
   bm_rhs r;
   s.alpha = alpha;
-  s.beta[0] = s.beta[1] = s.beta[2] = 0;
+  memset(s.beta, 0, sizeof(s.beta));
+  memset(s.B, 0, sizeof(s.B));
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
       s.g[i][j] = g6[pair_of(i, j)];
@@ -476,11 +522,30 @@ static void matter_now(const orc_params* p, double* rho, double* P) {
   *P = p->fluid_w * *rho;
 }
 
-/* Unpacks the 16 stored values and the shift into a bm_state (derivatives
- * added apart). */
-static void unpack_fields(const orc_params* p, const double v[ORC_NF], bm_state* s) {
+/* Shift at a cell: beta^i = the constant part plus the field's value, and
+ * B_k^i = d_k beta^i / 2 by central differences of the field (reading R15;
+ * zero without a field). */
+static void shift_state(const orc_params* p, int64_t x, int64_t y, int64_t z, bm_state* s) {
+  const int64_t cells = p->nx * p->ny * p->nz;
+  for (int i = 0; i < 3; ++i) {
+    s->beta[i] = p->beta[i];
+    for (int k = 0; k < 3; ++k) s->B[k][i] = 0;
+  }
+  if (!p->beta_field) return;
+  const int64_t c = cell_index(p, x, y, z);
+  for (int i = 0; i < 3; ++i) s->beta[i] += p->beta_field[i * cells + c];
+  for (int k = 0; k < 3; ++k) {
+    const int64_t cp = cell_index(p, x + (k == 0), y + (k == 1), z + (k == 2));
+    const int64_t cm = cell_index(p, x - (k == 0), y - (k == 1), z - (k == 2));
+    for (int i = 0; i < 3; ++i)
+      s->B[k][i] = (p->beta_field[i * cells + cp] - p->beta_field[i * cells + cm]) / (4 * p->dx);
+  }
+}
+
+/* Unpacks the 16 stored values into a bm_state (derivatives and shift added
+ * apart). */
+static void unpack_fields(const double v[ORC_NF], bm_state* s) {
   s->alpha = v[F_ALPHA];
-  for (int k = 0; k < 3; ++k) s->beta[k] = p->beta[k];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
       s->g[i][j] = v[F_G + pair_of(i, j)];
@@ -501,8 +566,8 @@ static void pack_sources(const bm_rhs* r, double S[ORC_NF]) {
 
 /* Macroscopic flux of every field along each axis, read off the
  * equilibria's first moments: -beta^k K_ij + alpha lambda^k_ij for K_ij,
- * -beta^k V_i for V_i, zero for alpha and gamma_ij (their shift terms are
- * sources). s holds the fields the flux is taken at. */
+ * -beta^k V_i + B^k_i - B_i^k for V_i, zero for alpha and gamma_ij (their
+ * shift terms are sources). s holds the fields the flux is taken at. */
 static void pack_fluxes(const bm_rhs* r, const bm_state* s, double Fl[ORC_NF][3]) {
   for (int F = 0; F < ORC_NF; ++F)
     for (int k = 0; k < 3; ++k) Fl[F][k] = 0;
@@ -511,7 +576,7 @@ static void pack_fluxes(const bm_rhs* r, const bm_state* s, double Fl[ORC_NF][3]
       Fl[F_K + q][k] = s->alpha * r->lam[k][PAIR_I[q]][PAIR_J[q]] -
                        s->beta[k] * s->K[PAIR_I[q]][PAIR_J[q]];
   for (int i = 0; i < 3; ++i)
-    for (int k = 0; k < 3; ++k) Fl[F_V + i][k] = -s->beta[k] * s->V[i];
+    for (int k = 0; k < 3; ++k) Fl[F_V + i][k] = -s->beta[k] * s->V[i] + r->VB[i][k];
 }
 
 /* Steps 1-5 at one cell: given the uncorrected moments rho~ of all cells
@@ -528,7 +593,8 @@ static void cell_macro(const orc_params* p, const double* mom, int64_t cells, in
   bm_state s;
   bm_rhs r;
   derivatives(p, mom, cells, x, y, z, s.A, s.D);
-  unpack_fields(p, rt, &s);
+  shift_state(p, x, y, z, &s);
+  unpack_fields(rt, &s);
   bm_point(&s, p->slicing, mrho, mP, &r);
   pack_sources(&r, S);
   if (!p->sources_on)
@@ -536,7 +602,7 @@ static void cell_macro(const orc_params* p, const double* mom, int64_t cells, in
   /* rho = sum_l f + dt S / 2 (Sec. LBM, macroscopic variables). */
   for (int F = 0; F < ORC_NF; ++F) rho[F] = rt[F] + 0.5 * p->dt * S[F];
   /* Flux at the corrected moments with the same derivatives (R5). */
-  unpack_fields(p, rho, &s);
+  unpack_fields(rho, &s);
   bm_point(&s, p->slicing, mrho, mP, &r);
   pack_fluxes(&r, &s, Fl);
 }
@@ -575,7 +641,8 @@ int orc_init(const orc_params* p, const double* fields, double* f_out) {
     bm_state s;
     bm_rhs r;
     derivatives(p, fields, cells, x, y, z, s.A, s.D);
-    unpack_fields(p, v, &s);
+    shift_state(p, x, y, z, &s);
+    unpack_fields(v, &s);
     bm_point(&s, p->slicing, mrho, mP, &r);
     pack_sources(&r, S);
     if (!p->sources_on)
@@ -713,13 +780,14 @@ int orc_step_cells(const orc_params* p, const double* f_in, int64_t n, const int
                             moment0(&vs, cells, f_in, F_G + q, cm)) / (4 * p->dx);
           }
       }
-      unpack_fields(p, rt, &s);
+      shift_state(p, sx, sy, sz, &s);
+      unpack_fields(rt, &s);
       bm_point(&s, p->slicing, mrho, mP, &r);
       pack_sources(&r, S);
       if (!p->sources_on)
         for (int F = 0; F < ORC_NF; ++F) S[F] = 0;
       for (int F = 0; F < ORC_NF; ++F) rho[F] = rt[F] + 0.5 * p->dt * S[F];
-      unpack_fields(p, rho, &s);
+      unpack_fields(rho, &s);
       bm_point(&s, p->slicing, mrho, mP, &r);
       pack_fluxes(&r, &s, Fl);
       const double src_fac = 1.0 - 1.0 / (2.0 * p->tau);

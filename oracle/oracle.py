@@ -51,6 +51,7 @@ class Params(ctypes.Structure):
         ("fluid_w", ctypes.c_double),
         ("fluid_t0", ctypes.c_double),
         ("beta", ctypes.c_double * 3),
+        ("beta_field", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -148,10 +149,12 @@ class Oracle:
     advances it by dt per step).
 
     shift = (bx, by, bz): a constant, uniform shift beta^i (Sec. "Bona-Masso
-    evolution equations" with B = 0); default zero."""
+    evolution equations" with B = 0); default zero. shift_field: a static
+    shift field beta^i(x), [3][nz][ny][nx] (or [3][cells]), added to shift;
+    its B_k^i = d_k beta^i / 2 come from central differences."""
 
     def __init__(self, vset, shape, tau, dx, dt=None, slicing=1, sources_on=True, fluid=None,
-                 shift=None):
+                 shift=None, shift_field=None):
         nx, ny, nz = shape
         self.vset = int(vset)
         self.Q = Q_OF[self.vset]
@@ -168,6 +171,13 @@ class Oracle:
         if shift is not None:
             for k in range(3):
                 self.p.beta[k] = float(shift[k])
+        self._beta_field = None
+        if shift_field is not None:
+            bf = np.ascontiguousarray(np.asarray(shift_field, dtype=np.float64).reshape(3, -1))
+            if bf.shape[1] != self.cells:
+                raise ValueError("shift_field must hold 3 x cells values")
+            self._beta_field = bf  # kept alive: the C side holds a pointer
+            self.p.beta_field = _dp(bf)
 
     def _at(self, t):
         self.p.t = self.t0 if t is None else float(t)

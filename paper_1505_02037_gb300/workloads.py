@@ -90,6 +90,54 @@ def gauge_wave(shape, dx, A, t=0.0, direction="x", beta=None):
     return _pack(np.sqrt(H), g, K, [zero, zero, zero], shape)
 
 
+def shear_shift(shape, dx, v0):
+    """Static shift field beta = (v(y), 0, 0), v(y) = v0 sin(2 pi y / L_y):
+    [3][nz][ny][nx]."""
+    nx, ny, nz = shape
+    X, Y, Z = coords(shape, dx)
+    out = np.zeros((3, nz, ny, nx))
+    out[0] = v0 * np.sin(2 * math.pi * Y / (ny * dx))
+    return out
+
+
+def sheared_gauge_wave(shape, dx, A, v0, t=0.0):
+    """The gauge wave along x (A = 0: flat space) in coordinates carried by
+    the flow of the static shift field of shear_shift(v0): x = x' + v(y') t,
+    y = y'. In them the shift is beta = (v(y'), 0, 0), alpha keeps its
+    value, and gamma, K transform with the Jacobian J (dx/dy' = s = v'(y') t):
+    gamma'_xx = H, gamma'_xy = H s, gamma'_yy = 1 + H s^2, K' = K_xx (1, s,
+    s^2) on (xx, xy, yy). V_k is its defining combination of the exact
+    derivatives of gamma'. Harmonic slicing. Needs ny > 1."""
+    nx, ny, nz = shape
+    X, Y, Z = coords(shape, dx)
+    d = nx * dx
+    ky = 2 * math.pi / (ny * dx)
+    v = v0 * np.sin(ky * Y)
+    s = v0 * ky * np.cos(ky * Y) * t          # v'(y) t
+    s1 = -v0 * ky * ky * np.sin(ky * Y) * t   # v''(y) t
+    ph = 2 * math.pi * ((X + v * t) - t) / d
+    H = 1 - A * np.sin(ph)
+    Hx = -A * np.cos(ph) * 2 * math.pi / d
+    Kxx = -(math.pi * A / d) * np.cos(ph) / np.sqrt(H)
+    zero, one = np.zeros_like(H), np.ones_like(H)
+    g = [[H, H * s, zero], [H * s, 1 + H * s * s, zero], [zero, zero, one]]
+    K = [[Kxx, Kxx * s, zero], [Kxx * s, Kxx * s * s, zero], [zero, zero, zero]]
+    # D_kij = d_k gamma_ij / 2 (exact), then V_k = g^{rs} (D_krs - D_rsk)
+    Dx = [[Hx, Hx * s, zero], [Hx * s, Hx * s * s, zero], [zero, zero, zero]]
+    Dy = [[Hx * s, Hx * s * s + H * s1, zero],
+          [Hx * s * s + H * s1, Hx * s ** 3 + 2 * H * s * s1, zero], [zero, zero, zero]]
+    D = np.zeros((3, 3, 3) + H.shape)
+    for i in range(3):
+        for j in range(3):
+            D[0, i, j] = 0.5 * Dx[i][j]
+            D[1, i, j] = 0.5 * Dy[i][j]
+    G = np.array([[g[i][j] for j in range(3)] for i in range(3)])
+    Gi = np.linalg.inv(np.moveaxis(G, (0, 1), (-2, -1)))
+    Gi = np.moveaxis(Gi, (-2, -1), (0, 1))
+    V = np.einsum("rs...,krs...->k...", Gi, D) - np.einsum("rs...,rsk...->k...", Gi, D)
+    return _pack(np.sqrt(H), g, K, [V[0], V[1], V[2]], shape)
+
+
 def _polarisation(direction):
     if direction == "x":
         return np.array([0.0, 1.0, 0.0]), np.array([0.0, 0.0, 1.0])

@@ -121,3 +121,43 @@ def test_transverse_shift_components_drop_out_of_an_x_wave(oracle_mod, vset):
     c = O.Oracle(1, (N, 1, 1), 1.5, 1 / N)
     m0 = c.moments(c.run(c.init(f1), 20)).reshape(16, 1, 1, N)
     assert np.abs(m0 - m1).max() > 1e-3
+
+
+# ---------------------------------------------------------------------------
+# Static shift field: B_k^i = d_k beta^i / 2 terms
+# ---------------------------------------------------------------------------
+def _sheared_errors(O, N, A, v0=0.1, t=0.25, tau=1.0):
+    shape = (N, N, 1)
+    o = O.Oracle(2, shape, tau, 1 / N, shift_field=W.shear_shift(shape, 1 / N, v0))
+    f = o.run(o.init(W.sheared_gauge_wave(shape, 1 / N, A, v0)), int(round(t * N)))
+    ex = W.sheared_gauge_wave(shape, 1 / N, A, v0, t=t).reshape(16, -1)
+    return np.abs(o.moments(f) - ex).max(axis=1)
+
+
+@pytest.mark.parametrize("A", [0.0, 0.01])
+def test_sheared_coordinates_converge_to_their_closed_form(oracle_mod, A):
+    """Flat space (A = 0) and the gauge wave (A = 0.01) carried by the flow
+    of the static shear shift beta = (0.1 sin(2 pi y), 0, 0): gamma_xy,
+    gamma_yy, K_xy, K_yy and both V_x and V_y are nonzero, so every B term
+    (metric source, K source, V flux and V source) acts. D2Q9, tau/dt = 1,
+    t = 1/4: each nonzero field's error falls linearly with the spacing."""
+    E = np.array([_sheared_errors(oracle_mod, N, A) for N in (64, 128, 256)])
+    live = E[-1] > 0
+    orders = np.log2(E[:-1, live] / E[1:, live])
+    assert live[[2, 4, 8, 10, 13, 14]].all()
+    assert np.all((orders > 0.85) & (orders < 1.25)), (E, orders)
+    assert E[-1].max() < 0.01
+
+
+def test_uniform_shift_field_is_the_constant_shift(oracle_mod):
+    """A uniform field has B = 0: it runs exactly as the same constant shift."""
+    O = oracle_mod
+    shape = (16, 12, 1)
+    f0 = W.add_noise(W.smooth_modes(shape, 1 / 16, 0.01, 5), 1e-4, 6)
+    beta = (0.2, -0.1, 0.05)
+    field = np.broadcast_to(np.array(beta).reshape(3, 1, 1, 1), (3, 1, 12, 16)).copy()
+    a = O.Oracle(2, shape, 0.9, 1 / 16, shift=beta)
+    b = O.Oracle(2, shape, 0.9, 1 / 16, shift_field=field)
+    fa, fb = a.init(f0), b.init(f0)
+    assert np.array_equal(fa, fb)
+    assert np.array_equal(a.run(fa, 3), b.run(fb, 3))
