@@ -42,7 +42,7 @@ sys.path.insert(0, ROOT)
 from paper_1505_02037_gb300 import workloads as W  # noqa: E402
 
 WORKLOADS = {
-    # name: (vset, N, storage, direction, A[, wave, streaming, shift])
+    # name: (vset, N, storage, direction, A[, wave, streaming, shift, shift field amplitude])
     "gauge3d-256-f32": (3, 256, "f32", "x", 0.1),
     "gauge3d-256-dev_bf16": (3, 256, "dev_bf16", "x", 0.1),
     "gauge3d-256-dev_f16": (3, 256, "dev_f16", "x", 0.1),
@@ -56,7 +56,11 @@ WORKLOADS = {
     # (larger shifts raise the scheme's amplification factor; this one keeps
     # the 256^3 run stable at tau = 4.5)
     "gauge3d-256-f32-shift": (3, 256, "f32", "x", 0.1, "gauge", "auto", (0.1, 0.05, -0.05)),
+    # plus a smooth static shift field of amplitude 0.05 (seeded): every B term
+    "gauge3d-256-f32-shiftfield": (3, 256, "f32", "x", 0.1, "gauge", "auto", (0.1, 0.05, -0.05),
+                                   0.05),
 }
+SHIFT_FIELD_SEED = 1505
 
 
 def workload(name):
@@ -70,6 +74,13 @@ def workload(name):
 def shift_of(name):
     t = WORKLOADS.get(name, ())
     return t[7] if len(t) > 7 else None
+
+
+def shift_field_of(name, shape, dx):
+    t = WORKLOADS.get(name, ())
+    if len(t) <= 8:
+        return None
+    return W.smooth_shift(shape, dx, t[8], SHIFT_FIELD_SEED)
 
 
 def fields_for(wave, shape, dx, A, direction, beta=None):
@@ -223,13 +234,15 @@ def traffic_for(kernel_key, cells):
     return e["dram_bytes_per_cell"] * cells
 
 
-def cpu_baseline(vset, storage, direction, A, tau, wave="gauge", seconds=12.0, beta=None):
+def cpu_baseline(vset, storage, direction, A, tau, wave="gauge", seconds=12.0, beta=None,
+                 field_fn=None):
     """The FP64 oracle as it stands, on this host's cores, on a bounded sample
     of the same workload (a 48^3 periodic piece of the same wave, same tau)."""
     from oracle import oracle as O
     n = 48
     shape = (n, n, n) if vset == 3 else (n, n, 1)
-    o = O.Oracle(vset, shape, tau, 1 / n, slicing=0 if wave == "linear" else 1, shift=beta)
+    o = O.Oracle(vset, shape, tau, 1 / n, slicing=0 if wave == "linear" else 1, shift=beta,
+                 shift_field=field_fn(shape, 1 / n) if field_fn else None)
     f = o.init(fields_for(wave, shape, 1 / n, A, direction, beta))
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     steps, t0 = 0, time.perf_counter()
@@ -252,7 +265,9 @@ def workload_config(args, streaming_name="ping-pong"):
     return {
         "workload": f"3D {wave} wave along {direction}, D3Q19 {N}^3 periodic, "
                     f"{storage} storage, A={A}, tau={args.tau}, {streaming_name} streaming"
-                    + (f", constant shift beta={beta}" if beta else ""),
+                    + (f", constant shift beta={beta}" if beta else "")
+                    + (f", static shift field (amplitude {WORKLOADS[args.workload][8]}, "
+                       f"seed {SHIFT_FIELD_SEED})" if len(WORKLOADS[args.workload]) > 8 else ""),
         "workload_key": args.workload, "cells": N ** 3, "fields": 16, "velocities": 19,
         "tau_note": "tau=0.6 of the configuration is linearly unstable for this scheme "
                     "(blows up near step 100 at any N and A); cost per step does not "
@@ -271,7 +286,7 @@ def run_reference(args):
     n = 24
     beta = shift_of(args.workload)
     o = O.Oracle(vset, (n, n, n), args.tau, 1 / n, slicing=0 if wave == "linear" else 1,
-                 shift=beta)
+                 shift=beta, shift_field=shift_field_of(args.workload, (n, n, n), 1 / n))
     f = o.init(fields_for(wave, (n, n, n), 1 / n, A, direction, beta))
     for _ in range(args.warmup):
         f = o.step(f)
@@ -522,6 +537,10 @@ def main():
                                   "aa": lbnr.LBNR_STREAM_AA}[streaming])
     if beta:
         lat.set_shift(beta)
+    sfield = shift_field_of(args.workload, shape, 1 / N)
+    if sfield is not None:
+        lat.set_shift_field(sfield)
+        del sfield
     lat.init(fields)
 
     def barrier():
@@ -539,7 +558,8 @@ def main():
         tuning = {}
     else:
         tuning = autotune.tune(lat)
-    form = "P1-reread-shift" if beta else lat.variants[lat.variant]
+    form = ("P1-reread-shiftfield" if len(WORKLOADS[args.workload]) > 8
+            else "P1-reread-shift" if beta else lat.variants[lat.variant])
     lat.step(args.warmup)
     barrier()
     stream = lat.stream
@@ -644,8 +664,10 @@ def main():
                        "steps_per_transfer": k}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(vset, storage, direction, A, args.tau, wave,
-                                            beta=beta)
+        line["cpu_baseline"] = cpu_baseline(
+            vset, storage, direction, A, args.tau, wave, beta=beta,
+            field_fn=(lambda sh, dx: shift_field_of(args.workload, sh, dx))
+            if len(WORKLOADS[args.workload]) > 8 else None)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -169,6 +169,22 @@ int lbnr_set_fluid(lbnr_ctx* ctx, double rho0, double w, double t0);
  * Errors: LBNR_EINVAL for a null context or non-finite values. */
 int lbnr_set_shift(lbnr_ctx* ctx, double bx, double by, double bz);
 
+/* Shift field (Sec. "Bona-Masso evolution equations"): a prescribed, static
+ * beta^i(x), host beta[3][cells] (x fastest), added to the constant shift of
+ * lbnr_set_shift; a gauge choice (the shift equation's Q_i is left free).
+ * B_k^i = d_k beta^i / 2 comes from central differences of the field, and
+ * the step gains every B term: s_ij = (B_ij + B_ji)/alpha in the metric
+ * source, (2/alpha)(K_ir B_j^r + K_jr B_i^r - K_ij trB) in S_ij,
+ * 2(B_k^r - delta_k^r trB)V_r + 2(D_rk^s - delta^s_k D^j_jr)B^r_s in Omega_k,
+ * and B^r_k - B_k^r in the flux of V_k along r. The field is copied to a
+ * device buffer of 24 bytes per cell that the context allocates on the first
+ * call and owns (freed by lbnr_destroy or a call with beta = NULL, which
+ * removes the field). The collide step then runs its shift-field launch form
+ * (one thread per cell). Call before lbnr_init. Errors: LBNR_EINVAL for a
+ * null context or a non-finite value, LBNR_ECUDA if the buffer cannot be
+ * allocated. */
+int lbnr_set_shift_field(lbnr_ctx* ctx, const double* beta);
+
 /* Thread-to-cell layouts of the collide kernel available for this context's
  * set and storage (all give the same results): their number, a short name,
  * and the selection (default 0). Used by the autotuner. */

@@ -134,6 +134,7 @@ __device__ void run_steps(const BatchParams& p, const BatchRun& R, const Assign&
   a.clock = nullptr;  // batched runs are vacuum, zero shift
   a.fluid_P0 = a.fluid_t0 = a.fluid_dt = 0;
   a.beta[0] = a.beta[1] = a.beta[2] = C(0);
+  a.beta_field = nullptr;
   C* const aux = static_cast<C*>(R.aux);
   const int64_t cells = a.G.cells;
   const int64_t B = blockDim.x;

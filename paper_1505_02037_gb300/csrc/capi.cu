@@ -101,6 +101,7 @@ struct lbnr_ctx {
   int64_t steps = 0;
   cudaGraphExec_t cycle[2] = {nullptr, nullptr};  // two-step cycle from even / odd step
   double fluid_rho0 = 0, fluid_w = 0, fluid_t0 = 1;  // perfect fluid (rho0 = 0: vacuum)
+  double* beta_field = nullptr;  // static shift field [3][cells] (owned)
   std::string err;
 };
 
@@ -394,6 +395,7 @@ int lbnr_create(const lbnr_grid* grid, int vset, double tau, double dx, double d
   L.fluid_P0 = L.fluid_t0 = L.fluid_P_now = 0;
   L.beta[0] = L.beta[1] = L.beta[2] = 0;
   L.shift_on = 0;
+  L.beta_field = nullptr;
   // zero everything once: the plane padding must hold finite values
   cudaError_t e = cudaMemsetAsync(c->base, 0, Ly.total, c->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
@@ -617,8 +619,32 @@ int lbnr_set_shift(lbnr_ctx* c, double bx, double by, double bz) {
   c->L.beta[0] = bx;
   c->L.beta[1] = by;
   c->L.beta[2] = bz;
-  c->L.shift_on = (bx != 0.0 || by != 0.0 || bz != 0.0) ? 1 : 0;
+  c->L.shift_on = (bx != 0.0 || by != 0.0 || bz != 0.0 || c->L.beta_field) ? 1 : 0;
   drop_graphs(c);  // the captured steps carry the old parameters
+  return LBNR_OK;
+}
+
+int lbnr_set_shift_field(lbnr_ctx* c, const double* beta) {
+  if (!c) return fail(c, LBNR_EINVAL, "null context");
+  const int64_t cells = c->L.cells;
+  if (beta) {
+    for (int64_t i = 0; i < 3 * cells; ++i)
+      if (!std::isfinite(beta[i])) return fail(c, LBNR_EINVAL, "shift field value %lld not finite", (long long)i);
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  if (beta) {
+    if (!c->beta_field)
+      CUDA_TRY(c, cudaMalloc(reinterpret_cast<void**>(&c->beta_field), sizeof(double) * 3 * cells));
+    CUDA_TRY(c, cudaMemcpy(c->beta_field, beta, sizeof(double) * 3 * cells, cudaMemcpyHostToDevice));
+    c->L.beta_field = c->beta_field;
+  } else {
+    if (c->beta_field) cudaFree(c->beta_field);
+    c->beta_field = nullptr;
+    c->L.beta_field = nullptr;
+  }
+  const double* b = c->L.beta;
+  c->L.shift_on = (b[0] != 0.0 || b[1] != 0.0 || b[2] != 0.0 || c->L.beta_field) ? 1 : 0;
+  drop_graphs(c);
   return LBNR_OK;
 }
 
@@ -641,6 +667,7 @@ void lbnr_destroy(lbnr_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   drop_graphs(c);
   if (c->own_mem && c->base) cudaFree(c->base);
+  if (c->beta_field) cudaFree(c->beta_field);
   if (c->own_stream && c->st) cudaStreamDestroy(c->st);
   delete c;
 }

@@ -30,9 +30,11 @@ struct LaunchCtx {
   // the pressure at the state the FP64 moment calls read.
   const int64_t* clock;
   double fluid_P0, fluid_t0, fluid_P_now;
-  // Constant shift beta^i; shift_on = 0 when all three are zero.
+  // Shift: constant beta^i plus an optional static field [3][cells] (FP64,
+  // nullptr: none); shift_on = 0 when both are absent or zero.
   double beta[3];
   int shift_on;
+  const double* beta_field;
 };
 
 // layout: 0 ping-pong, 1 AA at even step, 2 AA at odd step

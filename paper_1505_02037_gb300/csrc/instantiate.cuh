@@ -141,10 +141,10 @@ struct Impl {
     return cudaGetLastError();
   }
 
-  template <int LAYOUT>
+  template <int LAYOUT, int SHIFT>
   static cudaError_t launch_shifted(const LaunchCtx& L, const StepArgs<S, C>& a) {
     const int block = 128;
-    k_collide<Q, S, C, REP, LAYOUT, 1, false, true><<<grid_for(L.cells, block), block, 0, L.st>>>(a);
+    k_collide<Q, S, C, REP, LAYOUT, 1, false, SHIFT><<<grid_for(L.cells, block), block, 0, L.st>>>(a);
     return cudaGetLastError();
   }
 
@@ -228,11 +228,18 @@ struct Impl {
     a.fluid_t0 = L.fluid_t0;
     a.fluid_dt = L.dt;
     for (int k = 0; k < 3; ++k) a.beta[k] = C(L.beta[k]);
+    a.beta_field = L.beta_field;
+    if (L.beta_field) {
+      // A shift field: its own form (B terms), P1-reread, any layout.
+      if (layout == kPingPong) return launch_shifted<kPingPong, 2>(L, a);
+      if (layout == kAAEven) return launch_shifted<kAAEven, 2>(L, a);
+      return launch_shifted<kAAOdd, 2>(L, a);
+    }
     if (L.shift_on) {
-      // One launch form carries the shift terms: P1-reread, any layout.
-      if (layout == kPingPong) return launch_shifted<kPingPong>(L, a);
-      if (layout == kAAEven) return launch_shifted<kAAEven>(L, a);
-      return launch_shifted<kAAOdd>(L, a);
+      // One launch form carries the constant shift: P1-reread, any layout.
+      if (layout == kPingPong) return launch_shifted<kPingPong, 1>(L, a);
+      if (layout == kAAEven) return launch_shifted<kAAEven, 1>(L, a);
+      return launch_shifted<kAAOdd, 1>(L, a);
     }
     if (layout == kPingPong) return collide_layout<kPingPong>(L, variant, a);
     if (layout == kAAEven) return collide_layout<kAAEven>(L, variant, a);
@@ -264,6 +271,7 @@ struct Impl {
     a.fluidP = L.clock ? L.fluid_P0 : 0.0;  // the initial state is at t0
     for (int k = 0; k < 3; ++k) a.beta[k] = L.beta[k];
     a.shift_on = L.shift_on;
+    a.beta_field = L.beta_field;
     k_init<Q, S, REP><<<grid_for(L.cells, 128), 128, 0, L.st>>>(a);
     return cudaGetLastError();
   }
@@ -287,7 +295,7 @@ struct Impl {
     k_correct64<Q><<<grid_for(L.cells, 128), 128, 0, L.st>>>(
         L.macro, L.aux64, G, 1.0 / (2.0 * L.dx), 1.0 / (4.0 * L.dx), 0.5 * L.dt, L.slicing,
         L.sources_on, L.clock ? L.fluid_P_now : 0.0, L.shift_on ? L.beta[0] : 0.0,
-        L.shift_on ? L.beta[1] : 0.0, L.shift_on ? L.beta[2] : 0.0);
+        L.shift_on ? L.beta[1] : 0.0, L.shift_on ? L.beta[2] : 0.0, L.beta_field);
     return cudaGetLastError();
   }
 

@@ -249,8 +249,11 @@ struct StepArgs {
   // clock == nullptr is vacuum.
   const int64_t* clock;
   double fluid_P0, fluid_t0, fluid_dt;
-  // Constant shift beta^i (B = 0), read by the forms compiled with SHIFT.
+  // Shift, read by the forms compiled with SHIFT: the constant beta^i, and
+  // with SHIFT = 2 also a static field beta_field[3][cells] (FP64) added to
+  // it, whose central differences give B_k^i.
   C beta[3];
+  const double* beta_field;
 };
 
 // Adds the fluid's term (P/2) gamma_ij to the sources of K_ij (alpha S_ij),
@@ -285,6 +288,33 @@ __device__ __forceinline__ void shift_flux_k(const C beta[3], const C K[6], C Fl
   for (int k = 0; k < dim; ++k)
 #pragma unroll
     for (int q = 0; q < 6; ++q) Fl[q][k] -= beta[k] * K[q];
+}
+
+// Shift at a cell with a static field: beta^i = the constant part + the
+// field's value; B_k^i = d_k beta^i / 2 by central differences (zero along
+// the axes the velocity set does not span).
+template <int Q, class C>
+__device__ __forceinline__ void shift_field_at(const Nbr& n, int64_t cells,
+                                               const double* __restrict__ bf, const C beta0[3],
+                                               double inv4dx, C beta[3], C B[3][3]) {
+  constexpr int dim = Lattice<Q>::kDim;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) beta[i] = beta0[i] + C(__ldg(bf + (size_t)i * (size_t)cells + n.c));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (k < dim) {
+      const uint32_t cp = n.at(k == 0, k == 1, k == 2);
+      const uint32_t cm = n.at(-(k == 0), -(k == 1), -(k == 2));
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const double* pl = bf + (size_t)i * (size_t)cells;
+        B[k][i] = C((__ldg(pl + cp) - __ldg(pl + cm)) * inv4dx);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) B[k][i] = C(0);
+    }
+  }
 }
 
 // A_k and D_kij by central differences of the aux planes (reading: second
@@ -329,9 +359,10 @@ __device__ __forceinline__ void unpack(const C m[kNF], C& alpha, C g[6], C K[6],
 // ---------------------------------------------------------------------------
 // k_collide: the fused step
 // ---------------------------------------------------------------------------
-// SHIFT: the shift terms are compiled in (a.beta); the zero-shift forms keep
-// none of their code or registers.
-template <int Q, class S, class C, int REP, int LAYOUT, int P, bool HOLD, bool SHIFT = false>
+// SHIFT: the shift terms are compiled in: 1 a constant shift (a.beta),
+// 2 a static field on top of it (a.beta_field, with its B terms). The
+// zero-shift forms (0) keep none of their code or registers.
+template <int Q, class S, class C, int REP, int LAYOUT, int P, bool HOLD, int SHIFT = 0>
 __global__ void __launch_bounds__(128, HOLD ? 1 : 3) k_collide(const StepArgs<S, C> a) {
   using L = Lattice<Q>;
   constexpr int NJ = kNF / P;
@@ -395,7 +426,13 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : 3) k_collide(const StepArgs<S,
   C Sr[kNF];
   bm_sources<C>(alpha, gm, K, V, A, D, a.slicing, Sr);
   add_fluid(a, alpha, gm, Sr);
-  if (SHIFT) shift_sources<C>(a.beta, alpha, A, D, Sr);
+  C sb[3], sB[3][3];  // shift and B_k^i at this cell (SHIFT = 2)
+  if (SHIFT == 1) shift_sources<C>(a.beta, alpha, A, D, Sr);
+  if (SHIFT == 2) {
+    shift_field_at<Q, C>(n, cells, a.beta_field, a.beta, (double)a.inv4dx, sb, sB);
+    shift_sources<C>(sb, alpha, A, D, Sr);
+    shift_field_sources<C>(gm, K, V, D, sB, Sr);
+  }
   if (!a.sources_on) {
 #pragma unroll
     for (int F = 0; F < kNF; ++F) Sr[F] = C(0);
@@ -404,11 +441,16 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : 3) k_collide(const StepArgs<S,
 #pragma unroll
   for (int F = 0; F < kNF; ++F) rho[F] = rt[F] + a.half_dt * Sr[F];
   C Fl[6][3];
+  C Fv[SHIFT == 2 ? 3 : 1][3];  // V fluxes under a shift field
   {
     C alpha2, g2[6], K2[6], V2[3];
     unpack<REP, C>(rho, alpha2, g2, K2, V2);
     bm_flux<C, dim>(alpha2, g2, V2, A, D, Fl);
-    if (SHIFT) shift_flux_k<C, dim>(a.beta, K2, Fl);
+    if (SHIFT == 1) shift_flux_k<C, dim>(a.beta, K2, Fl);
+    if (SHIFT == 2) {
+      shift_flux_k<C, dim>(sb, K2, Fl);
+      shift_field_vflux<C, dim>(g2, V2, sb, sB, Fv);
+    }
   }
   // Per-field coefficients: coef = omega rho + sigma S; flux scaled by 3 omega.
   C coef[kNF];
@@ -445,7 +487,12 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : 3) k_collide(const StepArgs<S,
       v_[l] = HOLD ? fv[HOLD ? j : 0][HOLD ? l : 0]
               : LAYOUT == kPingPong ? Codec<S>::load(src) : Codec<S>::load_coh(src);
     }
-    if (vflux) {
+    if (vflux && SHIFT == 2) {
+      if (is_v(F)) {
+#pragma unroll
+        for (int k = 0; k < dim; ++k) b[k] = three_omega * Fv[SHIFT == 2 ? F - kV : 0][k];
+      }
+    } else if (vflux) {
       // V_i at the corrected moments, recovered from this field's own values
       // rather than kept live since pass 1: coef = omega rho~ + dt S (as
       // omega dt/2 + sigma = dt), so rho = rho~ + (coef - omega rho~) / 2.
@@ -645,6 +692,7 @@ struct Init64Args {
   double fluidP;  // fluid pressure at the initial time (0: vacuum)
   double beta[3];  // constant shift
   int shift_on;
+  const double* beta_field;  // static shift field [3][cells] or nullptr
 };
 
 // Shifted equilibrium: f = f_eq(rho0) - (dt/2) w_l S(rho0), A and D from rho0.
@@ -680,12 +728,18 @@ __global__ void __launch_bounds__(128) k_init(const Init64Args<S> a) {
   unpack<kABS, double>(r, alpha, gm, K, V);
   double Sr[kNF];
   bm_sources<double>(alpha, gm, K, V, A, D, a.slicing, Sr, a.fluidP);
-  if (a.shift_on) shift_sources<double>(a.beta, alpha, A, D, Sr);
+  double sb[3] = {a.beta[0], a.beta[1], a.beta[2]}, sB[3][3];
+  if (a.beta_field) {
+    shift_field_at<Q, double>(n, cells, a.beta_field, a.beta, a.inv4dx, sb, sB);
+    shift_field_sources<double>(gm, K, V, D, sB, Sr);
+  }
+  if (a.shift_on) shift_sources<double>(sb, alpha, A, D, Sr);
   if (!a.sources_on)
     for (int F = 0; F < kNF; ++F) Sr[F] = 0;
-  double Fl[6][3];
+  double Fl[6][3], Fv[3][3];
   bm_flux<double, dim>(alpha, gm, V, A, D, Fl);
-  if (a.shift_on) shift_flux_k<double, dim>(a.beta, K, Fl);
+  if (a.shift_on) shift_flux_k<double, dim>(sb, K, Fl);
+  if (a.beta_field) shift_field_vflux<double, dim>(gm, V, sb, sB, Fv);
   bool bad = false;
 #pragma unroll
   for (int F = 0; F < kNF; ++F) {
@@ -696,9 +750,12 @@ __global__ void __launch_bounds__(128) k_init(const Init64Args<S> a) {
 #pragma unroll
         for (int k = 0; k < dim; ++k) cf += L::c(l, k) * Fl[F - kK][k];
       }
-      if (is_v(F) && a.shift_on) {
+      if (is_v(F) && a.beta_field) {
 #pragma unroll
-        for (int k = 0; k < dim; ++k) cf += L::c(l, k) * (-a.beta[k] * r[F]);
+        for (int k = 0; k < dim; ++k) cf += L::c(l, k) * Fv[F - kV][k];
+      } else if (is_v(F) && a.shift_on) {
+#pragma unroll
+        for (int k = 0; k < dim; ++k) cf += L::c(l, k) * (-sb[k] * r[F]);
       }
       // f = w (rho + 3 c.F) - (dt/2) w S
       double v;
@@ -763,7 +820,8 @@ __global__ void __launch_bounds__(128) k_correct64(double* __restrict__ macro,
                                                    const double* __restrict__ aux64, Grid G,
                                                    double inv2dx, double inv4dx, double half_dt,
                                                    int slicing, int sources_on, double fluidP,
-                                                   double bx, double by, double bz) {
+                                                   double bx, double by, double bz,
+                                                   const double* __restrict__ beta_field) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= G.cells || !sources_on) return;
   const Nbr n = make_nbr(G, c);
@@ -776,10 +834,14 @@ __global__ void __launch_bounds__(128) k_correct64(double* __restrict__ macro,
   unpack<kABS, double>(r, alpha, gm, K, V);
   double S[kNF];
   bm_sources<double>(alpha, gm, K, V, A, D, slicing, S, fluidP);
-  if (bx != 0.0 || by != 0.0 || bz != 0.0) {
-    const double beta[3] = {bx, by, bz};
-    shift_sources<double>(beta, alpha, A, D, S);
+  double sb[3] = {bx, by, bz};
+  if (beta_field) {
+    const double b0[3] = {bx, by, bz};
+    double sB[3][3];
+    shift_field_at<Q, double>(n, G.cells, beta_field, b0, inv4dx, sb, sB);
+    shift_field_sources<double>(gm, K, V, D, sB, S);
   }
+  if (beta_field || bx != 0.0 || by != 0.0 || bz != 0.0) shift_sources<double>(sb, alpha, A, D, S);
 #pragma unroll
   for (int F = 0; F < kNF; ++F) macro[(int64_t)F * G.cells + c] = r[F] + half_dt * S[F];
 }

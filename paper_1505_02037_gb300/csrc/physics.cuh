@@ -235,4 +235,95 @@ __device__ __forceinline__ void bm_flux(const T alpha, const T g[6], const T V[3
     for (int q = 0; q < 6; ++q) F[q][k] = T(0);
 }
 
+// Shift-field terms (Sec. "Bona-Masso evolution equations"; B_k^i =
+// d_k beta^i / 2, B[k][i]): added to the sources S (metric, K_ij: alpha S_ij,
+// V: Omega_k) at the point, with B_ij = B_i^m gamma_mj, B^r_s = g^{rl} B_ls.
+//   gamma_ij: 2 (B_ij + B_ji)
+//   K_ij:     2 (K_ir B_j^r + K_jr B_i^r - K_ij tr B)
+//   V_k:      2 (B_k^r - delta_k^r tr B) V_r + 2 (D_rk^s - delta^s_k D^j_jr) B^r_s
+template <class T>
+__device__ __forceinline__ void shift_field_sources(const T g[6], const T K[6], const T V[3],
+                                                    const T D[3][6], const T B[3][3],
+                                                    T S[16]) {
+  T gi[6];
+  invert_sym3(g, gi);
+  T Bl[3][3], Bul[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      Bl[i][j] = B[i][0] * g[sym(0, j)] + B[i][1] * g[sym(1, j)] + B[i][2] * g[sym(2, j)];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      Bul[i][j] = gi[sym(i, 0)] * Bl[0][j] + gi[sym(i, 1)] * Bl[1][j] + gi[sym(i, 2)] * Bl[2][j];
+  const T trB = B[0][0] + B[1][1] + B[2][2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      const int q = sym(i, j);
+      S[1 + q] += T(2) * (Bl[i][j] + Bl[j][i]);
+      T t = -K[q] * trB;
+#pragma unroll
+      for (int r = 0; r < 3; ++r) t += K[sym(i, r)] * B[j][r] + K[sym(j, r)] * B[i][r];
+      S[7 + q] += T(2) * t;
+    }
+  // D^j_jr = g^{ja} D_jar
+  T Dt2[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    T t = T(0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) t += gi[sym(j, a)] * D[j][sym(a, r)];
+    Dt2[r] = t;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    T t = T(0);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) t += (B[k][r] - (k == r ? trB : T(0))) * V[r];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+#pragma unroll
+      for (int s2 = 0; s2 < 3; ++s2) {
+        // D_rk^s = g^{sm} D_rkm
+        const T Drks = gi[sym(s2, 0)] * D[r][sym(k, 0)] + gi[sym(s2, 1)] * D[r][sym(k, 1)] +
+                       gi[sym(s2, 2)] * D[r][sym(k, 2)];
+        t += (Drks - (s2 == k ? Dt2[r] : T(0))) * Bul[r][s2];
+      }
+    }
+    S[13 + k] += T(2) * t;
+  }
+}
+
+// Flux of V_i along k under a shift field: -beta^k V_i + B^k_i - B_i^k
+// (the V equation's flux; B^k_i = g^{kl} B_l^m gamma_mi).
+template <class T, int dim>
+__device__ __forceinline__ void shift_field_vflux(const T g[6], const T V[3], const T beta[3],
+                                                  const T B[3][3], T Fv[3][3]) {
+  T gi[6];
+  invert_sym3(g, gi);
+  T Bl[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      Bl[i][j] = B[i][0] * g[sym(0, j)] + B[i][1] * g[sym(1, j)] + B[i][2] * g[sym(2, j)];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if (k < dim) {
+        const T Bki = gi[sym(k, 0)] * Bl[0][i] + gi[sym(k, 1)] * Bl[1][i] + gi[sym(k, 2)] * Bl[2][i];
+        Fv[i][k] = -beta[k] * V[i] + Bki - B[i][k];
+      } else {
+        Fv[i][k] = T(0);
+      }
+    }
+}
+
 }  // namespace lbnr

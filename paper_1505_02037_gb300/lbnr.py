@@ -93,6 +93,7 @@ def library(path: str | None = None):
     L.lbnr_set_variant.argtypes = [vp, ctypes.c_int]
     L.lbnr_set_fluid.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     L.lbnr_set_shift.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    L.lbnr_set_shift_field.argtypes = [vp, vp]
     L.lbnr_constraint_norms_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(Grid),
                                                  ctypes.c_double, vp, vp, vp]
     L.lbnr_default_batch_opts.argtypes = [ctypes.POINTER(BatchOpts)]
@@ -238,6 +239,11 @@ def lbnr_set_fluid(ctx, rho0: float, w: float, t0: float):
 
 def lbnr_set_shift(ctx, bx: float, by: float, bz: float):
     _check(library().lbnr_set_shift(ctx, float(bx), float(by), float(bz)), ctx)
+
+
+def lbnr_set_shift_field(ctx, beta):
+    """beta: host float64 [3][cells] (C-contiguous) or None to remove."""
+    _check(library().lbnr_set_shift_field(ctx, None if beta is None else _host_ptr(beta)), ctx)
 
 
 def lbnr_constraint_norms_noalloc(vset: int, grid: Grid, dx: float, d_fields, d_out,
@@ -390,6 +396,15 @@ class Lattice:
         """Constant shift beta^i = (bx, by, bz) (call before init)."""
         bx, by, bz = (float(v) for v in beta)
         lbnr_set_shift(self.ctx, bx, by, bz)
+
+    def set_shift_field(self, field):
+        """Static shift field beta^i(x), [3][nz][ny][nx] or [3][cells], or
+        None to remove it (call before init)."""
+        if field is None:
+            lbnr_set_shift_field(self.ctx, None)
+            return
+        f = np.ascontiguousarray(np.asarray(field, dtype=np.float64).reshape(3, self.cells))
+        lbnr_set_shift_field(self.ctx, f)
 
     def step_timed(self, n=1):
         return lbnr_step_timed(self.ctx, n)

@@ -9,7 +9,8 @@ Prints the per-kernel milliseconds of the timed steps (CUDA events). Used to
 capture ncu reports of a single kernel on a small case. With --batch R the
 batched ensemble kernel advances R copies of the wave (tau 2.0) by --steps
 steps in each of four launches. With --shift the lattice carries that
-constant shift and runs the shift-carrying launch form (--variant is ignored).
+constant shift and runs the shift-carrying launch form (--variant is ignored);
+--shift-field AMP adds a seeded smooth static shift field (its own form).
 """
 from __future__ import annotations
 
@@ -33,6 +34,8 @@ def main(argv=None):
     p.add_argument("--block", type=int, default=256)
     p.add_argument("--per-sm", type=int, default=1)
     p.add_argument("--shift", default=None, help="bx,by,bz")
+    p.add_argument("--shift-field", type=float, default=0.0,
+                   help="amplitude of a seeded smooth static shift field")
     a = p.parse_args(argv)
     if a.batch:
         return batch_main(a)
@@ -46,11 +49,14 @@ def main(argv=None):
     beta = tuple(float(v) for v in a.shift.split(",")) if a.shift else None
     if beta:
         lat.set_shift(beta)
+    if a.shift_field:
+        lat.set_shift_field(W.smooth_shift(shape, 1 / n, a.shift_field, 1505))
     lat.init(W.gauge_wave(shape, 1 / n, 0.1, beta=beta))
     lat.step(a.steps)
     lat.status()
     ms = lat.step_timed(4)
-    form = "P1-reread-shift" if beta else lat.variants[a.variant]
+    form = ("P1-reread-shiftfield" if a.shift_field else
+            "P1-reread-shift" if beta else lat.variants[a.variant])
     print(f"{a.storage} n={n} vset={a.vset} {form}: "
           f"ms per step aux {ms[0] / 4:.4f} collide {ms[1] / 4:.4f}")
     return 0

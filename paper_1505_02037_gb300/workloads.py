@@ -100,6 +100,28 @@ def shear_shift(shape, dx, v0):
     return out
 
 
+def smooth_shift(shape, dx, amp, seed, modes=1):
+    """A seeded smooth periodic shift field [3][nz][ny][nx]: per component a
+    few Fourier modes of amplitude amp along the lattice's axes of extent
+    > 1 (no constant part)."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = shape
+    X, Y, Z = coords(shape, dx)
+    L = (nx * dx, ny * dx, nz * dx)
+    live = [a for a, n in enumerate(shape) if n > 1]
+    out = np.zeros((3, nz, ny, nx))
+    for i in range(3):
+        for _ in range(2):
+            k = np.zeros(3)
+            for a in live:
+                k[a] = rng.integers(-modes, modes + 1) / L[a]
+            if not k.any() and live:
+                k[live[0]] = 1.0 / L[live[0]]
+            ph = 2 * math.pi * (k[0] * X + k[1] * Y + k[2] * Z) + rng.uniform(0, 2 * math.pi)
+            out[i] += amp * rng.uniform(0.5, 1.0) * np.sin(ph)
+    return out
+
+
 def sheared_gauge_wave(shape, dx, A, v0, t=0.0):
     """The gauge wave along x (A = 0: flat space) in coordinates carried by
     the flow of the static shift field of shear_shift(v0): x = x' + v(y') t,

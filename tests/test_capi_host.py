@@ -134,6 +134,7 @@ def test_set_fluid_rejects_bad_arguments(lib):
 def test_set_shift_rejects_a_null_context(lib):
     assert lib.lbnr_set_shift(None, 0.1, 0.0, 0.0) == -1
     assert lib.lbnr_set_shift(None, float("nan"), 0.0, 0.0) == -1
+    assert lib.lbnr_set_shift_field(None, None) == -1
 
 
 @pytest.mark.parametrize("vset,shape", [

@@ -261,3 +261,163 @@ def test_full_size_256_cubed_with_shift(L, oracle_mod, storage, streaming):
         err = float(np.abs(m - o.moments(f)[:, None, :]).max() / A)
         assert err <= bound(storage, True, N, tau, n, lam), (n, err)
     lat.close()
+
+
+# ---------------------------------------------------------------------------
+# Static shift field (B terms)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("vset,shape", [
+    (2, (37, 23, 1)), (3, (21, 13, 11)), (3, (2, 5, 3)), (1, (333, 1, 1)),
+])
+@pytest.mark.parametrize("streaming", [1, 2])
+def test_random_state_steps_with_shift_field_fp64(L, oracle_mod, vset, shape, streaming):
+    """Seeded random near-flat distributions under a constant shift plus a
+    smooth seeded field (every B term active), ragged lattices, 1, 2 and 3
+    steps (both AA parities)."""
+    Q = {1: 3, 2: 9, 3: 19}[vset]
+    _, w = oracle_mod.velocity_set(vset)
+    f0 = W.random_distributions(Q, w, shape, seed=3000 + vset)
+    field = W.smooth_shift(shape, 1 / shape[0], 0.1, seed=40 + vset)
+    beta = (0.05, -0.03, 0.02)
+    o = oracle_mod.Oracle(vset, shape, 0.8, 1 / shape[0], shift=beta, shift_field=field)
+    lat = L.Lattice(vset, shape, 0.8, 1 / shape[0], streaming=streaming)
+    lat.set_shift(beta)
+    lat.set_shift_field(field)
+    lat.set_distributions(f0)
+    f = f0
+    for n in range(3):
+        lat.step(1)
+        f = o.step(f)
+        assert dist_err(lat.distributions(), f, 1e-2).max() < TOL64, n
+        assert field_err(lat.moments(), o.moments(f), 1e-2).max() < TOL64, n
+
+
+@pytest.mark.parametrize("A", [0.0, 0.05])
+def test_sheared_gauge_wave_init_and_run_fp64(L, oracle_mod, A):
+    """Flat space and the gauge wave carried by the shear shift's flow, from
+    their closed form, D2Q9 64^2, tau 1: init at 1e-12, then 32 steps against
+    the oracle (1e-12 or the one-ulp spread)."""
+    N, v0 = 64, 0.1
+    shape = (N, N, 1)
+    field = W.shear_shift(shape, 1 / N, v0)
+    fields = W.sheared_gauge_wave(shape, 1 / N, A, v0)
+    lat = L.Lattice(2, shape, 1.0, 1 / N)
+    lat.set_shift_field(field)
+    lat.init(fields)
+    o = oracle_mod.Oracle(2, shape, 1.0, 1 / N, shift_field=field)
+    f = o.init(fields)
+    assert dist_err(lat.distributions(), f, 0.1).max() < TOL64
+    fp = perturbed(f)
+    lat.step(32)
+    f, fp = o.run(f, 32), o.run(fp, 32)
+    spread = field_err(o.moments(fp), o.moments(f), 0.1).max()
+    assert field_err(lat.moments(), o.moments(f), 0.1).max() <= bar(spread)
+    # and the GPU run is as close to the closed form as the oracle
+    ex = W.sheared_gauge_wave(shape, 1 / N, A, v0, t=0.5).reshape(16, -1)
+    e_gpu = np.abs(lat.moments() - ex).max()
+    e_orc = np.abs(o.moments(f) - ex).max()
+    assert abs(e_gpu - e_orc) <= 1e-9 + 1e-6 * e_orc
+
+
+def test_uniform_shift_field_matches_the_constant_shift(L):
+    """A uniform field has B = 0: the field form and the constant-shift form
+    agree to round-off (they take V's flux by different routes)."""
+    shape = (24, 20, 1)
+    fields = W.add_noise(W.gauge_wave(shape, 1 / 24, 0.05), 1e-4, seed=2)
+    beta = (0.2, -0.1, 0.0)
+    uni = np.broadcast_to(np.array(beta).reshape(3, 1, 1, 1), (3, 1, 20, 24)).copy()
+    a = L.Lattice(2, shape, 1.5, 1 / 24)
+    a.set_shift(beta)
+    b = L.Lattice(2, shape, 1.5, 1 / 24)
+    b.set_shift_field(uni)
+    a.init(fields)
+    b.init(fields)
+    a.step(6)
+    b.step(6)
+    assert dist_err(b.distributions(), a.distributions(), 0.1).max() < 1e-13
+
+
+def test_removing_the_field_restores_the_previous_form(L):
+    """set_shift_field(None) gives back the zero-shift forms, bit for bit."""
+    shape = (32, 16, 8)
+    fields = W.add_noise(W.gauge_wave(shape, 1 / 32, 0.05), 1e-4, seed=6)
+    ref = L.Lattice(3, shape, 1.5, 1 / 32, storage="f32", streaming=1)
+    ref.init(fields)
+    ref.step(5)
+    a = L.Lattice(3, shape, 1.5, 1 / 32, storage="f32", streaming=1)
+    a.set_shift_field(W.smooth_shift(shape, 1 / 32, 0.1, seed=1))
+    a.set_shift_field(None)
+    a.init(fields)
+    a.step(5)
+    assert np.array_equal(ref.distributions(), a.distributions())
+
+
+def test_constraints_with_shift_field_fp64(L, oracle_mod):
+    """The monitor's corrected moments carry the field's B terms: the 22
+    values against the oracle at t = 0 and after 10 steps."""
+    N = 16
+    shape = (N, N, N)
+    field = W.smooth_shift(shape, 1 / N, 0.1, seed=12)
+    fields = W.add_noise(W.gauge_wave(shape, 1 / N, 0.1, direction="xyz"), 1e-4, seed=8)
+    lat = L.Lattice(3, shape, 1.5, 1 / N)
+    lat.set_shift_field(field)
+    lat.init(fields)
+    o = oracle_mod.Oracle(3, shape, 1.5, 1 / N, shift_field=field)
+    f = o.init(fields)
+    for n in (0, 10):
+        if n:
+            lat.step(n)
+            f = o.run(f, n)
+        g, r = lat.constraints(), o.constraints(f)
+        np.testing.assert_allclose(g[:6], r[:6], rtol=1e-10, atol=0)
+        np.testing.assert_allclose(g[6:], r[6:], rtol=1e-12, atol=1e-12)
+
+
+def test_full_size_sampled_step_with_shift_field_fp64(L, oracle_mod):
+    """128^3 D3Q19 FP64 with a constant shift plus a smooth field, one step
+    from a noisy diagonal wave, sampled cells against the oracle's per-cell
+    step."""
+    N = 128
+    shape = (N, N, N)
+    field = W.smooth_shift(shape, 1 / N, 0.1, seed=21)
+    fields = W.add_noise(W.gauge_wave(shape, 1 / N, 0.05, direction="xyz"), 1e-6, seed=5)
+    beta = (0.05, 0.02, -0.04)
+    o = oracle_mod.Oracle(3, shape, 0.9, 1 / N, shift=beta, shift_field=field)
+    f0 = o.init(fields)
+    lat = L.Lattice(3, shape, 0.9, 1 / N)
+    lat.set_shift(beta)
+    lat.set_shift_field(field)
+    lat.set_distributions(f0)
+    lat.step(1)
+    rng = np.random.default_rng(27)
+    corners = [x + N * (y + N * z) for x in (0, N - 1) for y in (0, N - 1) for z in (0, N - 1)]
+    idx = np.array(corners + list(rng.integers(0, N ** 3, size=120)), dtype=np.int64)
+    got = lat.cells_distributions(idx)
+    ref = o.step_cells(f0, idx)
+    scale = np.abs(ref).max(axis=(0, 2))
+    assert (np.abs(got - ref).max(axis=(0, 2)) / scale).max() < TOL64
+
+
+@pytest.mark.parametrize("storage", ["dev_f32", "f32", "dev_bf16"])
+def test_reduced_precision_shift_field_within_stated_bound(L, oracle_mod, storage):
+    """Sheared gauge wave (A = 0.01), D2Q9 128^2, tau 1.5: each storage
+    against the FP64 oracle after 1 and 10 steps, within the stated bound
+    (3D constants, amplification of the D1Q3 step at shift 0.1)."""
+    N, tau, A, v0 = 128, 1.5, 0.01, 0.1
+    shape = (N, N, 1)
+    field = W.shear_shift(shape, 1 / N, v0)
+    fields = W.sheared_gauge_wave(shape, 1 / N, A, v0)
+    lam = amplification(oracle_mod, tau, (v0, 0.0, 0.0))
+    o = oracle_mod.Oracle(2, shape, tau, 1 / N, shift_field=field)
+    f = o.init(fields)
+    lat = L.Lattice(2, shape, tau, 1 / N, storage=storage)
+    lat.set_shift_field(field)
+    lat.init(fields)
+    done = 0
+    for n in (1, 10):
+        lat.step(n - done)
+        f = o.run(f, n - done)
+        done = n
+        lat.status()
+        err = float(np.abs(lat.moments() - o.moments(f)).max() / A)
+        assert err <= bound(storage, True, N, tau, n, lam), (n, err)
