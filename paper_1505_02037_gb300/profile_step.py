@@ -10,7 +10,8 @@ capture ncu reports of a single kernel on a small case. With --batch R the
 batched ensemble kernel advances R copies of the wave (tau 2.0) by --steps
 steps in each of four launches. With --shift the lattice carries that
 constant shift and runs the shift-carrying launch form (--variant is ignored);
---shift-field AMP adds a seeded smooth static shift field (its own form).
+--shift-field AMP adds the static shear shift field of that amplitude (its
+own form).
 """
 from __future__ import annotations
 
@@ -35,7 +36,7 @@ def main(argv=None):
     p.add_argument("--per-sm", type=int, default=1)
     p.add_argument("--shift", default=None, help="bx,by,bz")
     p.add_argument("--shift-field", type=float, default=0.0,
-                   help="amplitude of a seeded smooth static shift field")
+                   help="amplitude of a static shear shift field")
     a = p.parse_args(argv)
     if a.batch:
         return batch_main(a)
@@ -50,7 +51,7 @@ def main(argv=None):
     if beta:
         lat.set_shift(beta)
     if a.shift_field:
-        lat.set_shift_field(W.smooth_shift(shape, 1 / n, a.shift_field, 1505))
+        lat.set_shift_field(W.shear_shift3(shape, 1 / n, a.shift_field))
     lat.init(W.gauge_wave(shape, 1 / n, 0.1, beta=beta))
     lat.step(a.steps)
     lat.status()

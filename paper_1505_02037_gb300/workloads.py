@@ -100,6 +100,22 @@ def shear_shift(shape, dx, v0):
     return out
 
 
+def shear_shift3(shape, dx, v0):
+    """Divergence-free static shift field on a 3D lattice: beta^x =
+    v0 sin(2 pi y/L_y), beta^y = v0 sin(2 pi z/L_z), beta^z = v0 sin(2 pi x/L_x).
+    Each component varies across its own direction only, so the coordinates
+    it carries shear (the Jacobian grows linearly in time) rather than
+    converge on the field's sinks (where a compressive field makes the metric
+    grow exponentially). [3][nz][ny][nx]."""
+    nx, ny, nz = shape
+    X, Y, Z = coords(shape, dx)
+    out = np.zeros((3, nz, ny, nx))
+    out[0] = v0 * np.sin(2 * math.pi * Y / (ny * dx))
+    out[1] = v0 * np.sin(2 * math.pi * Z / (nz * dx))
+    out[2] = v0 * np.sin(2 * math.pi * X / (nx * dx))
+    return out
+
+
 def smooth_shift(shape, dx, amp, seed, modes=1):
     """A seeded smooth periodic shift field [3][nz][ny][nx]: per component a
     few Fourier modes of amplitude amp along the lattice's axes of extent
