@@ -34,7 +34,8 @@
  *       lambda inside them) use the corrected rho with the same derivatives.
  *   R6  Initial distributions: f = f_eq(rho0) - (dt/2) w_l S(rho0), so that the
  *       first step's corrected moments reproduce rho0 to O(dt^2).
- *   R7  Vacuum and zero shift: G_ab = 0, beta = B = s = 0, R4_ij = 0.
+ *   R7  Vacuum and zero shift unless a fluid (R13) or a shift (R14 constant,
+ *       R15 static field) is set: G_ab = 0, beta = B = s = 0, R4_ij = 0.
  *   R8  Index placement of the contracted D terms: every raised index uses the
  *       inverse three-metric; D_kr^r = g^{rm} D_krm, D^r_rk = g^{rm} D_mrk,
  *       D_k^{rs} = g^{ra} g^{sb} D_kab, D^k_ij = g^{km} D_mij.
@@ -47,6 +48,13 @@
  *       of any constraint; with the reading it differs by exactly
  *       -(alpha/4) gamma_ij times the Hamiltonian constraint, which is how
  *       the paper describes the Einstein evolution system.
+ *   R16 Independently evolved A_k and D_kij (the original formulation the
+ *       paper mentions and sets aside): with zero shift their equations
+ *       follow from the definitions and the lapse and metric equations,
+ *       d_t A_k + d_k(alpha Q) = 0 and d_t D_kij + d_k(alpha K_ij) = 0, with
+ *       equilibria w_l [A_k + c_lk alpha Q / c_s^2] and
+ *       w_l [D_kij + c_lk alpha K_ij / c_s^2] and no sources. The other 16
+ *       fields then take A and D from these moments instead of a stencil.
  */
 #include <math.h>
 #include <stdint.h>
@@ -181,6 +189,7 @@ typedef struct {
   double lam[3][3][3]; /* lambda^k_ij, index [k][i][j] */
   double S_ij[3][3];   /* S_ij itself (without the factor alpha) */
   double VB[3][3];     /* B part of the flux of V_k along r: B^r_k - B_k^r, [k][r] */
+  double Qg;           /* the slicing's gauge function Q */
 } bm_rhs;
 
 static double inverse3(const double g[3][3], double gi[3][3]) {
@@ -420,6 +429,7 @@ static void bm_point(const bm_state* s, int slicing, double rho, double P, bm_rh
   else if (slicing == 2) Qg = trK / a;
   double bA = 0;
   for (int rr = 0; rr < 3; ++rr) bA += s->beta[rr] * s->A[rr];
+  r->Qg = Qg;
   r->S_alpha = a * bA - a * a * Qg;
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
@@ -976,5 +986,182 @@ int orc_constraints(const orc_params* p, const double* f, double* out) {
   }
   free(rho);
   free(cf);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Independently evolved A_k and D_kij (reading R16; Sec. "Bona-Masso        */
+/* evolution equations", the remark after the first-order derivatives)       */
+/* ------------------------------------------------------------------------ */
+/* Fields 0..15 as above, then A_x A_y A_z (16..18) and D_kij at
+ * 19 + 6 k + pair(i, j) (k = x, y, z; pairs in the order xx xy xz yy yz zz). */
+#define ORC_NF_AD 37
+enum { F_A = 16, F_D = 19 };
+
+static int check_params_ad(const orc_params* p, vset_t* vs) {
+  if (check_params(p, vs)) return -1;
+  if (p->beta[0] != 0 || p->beta[1] != 0 || p->beta[2] != 0 || p->beta_field) return -1;
+  return 0;
+}
+
+/* The 37 moments as a bm_state: A and D are the cell's own values. */
+static void ad_unpack(const double v[ORC_NF_AD], bm_state* s) {
+  unpack_fields(v, s);
+  memset(s->beta, 0, sizeof(s->beta));
+  memset(s->B, 0, sizeof(s->B));
+  for (int k = 0; k < 3; ++k) {
+    s->A[k] = v[F_A + k];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) s->D[k][i][j] = v[F_D + 6 * k + pair_of(i, j)];
+  }
+}
+
+/* Sources of the 37 fields at state v (zero for A and D) and, at the same
+ * state, the fluxes: those of the 16 fields, alpha Q along k for A_k and
+ * alpha K_ij along k for D_kij. */
+static void ad_rhs(const orc_params* p, const double v[ORC_NF_AD], double S[ORC_NF_AD],
+                   double Fl[ORC_NF_AD][3]) {
+  double mrho, mP;
+  matter_now(p, &mrho, &mP);
+  bm_state s;
+  bm_rhs r;
+  ad_unpack(v, &s);
+  bm_point(&s, p->slicing, mrho, mP, &r);
+  if (S) {
+    pack_sources(&r, S);
+    for (int F = ORC_NF; F < ORC_NF_AD; ++F) S[F] = 0;
+    if (!p->sources_on)
+      for (int F = 0; F < ORC_NF_AD; ++F) S[F] = 0;
+  }
+  if (Fl) {
+    double F16[ORC_NF][3];
+    pack_fluxes(&r, &s, F16);
+    for (int F = 0; F < ORC_NF; ++F)
+      for (int m = 0; m < 3; ++m) Fl[F][m] = F16[F][m];
+    for (int k = 0; k < 3; ++k)
+      for (int m = 0; m < 3; ++m) {
+        Fl[F_A + k][m] = (m == k) ? s.alpha * r.Qg : 0;
+        for (int q = 0; q < 6; ++q)
+          Fl[F_D + 6 * k + q][m] = (m == k) ? s.alpha * s.K[PAIR_I[q]][PAIR_J[q]] : 0;
+      }
+  }
+}
+
+static void ad_moments_all(const vset_t* vs, int64_t cells, const double* f, double* mom) {
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < cells; ++c)
+    for (int F = 0; F < ORC_NF_AD; ++F) mom[F * cells + c] = moment0(vs, cells, f, F, c);
+}
+
+/* Initial distributions from 37 given fields ([37][cells]), reading R6. */
+int orc_ad_init37(const orc_params* p, const double* fields, double* f_out) {
+  vset_t vs;
+  if (check_params_ad(p, &vs)) return -1;
+  const int64_t cells = p->nx * p->ny * p->nz;
+  int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+  for (int64_t c = 0; c < cells; ++c) {
+    double v[ORC_NF_AD], S[ORC_NF_AD], Fl[ORC_NF_AD][3];
+    for (int F = 0; F < ORC_NF_AD; ++F) v[F] = fields[F * cells + c];
+    ad_rhs(p, v, S, Fl);
+    for (int F = 0; F < ORC_NF_AD; ++F)
+      for (int l = 0; l < vs.Q; ++l) {
+        double val = feq(&vs, l, v[F], Fl[F]) - 0.5 * p->dt * vs.w[l] * S[F];
+        f_out[((int64_t)F * vs.Q + l) * cells + c] = val;
+        if (!isfinite(val)) bad = 1;
+      }
+  }
+  return bad ? -4 : 0;
+}
+
+/* Initial distributions from the 16 fields ([16][cells]): A and D start as
+ * the central differences of reading R4. */
+int orc_ad_init(const orc_params* p, const double* fields, double* f_out) {
+  vset_t vs;
+  if (check_params_ad(p, &vs)) return -1;
+  const int64_t cells = p->nx * p->ny * p->nz;
+  double* all = (double*)malloc(sizeof(double) * ORC_NF_AD * cells);
+  if (!all) return -2;
+  memcpy(all, fields, sizeof(double) * ORC_NF * cells);
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < cells; ++c) {
+    int64_t x, y, z;
+    cell_coords(p, c, &x, &y, &z);
+    double A[3], D[3][3][3];
+    derivatives(p, fields, cells, x, y, z, A, D);
+    for (int k = 0; k < 3; ++k) {
+      all[(F_A + k) * cells + c] = A[k];
+      for (int q = 0; q < 6; ++q) all[(F_D + 6 * k + q) * cells + c] = D[k][PAIR_I[q]][PAIR_J[q]];
+    }
+  }
+  int rc = orc_ad_init37(p, all, f_out);
+  free(all);
+  return rc;
+}
+
+/* One step of the 37-field scheme: every quantity is local to the cell. */
+int orc_ad_step(const orc_params* p, const double* f_in, double* f_out) {
+  vset_t vs;
+  if (check_params_ad(p, &vs)) return -1;
+  const int64_t cells = p->nx * p->ny * p->nz;
+  double* mom = (double*)malloc(sizeof(double) * ORC_NF_AD * cells);
+  if (!mom) return -2;
+  ad_moments_all(&vs, cells, f_in, mom);
+  const double src_fac = 1.0 - 1.0 / (2.0 * p->tau);
+  int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+  for (int64_t c = 0; c < cells; ++c) {
+    double rt[ORC_NF_AD], S[ORC_NF_AD], rho[ORC_NF_AD], Fl[ORC_NF_AD][3];
+    for (int F = 0; F < ORC_NF_AD; ++F) rt[F] = mom[F * cells + c];
+    ad_rhs(p, rt, S, NULL);
+    for (int F = 0; F < ORC_NF_AD; ++F) rho[F] = rt[F] + 0.5 * p->dt * S[F];
+    ad_rhs(p, rho, NULL, Fl);
+    int64_t x, y, z;
+    cell_coords(p, c, &x, &y, &z);
+    for (int l = 0; l < vs.Q; ++l) {
+      int64_t d = cell_index(p, x + vs.c[l][0], y + vs.c[l][1], z + vs.c[l][2]);
+      for (int F = 0; F < ORC_NF_AD; ++F) {
+        double fl = f_in[((int64_t)F * vs.Q + l) * cells + c];
+        double fe = feq(&vs, l, rho[F], Fl[F]);
+        double v = fl - (fl - fe) / p->tau + p->dt * vs.w[l] * src_fac * S[F];
+        f_out[((int64_t)F * vs.Q + l) * cells + d] = v;
+        if (!isfinite(v)) bad = 1;
+      }
+    }
+  }
+  free(mom);
+  return bad ? -4 : 0;
+}
+
+int orc_ad_run(const orc_params* p, double* f_io, double* scratch, int64_t n) {
+  orc_params q = *p;
+  vset_t vs;
+  if (check_params_ad(p, &vs)) return -1;
+  for (int64_t i = 0; i < n; ++i) {
+    int rc = orc_ad_step(&q, f_io, scratch);
+    q.t += q.dt;
+    if (rc) return rc;
+    memcpy(f_io, scratch, sizeof(double) * ORC_NF_AD * vs.Q * p->nx * p->ny * p->nz);
+  }
+  return 0;
+}
+
+/* Corrected moments of the 37 fields ([37][cells]); A and D have no source,
+ * so theirs are the plain sums. */
+int orc_ad_moments(const orc_params* p, const double* f, double* out) {
+  vset_t vs;
+  if (check_params_ad(p, &vs)) return -1;
+  const int64_t cells = p->nx * p->ny * p->nz;
+  double* mom = (double*)malloc(sizeof(double) * ORC_NF_AD * cells);
+  if (!mom) return -2;
+  ad_moments_all(&vs, cells, f, mom);
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < cells; ++c) {
+    double rt[ORC_NF_AD], S[ORC_NF_AD];
+    for (int F = 0; F < ORC_NF_AD; ++F) rt[F] = mom[F * cells + c];
+    ad_rhs(p, rt, S, NULL);
+    for (int F = 0; F < ORC_NF_AD; ++F) out[F * cells + c] = rt[F] + 0.5 * p->dt * S[F];
+  }
+  free(mom);
   return 0;
 }

@@ -28,6 +28,7 @@ _lock = threading.Lock()
 _lib = None
 
 NF = 16
+NF_AD = 37  # with independently evolved A_k (3) and D_kij (18)
 Q_OF = {1: 3, 2: 9, 3: 19}
 VSET_NAMES = {"D1Q3": 1, "D2Q9": 2, "D3Q19": 3}
 
@@ -86,6 +87,11 @@ def lib():
                 getattr(L, name).argtypes = [pp, dp, dp]
                 getattr(L, name).restype = ctypes.c_int
             L.orc_run.argtypes = [pp, dp, dp, ctypes.c_int64]
+            for name in ("orc_ad_init", "orc_ad_init37", "orc_ad_step", "orc_ad_moments"):
+                getattr(L, name).argtypes = [pp, dp, dp]
+                getattr(L, name).restype = ctypes.c_int
+            L.orc_ad_run.argtypes = [pp, dp, dp, ctypes.c_int64]
+            L.orc_ad_run.restype = ctypes.c_int
             L.orc_run.restype = ctypes.c_int
             L.orc_step_cells.argtypes = [pp, dp, ctypes.c_int64,
                                          ctypes.POINTER(ctypes.c_int64), dp]
@@ -234,4 +240,36 @@ class Oracle:
         f = np.ascontiguousarray(f, dtype=np.float64)
         out = np.zeros(22)
         _check(lib().orc_constraints(ctypes.byref(self.p), _dp(f), _dp(out)), "constraints")
+        return out
+
+    # --- independently evolved A_k and D_kij (37 distribution sets) ---------
+    def ad_init(self, fields: np.ndarray, t=None) -> np.ndarray:
+        """fields: [16][cells] (A, D start as central differences) or
+        [37][cells] (A, D given)."""
+        self._at(t)
+        fields = np.ascontiguousarray(fields, dtype=np.float64).reshape(-1, self.cells)
+        f = np.zeros((NF_AD, self.Q, self.cells))
+        fn = {NF: "orc_ad_init", NF_AD: "orc_ad_init37"}[fields.shape[0]]
+        _check(getattr(lib(), fn)(ctypes.byref(self.p), _dp(fields), _dp(f)), "ad_init")
+        return f
+
+    def ad_step(self, f: np.ndarray, t=None) -> np.ndarray:
+        self._at(t)
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        out = np.zeros((NF_AD, self.Q, self.cells))
+        _check(lib().orc_ad_step(ctypes.byref(self.p), _dp(f), _dp(out)), "ad_step")
+        return out
+
+    def ad_run(self, f: np.ndarray, n: int, t=None) -> np.ndarray:
+        self._at(t)
+        f = np.array(f, dtype=np.float64, order="C", copy=True)
+        scratch = np.zeros_like(f)
+        _check(lib().orc_ad_run(ctypes.byref(self.p), _dp(f), _dp(scratch), int(n)), "ad_run")
+        return f
+
+    def ad_moments(self, f: np.ndarray, t=None) -> np.ndarray:
+        self._at(t)
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        out = np.zeros((NF_AD, self.cells))
+        _check(lib().orc_ad_moments(ctypes.byref(self.p), _dp(f), _dp(out)), "ad_moments")
         return out

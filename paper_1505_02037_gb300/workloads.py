@@ -176,6 +176,24 @@ def sheared_gauge_wave(shape, dx, A, v0, t=0.0):
     return _pack(np.sqrt(H), g, K, [V[0], V[1], V[2]], shape)
 
 
+def gauge_wave_derivatives(shape, dx, A, t=0.0, direction="x"):
+    """Exact A_k = d_k ln alpha and D_kij = d_k gamma_ij / 2 of the gauge wave,
+    [21][nz][ny][nx]: A_x A_y A_z, then D_kij at 3 + 6 k + pair (pairs xx xy
+    xz yy yz zz). With H' = dH/du = -(2 pi A/d) cos(phase): A_k = H' n_k / (2H),
+    D_kij = H' n_k n_i n_j / 2."""
+    n, d = _direction(direction, shape, dx)
+    u = _shifted_u(n, shape, dx, t, None)
+    ph = 2 * math.pi * (u - t) / d
+    H = 1 - A * np.sin(ph)
+    Hu = -(2 * math.pi * A / d) * np.cos(ph)
+    out = np.zeros((21,) + H.shape)
+    for k in range(3):
+        out[k] = 0.5 * Hu * n[k] / H
+        for p, (i, j) in enumerate(PAIRS):
+            out[3 + 6 * k + p] = 0.5 * Hu * n[k] * n[i] * n[j]
+    return out
+
+
 def _polarisation(direction):
     if direction == "x":
         return np.array([0.0, 1.0, 0.0]), np.array([0.0, 0.0, 1.0])
