@@ -104,7 +104,7 @@ def parse():
                    help="default 10 (3 for the batched workload)")
     p.add_argument("--impl", default="lbnr", choices=["lbnr", "reference"])
     p.add_argument("--workload", default="gauge3d-256-f32",
-                   choices=sorted(WORKLOADS) + ["batched"])
+                   choices=sorted(WORKLOADS) + ["batched", "gauge3d-256-f32-ad"])
     p.add_argument("--tau", type=float, default=4.5)
     p.add_argument("--profile-steps", type=int, default=20)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -385,6 +385,167 @@ def run_reference_batched(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# The 37-field scheme (independently evolved A_k and D_kij)
+# ---------------------------------------------------------------------------
+AD_N, AD_A, AD_NF = 256, 0.1, 37
+
+
+def ad_config(args):
+    return {"workload": f"3D gauge wave along x, D3Q19 {AD_N}^3 periodic, the 37-field scheme "
+                        f"(A_k and D_kij evolved), f32 storage, A={AD_A}, tau={args.tau}, "
+                        "ping-pong streaming",
+            "workload_key": args.workload, "cells": AD_N ** 3, "fields": AD_NF, "velocities": 19,
+            "unit_note": "a lattice update is one of the 37 variables of one cell"}
+
+
+def ad_oracle_rate(args, n, steps=None, seconds=12.0):
+    from oracle import oracle as O
+    o = O.Oracle(3, (n, n, n), args.tau, 1 / n)
+    f = o.ad_init(W.gauge_wave((n, n, n), 1 / n, AD_A))
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    done, t0 = 0, time.perf_counter()
+    while True:
+        f = o.ad_step(f)
+        done += 1
+        el = time.perf_counter() - t0
+        if (steps is not None and done >= steps) or (steps is None and (el > seconds or done >= 200)):
+            break
+    return n ** 3 * AD_NF * done / el / 1e6, done, el, cores
+
+
+def run_reference_ad(args):
+    """Reference arm for the 37-field workload: the FP64 oracle on a 24^3
+    piece, one oracle step per step."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    n = 24
+    ad_oracle_rate(args, n, steps=args.warmup)
+    value, done, el, cores = ad_oracle_rate(args, n, steps=args.steps)
+    sample = (f"each step: one FP64 oracle step of the 37-field scheme on a {n}^3 periodic piece "
+              f"of the workload on {cores} host threads")
+    line = {"impl": "reference", "metric": "lattice updates/s", "value": value,
+            "unit": "Mcell*var/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el / done * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": ad_config(args),
+            "cpu_baseline": {"value": value, "unit": "Mcell*var/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "Mcell*var/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main_ad(args):
+    """The 37-field scheme on 256^3 D3Q19, FP32 storage: one fused kernel per
+    step (no stencil pass), timed like the main workload."""
+    import torch
+    import torch.distributed as dist
+    from paper_1505_02037_gb300 import lbnr
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    N = AD_N
+    shape, cells = (N, N, N), N ** 3
+    fields = W.gauge_wave(shape, 1 / N, AD_A).reshape(16, cells)
+    stream = torch.cuda.Stream(device=dev)
+    lat = lbnr.ADLattice(3, shape, args.tau, 1 / N, storage="f32", stream=stream)
+    lat.init(fields)
+    # the launch form: each timed over a few steps, the fastest kept
+    tuning = {}
+    for form, name in enumerate(lat.forms):
+        lat.set_form(form)
+        lat.step(1)
+        tuning[name] = lat.step_timed(4) / 4
+    best = min(tuning, key=tuning.get)
+    lat.set_form(lat.forms.index(best))
+    lat.init(fields)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    lat.step(args.warmup)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        e0.record(stream)
+        lat.step(args.steps)
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    ms_max, units_all = over_ranks(ms, cells * AD_NF * args.steps, world, dev)
+    finite = True
+    try:
+        lat.status()
+    except lbnr.NonFiniteError:
+        finite = False
+    # the kernel alone: events around each launch on the lattice's stream
+    kms = lat.step_timed(args.profile_steps) / args.profile_steps
+    alg = cells * 2 * AD_NF * 19 * 4  # every distribution read once and written once
+    peaks, peak_kind = measured_peaks()
+    peak = float(peaks["hbm_gbs"])
+    achieved = alg / (kms * 1e-3) / 1e9
+    tkey = f"k_ad_collide:gauge3d-256-f32-ad:{best}"
+    line = {
+        "metric": "lattice updates/s", "value": units_all / (ms_max * 1e-3) / 1e6,
+        "unit": "Mcell*var/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(ad_config(args),
+                       l2=f"inputs larger than L2 ({2 * AD_NF * 19 * 4 * cells / 1e9:.1f} GB of "
+                          "distributions)",
+                       state_finite_after_run=finite,
+                       parallelism="replicas" if world > 1 else "single GPU"),
+        "roofline": {"bound": "hbm", "kernel": "k_ad_collide (37-field collide-and-stream)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": f"hbm_gbs of {peak_kind}",
+                     "algorithmic_bytes_per_cell": alg / cells, "avg_launch_ms": kms,
+                     "traffic": traffic_for(tkey, cells)},
+        "gpu_launches": args.steps, "launch_form": f"37-field, {best}",
+        "autotune_ms_per_collide": tuning,
+        "clocks": clk.summary(),
+    }
+    if not args.no_e2e:
+        hf = torch.from_numpy(fields.copy()).pin_memory()
+        hout = np.empty((AD_NF, cells))
+        k = args.steps
+        barrier()
+        t0 = time.perf_counter()
+        lat.init(hf.numpy())
+        lat.step(k)
+        try:
+            hout = lat.moments()
+        except lbnr.NonFiniteError:
+            pass
+        barrier()
+        el = time.perf_counter() - t0
+        el, u = over_ranks(el, cells * AD_NF * k, world, dev)
+        line["e2e"] = {"value": u / el / 1e6, "unit": "Mcell*var/s",
+                       "h2d_bytes_per_step": hf.numel() * 8 / k,
+                       "d2h_bytes_per_step": hout.size * 8 / k, "steps_per_transfer": k}
+    lat.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        value, done, el, cores = ad_oracle_rate(args, 48)
+        line["cpu_baseline"] = {"value": value, "unit": "Mcell*var/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"FP64 oracle, 37-field scheme, D3Q19 48^3 periodic gauge "
+                                          f"wave (A={AD_A}, tau={args.tau}), {done} steps in "
+                                          f"{el:.1f} s on {cores} host threads"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main_batched(args):
     import torch
     import torch.distributed as dist
@@ -511,6 +672,8 @@ def main():
     args = parse()
     if args.workload == "batched":
         return run_reference_batched(args) if args.impl == "reference" else main_batched(args)
+    if args.workload == "gauge3d-256-f32-ad":
+        return run_reference_ad(args) if args.impl == "reference" else main_ad(args)
     if args.impl == "reference":
         return run_reference(args)
     import torch

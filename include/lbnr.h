@@ -322,6 +322,70 @@ void lbnr_destroy(lbnr_ctx* ctx);
 /* Last error message of ctx, or of the calling thread when ctx is NULL. */
 const char* lbnr_last_error(const lbnr_ctx* ctx);
 
+/* ------------------------------------------------------------------------
+ * Independently evolved A_k and D_kij: the 37-field scheme
+ * ------------------------------------------------------------------------
+ * The original Bona-Masso formulation evolves A_k = d_k ln alpha and
+ * D_kij = d_k gamma_ij / 2 as variables of their own; the paper mentions it
+ * and reports that they then drift from the derivatives of alpha and gamma
+ * (Sec. "Bona-Masso evolution equations", after the first-order derivatives).
+ * This comparison variant evolves them, with zero shift, by
+ *   d_t A_k + d_k(alpha Q) = 0,  d_t D_kij + d_k(alpha K_ij) = 0
+ * (flux-only sets, equilibria w [A_k + c_k alpha Q / c_s^2] and
+ * w [D_kij + c_k alpha K_ij / c_s^2], no sources), and the other 16 fields
+ * take A and D from these moments: the step reads no neighbour's moments.
+ * Fields: the 16 of lbnr_init, then A_x A_y A_z (16..18), then D_kij at
+ * 19 + 6 k + pair(i, j) (pairs xx xy xz yy yz zz). Distributions
+ * [37][Q][pstride] (pstride = cells rounded up to 32), ping-pong, FP64 or
+ * FP32 storage (arithmetic in the storage type). The context owns its device
+ * memory: 2 x 37 x Q x pstride values, plus 37 FP64 values per cell. */
+typedef struct lbnr_ad_ctx lbnr_ad_ctx;
+
+/* vset LBNR_D1Q3/D2Q9/D3Q19; tau the dimensionless tau/dt (> 1/2); dt must
+ * equal dx; slicing LBNR_GEODESIC/HARMONIC/ONE_PLUS_LOG; storage LBNR_F64 or
+ * LBNR_F32; cuda_stream a cudaStream_t or NULL (the context makes one).
+ * Errors: LBNR_EINVAL, LBNR_ENOMEM (device memory), LBNR_ECUDA. */
+int lbnr_ad_create(const lbnr_grid* grid, int vset, double tau, double dx, double dt,
+                   int slicing, int storage, void* cuda_stream, lbnr_ad_ctx** out);
+
+/* Host fields[nfields][cells], nfields 16 (A and D start as second-order
+ * central differences of ln alpha and gamma / 2) or 37 (given). Initial
+ * distributions f = f_eq - (dt/2) w S, as lbnr_init. Errors: LBNR_EINVAL
+ * (NULL, nfields, alpha <= 0), LBNR_ECUDA. */
+int lbnr_ad_init(lbnr_ad_ctx* ctx, const double* fields, int nfields);
+
+/* n steps, enqueued on the context's stream (asynchronous). */
+int lbnr_ad_step(lbnr_ad_ctx* ctx, int64_t n);
+
+/* n steps timed with CUDA events on the context's stream; *ms_out the total. */
+int lbnr_ad_step_timed(lbnr_ad_ctx* ctx, int64_t n, double* ms_out);
+
+/* Corrected moments of the 37 fields into host out[37][cells] (FP64):
+ * rho = sum f + dt S / 2 for the 16, the plain sums for A and D. Returns
+ * LBNR_ENONFINITE (after the copy) if a step saw a non-finite moment. */
+int lbnr_ad_moments(lbnr_ad_ctx* ctx, double* out);
+
+/* LBNR_ENONFINITE if any step so far saw a non-finite moment, else LBNR_OK. */
+int lbnr_ad_status(lbnr_ad_ctx* ctx);
+
+/* Distributions to / from host [37][Q][cells] (FP64). */
+int lbnr_ad_get_distributions(lbnr_ad_ctx* ctx, double* out);
+int lbnr_ad_set_distributions(lbnr_ad_ctx* ctx, const double* in);
+
+int64_t lbnr_ad_steps_done(const lbnr_ad_ctx* ctx);
+
+/* Launch forms of the 37-field collide kernel: blocks of 128 threads with
+ * registers sized for lbnr_ad_form_blocks(form) blocks per SM (2 to 5: more
+ * warps in flight against more spilled values). All forms compute the same
+ * values. lbnr_ad_set_form returns LBNR_EINVAL for an unknown form; the
+ * default is 2 blocks per SM with FP64 storage and 3 with FP32. */
+int lbnr_ad_num_forms(void);
+int lbnr_ad_form_blocks(int form);
+int lbnr_ad_set_form(lbnr_ad_ctx* ctx, int form);
+void lbnr_ad_destroy(lbnr_ad_ctx* ctx);
+/* Last error message of ctx (or of the calling thread when ctx is NULL). */
+const char* lbnr_ad_last_error(const lbnr_ad_ctx* ctx);
+
 #ifdef __cplusplus
 }
 #endif

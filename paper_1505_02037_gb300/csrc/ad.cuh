@@ -1,0 +1,335 @@
+// Kernels and launchers of the 37-field scheme: the 16 Bona-Masso fields plus independently evolved
+// A_k and D_kij, the original formulation that the paper mentions and sets
+// aside (Sec. "Bona-Masso evolution equations", the remark after the
+// first-order derivatives). With zero shift their equations follow from the
+// definitions and the lapse and metric equations:
+//   d_t A_k + d_k(alpha Q) = 0,   d_t D_kij + d_k(alpha K_ij) = 0,
+// flux-only lattice Boltzmann sets with equilibria w [A_k + c_k alpha Q / c_s^2]
+// and w [D_kij + c_k alpha K_ij / c_s^2]. The other 16 fields read A and D
+// from these moments, so a cell's update needs no neighbour's moments: one
+// kernel per step, no stencil pass. Ping-pong streaming; FP64 or FP32
+// storage. C-ABI: lbnr_ad_* in include/lbnr.h.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "../../include/lbnr.h"
+#include "dispatch.h"
+#include "kernels.cuh"
+
+namespace lbnr {
+namespace ad {
+
+constexpr int kNFA = 37;  // 16 fields, A_k (3), D_kij (3 x 6)
+constexpr int kA = 16, kD = 19;
+
+// alpha Q of the slicing (Sec. "Gauge choices": Q = 0, tr K, tr K / alpha).
+template <class T>
+__device__ __forceinline__ T alpha_q(int slicing, T alpha, const T g[6], const T K[6]) {
+  if (slicing == 0) return T(0);
+  T gi[6];
+  invert_sym3(g, gi);
+  const T trK = gi[0] * K[0] + gi[3] * K[3] + gi[5] * K[5] +
+                T(2) * (gi[1] * K[1] + gi[2] * K[2] + gi[4] * K[4]);
+  return slicing == 1 ? alpha * trK : trK;
+}
+
+template <class S, class C>
+struct Args {
+  const S* fin;
+  S* fout;
+  int* flag;
+  Grid G;
+  C half_dt, omega, omc, sigma;
+  int slicing;
+};
+
+// One step: moments, sources (A and D from the cell's own moments), the
+// corrected moments, fluxes at them, relax, stream to x + c_l. MINB: thread
+// blocks of 128 per SM the registers are sized for (the launch forms trade
+// occupancy against spills).
+template <int Q, class S, class C, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_ad_collide(const Args<S, C> a) {
+  using L = Lattice<Q>;
+  constexpr int dim = L::kDim;
+  const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = cell < a.G.cells;
+  const int64_t c = valid ? cell : a.G.cells - 1;
+  const uint32_t ps = (uint32_t)a.G.pstride;
+  const Nbr n = make_nbr(a.G, c);
+
+  C rt[kNFA];
+#pragma unroll
+  for (int F = 0; F < kNFA; ++F) {
+    const S* fb = a.fin + (size_t)F * Q * ps + n.c;
+    C s = C(0);
+#pragma unroll
+    for (int l = 0; l < Q; ++l) s += (C)Codec<S>::load_keep(fb + (size_t)l * ps);
+    rt[F] = s;
+  }
+  {
+    C chk = C(0);
+#pragma unroll
+    for (int F = 0; F < kNFA; ++F) chk += rt[F];
+    if (valid && !isfinite(chk)) atomicOr(a.flag, 1);
+  }
+  C A[3], D[3][6];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    A[k] = rt[kA + k];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) D[k][q] = rt[kD + 6 * k + q];
+  }
+  C alpha, gm[6], K[6], V[3];
+  unpack<kABS, C>(rt, alpha, gm, K, V);
+  C Sr[kNF];
+  bm_sources<C>(alpha, gm, K, V, A, D, a.slicing, Sr);
+  C rho[kNF];
+#pragma unroll
+  for (int F = 0; F < kNF; ++F) rho[F] = rt[F] + a.half_dt * Sr[F];
+  C Fl[6][3], aQ, aK[6];
+  {
+    C alpha2, g2[6], K2[6], V2[3];
+    unpack<kABS, C>(rho, alpha2, g2, K2, V2);
+    bm_flux<C, dim>(alpha2, g2, V2, A, D, Fl);
+    aQ = alpha_q<C>(a.slicing, alpha2, g2, K2);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) aK[q] = alpha2 * K2[q];
+  }
+  C coef[kNF];
+#pragma unroll
+  for (int F = 0; F < kNF; ++F) coef[F] = a.omega * rho[F] + a.sigma * Sr[F];
+  const C three_omega = C(3) * a.omega;
+
+#pragma unroll
+  for (int F = 0; F < kNFA; ++F) {
+    const S* fb = a.fin + (size_t)F * Q * ps + n.c;
+    S* ob = a.fout + (size_t)F * Q * ps;
+    C v_[Q];
+#pragma unroll
+    for (int l = 0; l < Q; ++l) v_[l] = (C)Codec<S>::load(fb + (size_t)l * ps);
+    C cf;
+    C b[3] = {C(0), C(0), C(0)};
+    if (F < kNF) {
+      cf = coef[F];
+      if (has_flux(F)) {
+#pragma unroll
+        for (int k = 0; k < dim; ++k) b[k] = three_omega * Fl[F - kK][k];
+      }
+    } else {
+      // A and D have no source: coef = omega rho~, the sum of this field's
+      // own values, in the order of the moment pass.
+      C s = C(0);
+#pragma unroll
+      for (int l = 0; l < Q; ++l) s += v_[l];
+      cf = a.omega * s;
+      const int k = F < kD ? F - kA : (F - kD) / 6;
+      const C fk = F < kD ? aQ : aK[(F - kD) % 6];
+#pragma unroll
+      for (int kk = 0; kk < dim; ++kk)
+        if (kk == k) b[kk] = three_omega * fk;
+    }
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+      C t = cf;
+#pragma unroll
+      for (int k = 0; k < dim; ++k) {
+        if (L::c(l, k) > 0) t += b[k];
+        if (L::c(l, k) < 0) t -= b[k];
+      }
+      const C out = fma(a.omc, v_[l], C(L::w(l)) * t);
+      Codec<S>::store(ob + (size_t)l * ps + n.at(L::c(l, 0), L::c(l, 1), L::c(l, 2)), out);
+    }
+  }
+}
+
+// Initial distributions f = f_eq(v) - (dt/2) w S(v) from nf = 16 fields
+// (A, D as central differences of ln alpha and gamma / 2) or nf = 37.
+template <int Q, class S>
+__global__ void __launch_bounds__(128) k_ad_init(const double* __restrict__ fields, int nf, S* f,
+                                                  int* flag, Grid G, double inv2dx, double inv4dx,
+                                                  double half_dt, int slicing) {
+  using L = Lattice<Q>;
+  constexpr int dim = L::kDim;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= G.cells) return;
+  const int64_t cells = G.cells;
+  const Nbr n = make_nbr(G, c);
+  double v[kNFA];
+#pragma unroll
+  for (int F = 0; F < kNF; ++F) v[F] = fields[(int64_t)F * cells + c];
+  if (nf == kNFA) {
+#pragma unroll
+    for (int F = kNF; F < kNFA; ++F) v[F] = fields[(int64_t)F * cells + c];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if (k < dim) {
+        const int64_t cp = n.at(k == 0, k == 1, k == 2);
+        const int64_t cm = n.at(-(k == 0), -(k == 1), -(k == 2));
+        v[kA + k] = (log(fields[cp]) - log(fields[cm])) * inv2dx;
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+          v[kD + 6 * k + q] =
+              (fields[(int64_t)(1 + q) * cells + cp] - fields[(int64_t)(1 + q) * cells + cm]) * inv4dx;
+      } else {
+        v[kA + k] = 0;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) v[kD + 6 * k + q] = 0;
+      }
+    }
+  }
+  double A[3], D[3][6];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    A[k] = v[kA + k];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) D[k][q] = v[kD + 6 * k + q];
+  }
+  double alpha, gm[6], K[6], V[3];
+  unpack<kABS, double>(v, alpha, gm, K, V);
+  double Sr[kNF], Fl[6][3];
+  bm_sources<double>(alpha, gm, K, V, A, D, slicing, Sr);
+  bm_flux<double, dim>(alpha, gm, V, A, D, Fl);
+  const double aQ = alpha_q<double>(slicing, alpha, gm, K);
+  bool bad = false;
+#pragma unroll
+  for (int F = 0; F < kNFA; ++F) {
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+      double cf = 0;
+      if (has_flux(F)) {
+#pragma unroll
+        for (int k = 0; k < dim; ++k) cf += L::c(l, k) * Fl[F - kK][k];
+      } else if (F >= kA) {
+        const int k = F < kD ? F - kA : (F - kD) / 6;
+        const double fk = F < kD ? aQ : alpha * K[(F - kD) % 6];
+#pragma unroll
+        for (int kk = 0; kk < dim; ++kk)
+          if (kk == k) cf += L::c(l, kk) * fk;
+      }
+      const double s = F < kNF ? Sr[F] : 0.0;
+      const double val = L::w(l) * (v[F] + 3.0 * cf) - half_dt * L::w(l) * s;
+      bad |= !isfinite(val);
+      Codec<S>::store(f + (size_t)(F * Q + l) * G.pstride + c, (decltype(Codec<S>::load(f)))val);
+    }
+  }
+  if (bad) atomicOr(flag, 1);
+}
+
+// Corrected moments of the 37 fields in FP64 ([37][cells]): rho = rho~ +
+// dt S(rho~)/2 for the 16, the plain sums for A and D.
+template <int Q, class S>
+__global__ void __launch_bounds__(128) k_ad_moments(const S* __restrict__ f,
+                                                     double* __restrict__ out, Grid G,
+                                                     double half_dt, int slicing) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= G.cells) return;
+  double rt[kNFA];
+#pragma unroll
+  for (int F = 0; F < kNFA; ++F) {
+    double s = 0;
+#pragma unroll
+    for (int l = 0; l < Q; ++l) s += (double)Codec<S>::load_keep(f + (size_t)(F * Q + l) * G.pstride + c);
+    rt[F] = s;
+  }
+  double A[3], D[3][6];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    A[k] = rt[kA + k];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) D[k][q] = rt[kD + 6 * k + q];
+  }
+  double alpha, gm[6], K[6], V[3];
+  unpack<kABS, double>(rt, alpha, gm, K, V);
+  double Sr[kNF];
+  bm_sources<double>(alpha, gm, K, V, A, D, slicing, Sr);
+#pragma unroll
+  for (int F = 0; F < kNFA; ++F)
+    out[(int64_t)F * G.cells + c] = F < kNF ? rt[F] + half_dt * Sr[F] : rt[F];
+}
+
+inline unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+// Per-(Q, storage) launchers.
+template <int Q, class S>
+struct Ops {
+  using C = typename std::conditional<sizeof(S) == 8, double, float>::type;
+  template <int MINB>
+  static cudaError_t step(const Grid& G, const void* fin, void* fout, int* flag, double tau,
+                          double dt, int slicing, cudaStream_t st) {
+    Args<S, C> a;
+    a.fin = static_cast<const S*>(fin);
+    a.fout = static_cast<S*>(fout);
+    a.flag = flag;
+    a.G = G;
+    a.half_dt = C(0.5 * dt);
+    a.omega = C(1.0 / tau);
+    a.omc = C(1.0 - 1.0 / tau);
+    a.sigma = C(dt * (1.0 - 1.0 / (2.0 * tau)));
+    a.slicing = slicing;
+    k_ad_collide<Q, S, C, MINB><<<blocks_for(G.cells, 128), 128, 0, st>>>(a);
+    return cudaGetLastError();
+  }
+  static cudaError_t init(const Grid& G, const double* fields, int nf, void* f, int* flag,
+                          double dx, double dt, int slicing, cudaStream_t st) {
+    k_ad_init<Q, S><<<blocks_for(G.cells, 128), 128, 0, st>>>(
+        fields, nf, static_cast<S*>(f), flag, G, 1.0 / (2.0 * dx), 1.0 / (4.0 * dx), 0.5 * dt,
+        slicing);
+    return cudaGetLastError();
+  }
+  static cudaError_t moments(const Grid& G, const void* f, double* out, double dt, int slicing,
+                             cudaStream_t st) {
+    k_ad_moments<Q, S><<<blocks_for(G.cells, 128), 128, 0, st>>>(static_cast<const S*>(f), out,
+                                                                 G, 0.5 * dt, slicing);
+    return cudaGetLastError();
+  }
+  static cudaError_t get_plane(const Grid& G, const void* f, int F, int l, double* out,
+                               cudaStream_t st) {
+    k_get_plane<Q, S, kABS, kPingPong><<<blocks_for(G.cells, 256), 256, 0, st>>>(
+        static_cast<const S*>(f), out, G, F, l);
+    return cudaGetLastError();
+  }
+  static cudaError_t set_plane(const Grid& G, void* f, int F, int l, const double* in,
+                               cudaStream_t st) {
+    k_set_plane<Q, S, kABS, kPingPong><<<blocks_for(G.cells, 256), 256, 0, st>>>(
+        static_cast<S*>(f), in, G, F, l);
+    return cudaGetLastError();
+  }
+};
+
+// Launch forms: blocks of 128 threads sized for 2 to 5 blocks per SM.
+constexpr int kForms = 4;
+constexpr int kFormBlocks[kForms] = {2, 3, 4, 5};
+
+struct Table {
+  cudaError_t (*step[kForms])(const Grid&, const void*, void*, int*, double, double, int,
+                              cudaStream_t);
+  cudaError_t (*init)(const Grid&, const double*, int, void*, int*, double, double, int,
+                      cudaStream_t);
+  cudaError_t (*moments)(const Grid&, const void*, double*, double, int, cudaStream_t);
+  cudaError_t (*get_plane)(const Grid&, const void*, int, int, double*, cudaStream_t);
+  cudaError_t (*set_plane)(const Grid&, void*, int, int, const double*, cudaStream_t);
+};
+
+template <int Q, class S>
+Table make_table() {
+  return Table{{&Ops<Q, S>::template step<2>, &Ops<Q, S>::template step<3>,
+                &Ops<Q, S>::template step<4>, &Ops<Q, S>::template step<5>},
+               &Ops<Q, S>::init, &Ops<Q, S>::moments, &Ops<Q, S>::get_plane,
+               &Ops<Q, S>::set_plane};
+}
+
+// One translation unit per (Q, storage), compiled in parallel.
+Table table_q3_f64();
+Table table_q9_f64();
+Table table_q19_f64();
+Table table_q3_f32();
+Table table_q9_f32();
+Table table_q19_f32();
+
+}  // namespace ad
+}  // namespace lbnr
+

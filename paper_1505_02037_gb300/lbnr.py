@@ -118,14 +118,33 @@ def library(path: str | None = None):
     L.lbnr_destroy.restype = None
     L.lbnr_last_error.argtypes = [vp]
     L.lbnr_last_error.restype = ctypes.c_char_p
+    L.lbnr_ad_create.argtypes = [ctypes.POINTER(Grid), ctypes.c_int, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                 vp, ctypes.POINTER(vp)]
+    L.lbnr_ad_init.argtypes = [vp, dp, ctypes.c_int]
+    L.lbnr_ad_step.argtypes = [vp, i64]
+    L.lbnr_ad_step_timed.argtypes = [vp, i64, dp]
+    for name in ("lbnr_ad_moments", "lbnr_ad_get_distributions", "lbnr_ad_set_distributions"):
+        getattr(L, name).argtypes = [vp, dp]
+    L.lbnr_ad_status.argtypes = [vp]
+    L.lbnr_ad_set_form.argtypes = [vp, ctypes.c_int]
+    L.lbnr_ad_form_blocks.argtypes = [ctypes.c_int]
+    L.lbnr_ad_steps_done.argtypes = [vp]
+    L.lbnr_ad_steps_done.restype = i64
+    L.lbnr_ad_destroy.argtypes = [vp]
+    L.lbnr_ad_destroy.restype = None
+    L.lbnr_ad_last_error.argtypes = [vp]
+    L.lbnr_ad_last_error.restype = ctypes.c_char_p
     _lib = L
     return L
 
 
-def _check(rc, ctx=None, batch=None):
+def _check(rc, ctx=None, batch=None, ad=None):
     if rc == 0:
         return
-    if batch is not None:
+    if ad is not None:
+        msg = library().lbnr_ad_last_error(ad).decode(errors="replace")
+    elif batch is not None:
         msg = library().lbnr_batch_last_error(batch).decode(errors="replace")
     else:
         msg = library().lbnr_last_error(ctx).decode(errors="replace")
@@ -530,6 +549,78 @@ class Batch:
         if getattr(self, "b", None) is not None and self.b.value:
             lbnr_batch_destroy(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ADLattice:
+    """The 37-field scheme with independently evolved A_k and D_kij (the
+    original Bona-Masso formulation; lbnr_ad_* in include/lbnr.h): the 16
+    fields, then A_x A_y A_z, then D_kij at 19 + 6 k + pair. Ping-pong,
+    storage "f64" or "f32"."""
+
+    NF = 37
+
+    def __init__(self, vset, shape, tau, dx, slicing=LBNR_HARMONIC, storage="f64", stream=None):
+        lib = library()
+        self.vset, self.shape = int(vset), tuple(int(v) for v in shape)
+        self.cells = self.shape[0] * self.shape[1] * self.shape[2]
+        self.Q = {1: 3, 2: 9, 3: 19}[self.vset]
+        st = {"f64": LBNR_F64, "f32": LBNR_F32}[storage]
+        self.ctx = ctypes.c_void_p()
+        g = Grid(*self.shape)
+        sp = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+        _check(lib.lbnr_ad_create(ctypes.byref(g), self.vset, float(tau), float(dx), float(dx),
+                                  int(slicing), st, sp, ctypes.byref(self.ctx)), ad=None)
+        self.form = 0 if storage == "f64" else 1
+
+    @property
+    def forms(self):
+        """Launch forms: thread blocks per SM the registers are sized for."""
+        lib = library()
+        return [f"{lib.lbnr_ad_form_blocks(i)} blocks/SM" for i in range(lib.lbnr_ad_num_forms())]
+
+    def set_form(self, form):
+        _check(library().lbnr_ad_set_form(self.ctx, int(form)), ad=self.ctx)
+        self.form = int(form)
+
+    def init(self, fields):
+        f = np.ascontiguousarray(np.asarray(fields, dtype=np.float64)).reshape(-1, self.cells)
+        _check(library().lbnr_ad_init(self.ctx, _dptr(f), f.shape[0]), ad=self.ctx)
+
+    def step(self, n=1):
+        _check(library().lbnr_ad_step(self.ctx, int(n)), ad=self.ctx)
+
+    def step_timed(self, n=1):
+        ms = ctypes.c_double()
+        _check(library().lbnr_ad_step_timed(self.ctx, int(n), ctypes.byref(ms)), ad=self.ctx)
+        return ms.value
+
+    def moments(self):
+        out = np.empty((self.NF, self.cells))
+        _check(library().lbnr_ad_moments(self.ctx, _dptr(out)), ad=self.ctx)
+        return out
+
+    def status(self):
+        _check(library().lbnr_ad_status(self.ctx), ad=self.ctx)
+
+    def distributions(self):
+        out = np.empty((self.NF, self.Q, self.cells))
+        _check(library().lbnr_ad_get_distributions(self.ctx, _dptr(out)), ad=self.ctx)
+        return out
+
+    def set_distributions(self, f):
+        f = np.ascontiguousarray(np.asarray(f, dtype=np.float64))
+        _check(library().lbnr_ad_set_distributions(self.ctx, _dptr(f)), ad=self.ctx)
+
+    def close(self):
+        if self.ctx:
+            library().lbnr_ad_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
 
     def __del__(self):
         try:

@@ -2,6 +2,8 @@
 
   python -m paper_1505_02037_gb300.profile_step --storage f32 --n 128 \
       --variant 3 --steps 4 [--vset 3] [--tau 4.5] [--streaming 1] [--shift 0.25,0.1,-0.2]
+  python -m paper_1505_02037_gb300.profile_step --ad --storage f32 --n 128 --steps 4 \
+      [--variant FORM]
   python -m paper_1505_02037_gb300.profile_step --batch 16 --vset 2 --n 256 \
       --storage dev_f32 --steps 16 [--block 256 --per-sm 1]
 
@@ -35,11 +37,15 @@ def main(argv=None):
     p.add_argument("--block", type=int, default=256)
     p.add_argument("--per-sm", type=int, default=1)
     p.add_argument("--shift", default=None, help="bx,by,bz")
+    p.add_argument("--ad", action="store_true",
+                   help="the 37-field scheme (A_k and D_kij evolved); f64 or f32 storage")
     p.add_argument("--shift-field", type=float, default=0.0,
                    help="amplitude of a static shear shift field")
     a = p.parse_args(argv)
     if a.batch:
         return batch_main(a)
+    if a.ad:
+        return ad_main(a)
     n = a.n
     shape = (n, n, n) if a.vset == 3 else ((n, n, 1) if a.vset == 2 else (n, 1, 1))
     lat = lbnr.Lattice(a.vset, shape, a.tau, 1 / n, storage=a.storage, streaming=a.streaming)
@@ -60,6 +66,22 @@ def main(argv=None):
             "P1-reread-shift" if beta else lat.variants[a.variant])
     print(f"{a.storage} n={n} vset={a.vset} {form}: "
           f"ms per step aux {ms[0] / 4:.4f} collide {ms[1] / 4:.4f}")
+    return 0
+
+
+def ad_main(a):
+    n = a.n
+    shape = (n, n, n) if a.vset == 3 else ((n, n, 1) if a.vset == 2 else (n, 1, 1))
+    lat = lbnr.ADLattice(a.vset, shape, a.tau, 1 / n, storage=a.storage)
+    if a.variant >= 0:
+        lat.set_form(a.variant)
+    lat.init(W.gauge_wave(shape, 1 / n, 0.1))
+    lat.step(a.steps)
+    lat.status()
+    ms = lat.step_timed(4)
+    print(f"{a.storage} n={n} vset={a.vset} 37-field scheme, {lat.forms[lat.form]}: "
+          f"ms per step {ms / 4:.4f}")
+    lat.close()
     return 0
 
 

@@ -166,3 +166,32 @@ def test_largest_accepted_lattice_has_a_workspace_size():
     o.storage, o.streaming = 1, lbnr.LBNR_STREAM_AA
     n = lbnr.lbnr_workspace_bytes(lbnr.Grid(600, 600, 600), 3, o)
     assert n >= 16 * 19 * 4 * 600 ** 3
+
+
+@pytest.mark.parametrize("vset,shape,tau,dx,dt,slicing,storage", [
+    (3, (8, 8, 8), 1.0, 0.1, 0.1, 1, 2),      # deviation storage: not offered
+    (3, (8, 8, 8), 1.0, 0.1, 0.2, 1, 0),      # dt != dx
+    (3, (8, 8, 8), 0.5, 0.1, 0.1, 1, 0),      # tau <= 1/2
+    (1, (8, 2, 1), 1.0, 0.1, 0.1, 1, 0),      # D1Q3 with ny > 1
+    (4, (8, 8, 8), 1.0, 0.1, 0.1, 1, 0),      # unknown velocity set
+    (3, (8, 8, 8), 1.0, 0.1, 0.1, 3, 1),      # unknown slicing
+    (3, (1291, 1291, 1291), 1.0, 0.1, 0.1, 1, 1),  # past the 32-bit index limits
+])
+def test_ad_create_rejects_bad_arguments_before_the_device(lib, vset, shape, tau, dx, dt,
+                                                           slicing, storage):
+    """The 37-field context refuses bad arguments with LBNR_EINVAL before any
+    CUDA call (no GPU here)."""
+    from paper_1505_02037_gb300 import lbnr
+    out = ctypes.c_void_p()
+    g = lbnr.Grid(*shape)
+    rc = lib.lbnr_ad_create(ctypes.byref(g), vset, tau, dx, dt, slicing, storage, None,
+                            ctypes.byref(out))
+    assert rc == -1 and not out.value
+
+
+def test_ad_null_calls_fail_cleanly(lib):
+    assert lib.lbnr_ad_step(None, 1) == -1
+    assert lib.lbnr_ad_status(None) == -1
+    assert lib.lbnr_ad_moments(None, None) == -1
+    assert lib.lbnr_ad_steps_done(None) == -1
+    lib.lbnr_ad_destroy(None)
