@@ -199,6 +199,11 @@ COLLIDE_SOURCES = ("collide_tma.cuh", "dispatch.h", "instantiate.cuh", "kernels.
                    "inst_q19_s2.cu", "inst_q19_s3.cu", "inst_q19_s4.cu")
 
 
+# Sources the 37-field collide kernel is built from.
+AD_SOURCES = ("ad.cuh", "ad_q19_f32.cu", "dispatch.h", "kernels.cuh", "lattice.cuh",
+              "physics.cuh")
+
+
 def source_hash(files=COLLIDE_SOURCES):
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1505_02037_gb300", "csrc")
@@ -221,7 +226,7 @@ def profile_entry(kernel_key, field):
     return e.get(field)
 
 
-def traffic_for(kernel_key, cells):
+def traffic_for(kernel_key, cells, files=COLLIDE_SOURCES):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel sources (else None)."""
     try:
@@ -230,7 +235,7 @@ def traffic_for(kernel_key, cells):
     except OSError:
         return None
     e = t.get(kernel_key)
-    if not e or e.get("source_hash") != source_hash():
+    if not e or e.get("source_hash") != source_hash(files):
         return None
     return e["dram_bytes_per_cell"] * cells
 
@@ -509,7 +514,7 @@ def main_ad(args):
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": f"hbm_gbs of {peak_kind}",
                      "algorithmic_bytes_per_cell": alg / cells, "avg_launch_ms": kms,
-                     "traffic": traffic_for(tkey, cells)},
+                     "traffic": traffic_for(tkey, cells, AD_SOURCES)},
         "gpu_launches": args.steps, "launch_form": f"37-field, {best}",
         "autotune_ms_per_collide": tuning,
         "clocks": clk.summary(),
