@@ -16,6 +16,9 @@
 #include <type_traits>
 
 #include "../../include/lbnr.h"
+#include <cudaTypedefs.h>
+
+#include "collide_tma.cuh"
 #include "dispatch.h"
 #include "kernels.cuh"
 
@@ -253,6 +256,276 @@ __global__ void __launch_bounds__(128) k_ad_moments(const S* __restrict__ f,
 
 inline unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
+// ---------------------------------------------------------------------------
+// Shared-memory staged form: every distribution is read from HBM once
+// ---------------------------------------------------------------------------
+// One persistent CTA per SM. Warp NC (the producer) streams tiles of 32
+// consecutive cells, all 37*Q planes of each, into NS shared-memory stages
+// through 2D tensor copies of 37 planes each. Each stage belongs to a group
+// of P consumer warps, which takes the CTA's tiles s, s + NS, ... With P = 2
+// two lanes share a cell: each sums half of the 37 moments from shared
+// memory and the partner lanes swap them, both evaluate the cell's sources
+// and fluxes, and each relaxes and stores its half of the fields. The group
+// then frees the stage. Every wait is bounded (~2 s, then bit 1 of the flag).
+constexpr int kTileCells = 32;
+constexpr int kPlanesPerBox = kNFA;  // 37*Q planes = Q boxes of 37
+
+template <class S>
+__host__ __device__ constexpr uint32_t tma_stage(int Q) {
+  return (uint32_t)(kNFA * Q * kTileCells * sizeof(S));
+}
+// Stages that fit the 227 KB of shared memory (at most 4).
+template <class S>
+__host__ __device__ constexpr int tma_stages(int Q) {
+  return (int)((232448u - 1024u) / tma_stage<S>(Q)) > 4 ? 4
+                                                       : (int)((232448u - 1024u) / tma_stage<S>(Q));
+}
+
+// Relaxation coefficient and flux of field F (compile-time F after
+// unrolling): coef = omega rho + sigma S for the 16 fields, omega rho~ for A
+// and D (no source); b[k] = 3 omega times the flux along k.
+template <int dim, class C>
+__device__ __forceinline__ void ad_field_terms(int F, const C rt[kNFA], const C rho[kNF],
+                                               const C Sr[kNF], const C Fl[6][3], C aQ,
+                                               const C aK[6], C omega, C sigma, C& cf, C b[3]) {
+  const C three_omega = C(3) * omega;
+  b[0] = b[1] = b[2] = C(0);
+  if (F < kNF) {
+    cf = omega * rho[F] + sigma * Sr[F];
+    if (has_flux(F)) {
+#pragma unroll
+      for (int k = 0; k < dim; ++k) b[k] = three_omega * Fl[F - kK][k];
+    }
+  } else {
+    cf = omega * rt[F];
+    const int k = F < kD ? F - kA : (F - kD) / 6;
+    const C fk = F < kD ? aQ : aK[(F - kD) % 6];
+#pragma unroll
+    for (int kk = 0; kk < dim; ++kk)
+      if (kk == k) b[kk] = three_omega * fk;
+  }
+}
+
+template <int Q, class S, class C, int NS, int P>
+__global__ void __launch_bounds__(32 * (NS * P + 1), 1)
+    k_ad_collide_tma(const Args<S, C> a, const __grid_constant__ CUtensorMap tmap, int64_t ntiles) {
+  static_assert(P == 1 || P == 2, "one or two lanes per cell");
+  using L = Lattice<Q>;
+  constexpr int dim = L::kDim;
+  constexpr int T = kTileCells;
+  constexpr int NC = NS * P;  // consumer warps
+  constexpr int kBoxes = Q;
+  constexpr uint32_t ROWB = T * sizeof(S);
+  constexpr uint32_t BOXB = kPlanesPerBox * ROWB;
+  constexpr uint32_t STAGEB = tma_stage<S>(Q);
+  constexpr uint64_t kLimitNs = 2000000000ull;
+  static_assert(BOXB % 128 == 0 && STAGEB % 128 == 0, "tensor copies land on 128-byte rows");
+
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);  // [0,NS) full, [NS,2NS) empty
+  unsigned char* stages = smem + 1024;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(smem_u32(&bars[s]), 1);
+      mbar_init(smem_u32(&bars[NS + s]), P);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int64_t G = gridDim.x;
+  const int64_t my = (int64_t)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / G + 1 : 0;
+
+  if (warp == NC) {
+    // ---------------- producer ----------------
+    if (lane == 0) {
+      int64_t issued = 0;
+      for (int64_t j = 0; j < my; ++j) {
+        const int s = (int)(j % NS);
+        const int64_t r = j / NS;
+        if (r >= 1 && !mbar_wait(smem_u32(&bars[NS + s]), (uint32_t)((r - 1) & 1), kLimitNs)) {
+          atomicOr(a.flag, 2);
+          break;
+        }
+        const int64_t tile = blockIdx.x + j * G;
+        if ((tile + 1) * T > a.G.pstride) {  // never true for a consistent launch
+          atomicOr(a.flag, 4);
+          break;
+        }
+        const uint32_t fb = smem_u32(&bars[s]);
+        mbar_expect_tx(fb, STAGEB);
+        const uint32_t dst = smem_u32(stages + (size_t)s * STAGEB);
+#pragma unroll 1
+        for (int b = 0; b < kBoxes; ++b)
+          tma_load_2d(dst + b * BOXB, &tmap, (int32_t)(tile * T), b * kPlanesPerBox, fb);
+        issued = j + 1;
+      }
+      // leave only when every copy started here has landed
+      for (int64_t j = issued > NS ? issued - NS : 0; j < issued; ++j) {
+        if (!mbar_wait(smem_u32(&bars[j % NS]), (uint32_t)((j / NS) & 1), kLimitNs)) {
+          atomicOr(a.flag, 2);
+          break;
+        }
+      }
+    }
+    return;
+  }
+
+  // ---------------- consumers ----------------
+  const int s = warp / P;
+  const int g = P == 2 ? (lane >> 4) : 0;  // which half of the fields this lane owns
+  const int ci = P == 2 ? (warp % P) * 16 + (lane & 15) : lane;
+  const int64_t cells = a.G.cells;
+  const uint32_t ps = (uint32_t)a.G.pstride;
+  for (int64_t m = 0;; ++m) {
+    const int64_t j = s + m * NS;
+    if (j >= my) break;
+    const int64_t tile = blockIdx.x + j * G;
+    const int64_t cell = tile * T + ci;
+    const bool valid = cell < cells;
+    const int64_t c = valid ? cell : cells - 1;
+    const Nbr n = make_nbr(a.G, c);
+    if (!mbar_wait(smem_u32(&bars[s]), (uint32_t)(m & 1), kLimitNs)) {
+      if (lane == 0) atomicOr(a.flag, 2);
+      break;
+    }
+    const S* st = reinterpret_cast<const S*>(stages + (size_t)s * STAGEB);
+    C rt[kNFA];
+    if constexpr (P == 1) {
+#pragma unroll
+      for (int F = 0; F < kNFA; ++F) {
+        const S* row = st + (F * Q) * T + ci;
+        C sum = C(0);
+#pragma unroll
+        for (int l = 0; l < Q; ++l) sum += (C)row[l * T];
+        rt[F] = sum;
+      }
+    } else {
+      // fields 2jj (lanes g = 0) and 2jj + 1 (g = 1), swapped between
+      // partner lanes; both lanes sum field 36
+#pragma unroll
+      for (int jj = 0; jj < kNFA / 2; ++jj) {
+        const S* row = st + ((2 * jj + g) * Q) * T + ci;
+        C sum = C(0);
+#pragma unroll
+        for (int l = 0; l < Q; ++l) sum += (C)row[l * T];
+        const C other = __shfl_xor_sync(0xffffffffu, sum, 16);
+        rt[2 * jj] = g ? other : sum;
+        rt[2 * jj + 1] = g ? sum : other;
+      }
+      {
+        const S* row = st + ((kNFA - 1) * Q) * T + ci;
+        C sum = C(0);
+#pragma unroll
+        for (int l = 0; l < Q; ++l) sum += (C)row[l * T];
+        rt[kNFA - 1] = sum;
+      }
+    }
+    {
+      C chk = C(0);
+#pragma unroll
+      for (int F = 0; F < kNFA; ++F) chk += rt[F];
+      if (valid && g == 0 && !isfinite(chk)) atomicOr(a.flag, 1);
+    }
+    C A[3], D[3][6];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      A[k] = rt[kA + k];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) D[k][q] = rt[kD + 6 * k + q];
+    }
+    C alpha, gm[6], K[6], V[3];
+    unpack<kABS, C>(rt, alpha, gm, K, V);
+    C Sr[kNF];
+    bm_sources<C>(alpha, gm, K, V, A, D, a.slicing, Sr);
+    C rho[kNF];
+#pragma unroll
+    for (int F = 0; F < kNF; ++F) rho[F] = rt[F] + a.half_dt * Sr[F];
+    C Fl[6][3], aQ, aK[6];
+    {
+      C alpha2, g2[6], K2[6], V2[3];
+      unpack<kABS, C>(rho, alpha2, g2, K2, V2);
+      bm_flux<C, dim>(alpha2, g2, V2, A, D, Fl);
+      aQ = alpha_q<C>(a.slicing, alpha2, g2, K2);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) aK[q] = alpha2 * K2[q];
+    }
+    uint32_t woff[Q];
+#pragma unroll
+    for (int l = 0; l < Q; ++l) woff[l] = (uint32_t)l * ps + n.at(L::c(l, 0), L::c(l, 1), L::c(l, 2));
+
+    // relax and store: field F of this lane, coefficients cf and b
+    auto relax = [&](int F, C cf, const C b[3], bool store) {
+      const S* row = st + (F * Q) * T + ci;
+      S* ob = a.fout + (size_t)F * Q * ps;
+#pragma unroll
+      for (int l = 0; l < Q; ++l) {
+        C t = cf;
+#pragma unroll
+        for (int k = 0; k < dim; ++k) {
+          if (L::c(l, k) > 0) t += b[k];
+          if (L::c(l, k) < 0) t -= b[k];
+        }
+        const C out = fma(a.omc, (C)row[l * T], C(L::w(l)) * t);
+        Codec<S>::store_if(ob + woff[l], out, store);
+      }
+    };
+    if constexpr (P == 1) {
+#pragma unroll
+      for (int F = 0; F < kNFA; ++F) {
+        C cf, b[3];
+        ad_field_terms<dim, C>(F, rt, rho, Sr, Fl, aQ, aK, a.omega, a.sigma, cf, b);
+        relax(F, cf, b, valid);
+      }
+    } else {
+#pragma unroll
+      for (int jj = 0; jj < kNFA / 2; ++jj) {
+        C cf0, b0[3], cf1, b1[3];
+        ad_field_terms<dim, C>(2 * jj, rt, rho, Sr, Fl, aQ, aK, a.omega, a.sigma, cf0, b0);
+        ad_field_terms<dim, C>(2 * jj + 1, rt, rho, Sr, Fl, aQ, aK, a.omega, a.sigma, cf1, b1);
+        const C b[3] = {g ? b1[0] : b0[0], g ? b1[1] : b0[1], g ? b1[2] : b0[2]};
+        relax(2 * jj + g, g ? cf1 : cf0, b, valid);
+      }
+      C cf, b[3];
+      ad_field_terms<dim, C>(kNFA - 1, rt, rho, Sr, Fl, aQ, aK, a.omega, a.sigma, cf, b);
+      relax(kNFA - 1, cf, b, valid && g == 0);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(smem_u32(&bars[NS + s]));
+  }
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point.
+inline PFN_cuTensorMapEncodeTiled_v12000 ad_tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 2D view of a 37-field buffer: x = cell (stride 1), y = plane (37*Q planes,
+// stride pstride); boxes of 32 cells x 37 planes.
+template <int Q, class S>
+cudaError_t encode_ad_planes(const void* base, int64_t pstride, CUtensorMap* map) {
+  auto fn = ad_tensor_map_encoder();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t dims[2] = {(cuuint64_t)pstride, (cuuint64_t)(kNFA * Q)};
+  const cuuint64_t strides[1] = {(cuuint64_t)pstride * sizeof(S)};
+  const cuuint32_t box[2] = {(cuuint32_t)kTileCells, (cuuint32_t)kPlanesPerBox};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, sizeof(S) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                  2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 // Per-(Q, storage) launchers.
 template <int Q, class S>
 struct Ops {
@@ -271,6 +544,36 @@ struct Ops {
     a.sigma = C(dt * (1.0 - 1.0 / (2.0 * tau)));
     a.slicing = slicing;
     k_ad_collide<Q, S, C, MINB><<<blocks_for(G.cells, 128), 128, 0, st>>>(a);
+    return cudaGetLastError();
+  }
+  template <int P>
+  static cudaError_t step_tma(const Grid& G, const void* fin, void* fout, int* flag, double tau,
+                              double dt, int slicing, cudaStream_t st) {
+    constexpr int NS = tma_stages<S>(Q);
+    static_assert(NS >= 1, "a stage must fit in shared memory");
+    constexpr uint32_t smem = 1024u + NS * tma_stage<S>(Q);
+    Args<S, C> a;
+    a.fin = static_cast<const S*>(fin);
+    a.fout = static_cast<S*>(fout);
+    a.flag = flag;
+    a.G = G;
+    a.half_dt = C(0.5 * dt);
+    a.omega = C(1.0 / tau);
+    a.omc = C(1.0 - 1.0 / tau);
+    a.sigma = C(dt * (1.0 - 1.0 / (2.0 * tau)));
+    a.slicing = slicing;
+    auto kern = k_ad_collide_tma<Q, S, C, NS, P>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    CUtensorMap map;
+    e = encode_ad_planes<Q, S>(fin, G.pstride, &map);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t ntiles = G.pstride / kTileCells;
+    const int64_t grid = ntiles < sms ? ntiles : (sms > 0 ? sms : 1);
+    kern<<<(unsigned)grid, 32 * (NS * P + 1), smem, st>>>(a, map, ntiles);
     return cudaGetLastError();
   }
   static cudaError_t init(const Grid& G, const double* fields, int nf, void* f, int* flag,
@@ -300,9 +603,11 @@ struct Ops {
   }
 };
 
-// Launch forms: blocks of 128 threads sized for 2 to 5 blocks per SM.
-constexpr int kForms = 4;
-constexpr int kFormBlocks[kForms] = {2, 3, 4, 5};
+// Launch forms: blocks of 128 threads sized for 2 to 5 blocks per SM, and
+// the shared-memory staged form with one or two lanes per cell (blocks per
+// SM 0 and -1 mark them).
+constexpr int kForms = 6;
+constexpr int kFormBlocks[kForms] = {2, 3, 4, 5, 0, -1};
 
 struct Table {
   cudaError_t (*step[kForms])(const Grid&, const void*, void*, int*, double, double, int,
@@ -317,7 +622,8 @@ struct Table {
 template <int Q, class S>
 Table make_table() {
   return Table{{&Ops<Q, S>::template step<2>, &Ops<Q, S>::template step<3>,
-                &Ops<Q, S>::template step<4>, &Ops<Q, S>::template step<5>},
+                &Ops<Q, S>::template step<4>, &Ops<Q, S>::template step<5>,
+                &Ops<Q, S>::template step_tma<1>, &Ops<Q, S>::template step_tma<2>},
                &Ops<Q, S>::init, &Ops<Q, S>::moments, &Ops<Q, S>::get_plane,
                &Ops<Q, S>::set_plane};
 }

@@ -576,13 +576,15 @@ class ADLattice:
         sp = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
         _check(lib.lbnr_ad_create(ctypes.byref(g), self.vset, float(tau), float(dx), float(dx),
                                   int(slicing), st, sp, ctypes.byref(self.ctx)), ad=None)
-        self.form = 0 if storage == "f64" else 1
+        self.form = 0 if storage == "f64" else 5
 
     @property
     def forms(self):
         """Launch forms: thread blocks per SM the registers are sized for."""
         lib = library()
-        return [f"{lib.lbnr_ad_form_blocks(i)} blocks/SM" for i in range(lib.lbnr_ad_num_forms())]
+        names = {0: "smem-staged, 1 lane/cell", -1: "smem-staged, 2 lanes/cell"}
+        return [names.get(b, f"{b} blocks/SM") for b in
+                (lib.lbnr_ad_form_blocks(i) for i in range(lib.lbnr_ad_num_forms()))]
 
     def set_form(self, form):
         _check(library().lbnr_ad_set_form(self.ctx, int(form)), ad=self.ctx)
