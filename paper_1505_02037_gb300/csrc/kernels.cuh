@@ -361,9 +361,10 @@ __device__ __forceinline__ void unpack(const C m[kNF], C& alpha, C g[6], C K[6],
 // ---------------------------------------------------------------------------
 // SHIFT: the shift terms are compiled in: 1 a constant shift (a.beta),
 // 2 a static field on top of it (a.beta_field, with its B terms). The
-// zero-shift forms (0) keep none of their code or registers.
-template <int Q, class S, class C, int REP, int LAYOUT, int P, bool HOLD, int SHIFT = 0>
-__global__ void __launch_bounds__(128, HOLD ? 1 : 3) k_collide(const StepArgs<S, C> a) {
+// zero-shift forms (0) keep none of their code or registers. MINB: blocks
+// per SM the registers are sized for (without HOLD).
+template <int Q, class S, class C, int REP, int LAYOUT, int P, bool HOLD, int SHIFT = 0, int MINB = 3>
+__global__ void __launch_bounds__(128, HOLD ? 1 : MINB) k_collide(const StepArgs<S, C> a) {
   using L = Lattice<Q>;
   constexpr int NJ = kNF / P;
   constexpr int dim = L::kDim;
