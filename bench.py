@@ -256,7 +256,7 @@ def cpu_baseline(vset, storage, direction, A, tau, wave="gauge", seconds=12.0, b
         f = o.step(f)
         steps += 1
         el = time.perf_counter() - t0
-        if el > seconds or steps >= 200:
+        if el > seconds or steps >= 1000:
             break
     cells = n ** 3 if vset == 3 else n * n
     return {"value": cells * 16 * steps / el / 1e6, "unit": "Mcell*var/s", "cores": cores,
@@ -414,7 +414,7 @@ def ad_oracle_rate(args, n, steps=None, seconds=12.0):
         f = o.ad_step(f)
         done += 1
         el = time.perf_counter() - t0
-        if (steps is not None and done >= steps) or (steps is None and (el > seconds or done >= 200)):
+        if (steps is not None and done >= steps) or (steps is None and (el > seconds or done >= 1000)):
             break
     return n ** 3 * AD_NF * done / el / 1e6, done, el, cores
 
