@@ -787,10 +787,29 @@ __global__ void __launch_bounds__(256) k_sum64(const S* __restrict__ f, double* 
   for (int F = 0; F < kNF; ++F) {
     double s = 0;
     if (valid) {
+      if constexpr (sizeof(S) == 4 && REP == kABS) {
+        // FP32 values summed in FP32 with the rounding error of every
+        // addition carried along (Knuth's TwoSum): hi + lo holds the sum to
+        // about twice FP32's precision, as the FP64 sum would, without
+        // putting 2 Q FP64 operations per field on the FP64 pipe.
+        float hi = 0.f, lo = 0.f;
 #pragma unroll
-      for (int l = 0; l < Q; ++l) {
-        const double v = (double)Codec<S>::load_keep(f + read_index<Q, LAYOUT>(n, G.pstride, F, l));
-        s += REP == kDEV ? L::w(l) * v : v;
+        for (int l = 0; l < Q; ++l) {
+          const float v = Codec<S>::load_keep(f + read_index<Q, LAYOUT>(n, G.pstride, F, l));
+          const float t = __fadd_rn(hi, v);
+          const float bp = __fsub_rn(t, hi);
+          const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(v, bp));
+          hi = t;
+          lo = __fadd_rn(lo, e);
+        }
+        s = (double)hi + (double)lo;
+      } else {
+#pragma unroll
+        for (int l = 0; l < Q; ++l) {
+          const double v =
+              (double)Codec<S>::load_keep(f + read_index<Q, LAYOUT>(n, G.pstride, F, l));
+          s += REP == kDEV ? L::w(l) * v : v;
+        }
       }
       if (REP == kDEV) s += flat_value(F);
       macro[(int64_t)F * G.cells + c] = s;

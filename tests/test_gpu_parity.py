@@ -291,3 +291,23 @@ def test_flat_space_stays_flat_all_storages(L):
         lat.step(5)
         m = lat.moments()
         assert np.abs(m - W.flat(shape).reshape(16, -1)).max() < 1e-6, storage
+
+
+@pytest.mark.parametrize("streaming", [1, 2])
+def test_fp32_moment_sums_match_exact_sums(L, streaming):
+    """The FP64 moment pass over FP32 storage adds each cell's 19 values in
+    FP32 with compensated (TwoSum) arithmetic. Its 16 lattice sums of rho~ (the
+    monitor's last 16 values) must match the exact sums of the stored values,
+    taken here with math.fsum, to 1e-13 of each field's magnitude, after odd and
+    even step counts (both AA parities)."""
+    shape = (28, 28, 28)
+    fields = W.add_noise(W.gauge_wave(shape, 1 / 28, 0.1, direction="xyz"), 1e-3, seed=12)
+    lat = L.Lattice(3, shape, 1.5, 1 / 28, storage="f32", streaming=streaming)
+    lat.init(fields)
+    for n in (3, 4):
+        lat.step(n)
+        f = lat.distributions().reshape(16, -1)
+        exact = np.array([math.fsum(f[F]) for F in range(16)])
+        got = lat.constraints()[6:]
+        scale = np.abs(f).reshape(16, -1).sum(axis=1)
+        assert np.all(np.abs(got - exact) <= 1e-13 * scale), (got - exact) / scale
