@@ -451,3 +451,26 @@ def test_full_size_256_cubed_shift_field_fp32_against_fp64(L, oracle_mod):
     for n in (1, 2):
         err = float(np.abs(runs["f32"][n - 1] - runs["f64"][n - 1]).max() / A)
         assert err <= bound("f32", True, N, tau, n, lam), (n, err)
+
+
+@pytest.mark.parametrize("storage", ["f32", "dev_f32", "dev_bf16"])
+def test_shift_field_aa_equals_pingpong(L, storage):
+    """The shift-field form in place (AA, both parities) against ping-pong, in
+    each reduced storage: the same arithmetic, to a few rounding units."""
+    shape = (20, 12, 8)
+    beta = (0.05, -0.02, 0.03)
+    field = W.smooth_shift(shape, 1 / 20, 0.05, seed=31)
+    fields = W.add_noise(W.gauge_wave(shape, 1 / 20, 0.05, beta=beta), 1e-4, seed=32)
+    tol = {"f32": 1e-5, "dev_f32": 1e-5, "dev_bf16": 3e-2}[storage]
+    lats = []
+    for streaming in (1, 2):
+        lat = L.Lattice(3, shape, 1.2, 1 / 20, storage=storage, streaming=streaming)
+        lat.set_shift(beta)
+        lat.set_shift_field(field)
+        lat.init(fields)
+        lats.append(lat)
+    for n in (1, 2, 3):
+        for lat in lats:
+            lat.step(n)
+        a, b = lats[0].distributions(), lats[1].distributions()
+        assert dist_err(b, a, 0.05 * math.pi).max() < tol, (storage, n)
