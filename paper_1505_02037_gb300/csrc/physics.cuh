@@ -131,6 +131,11 @@ __device__ __forceinline__ void bm_sources(const T alpha, const T g[6], const T 
       for (int a = 0; a < 3; ++a) t += gi[sym(k, a)] * Dl[k][a][r];
     Dkk[r] = t;
   }
+  // In FP64 (bound by its arithmetic) two sums are taken with fewer
+  // operations: D_k^{rs} Gamma^k_rs over the six pairs r <= s (both factors
+  // are symmetric in rs), and M_ij = D_ik^r D_rj^k once for all six S_ij. The
+  // FP32 forms keep the plain sums, whose register allocation they are tuned to.
+  constexpr bool kLean = sizeof(T) == 8;
   // D_k^{rs} Gamma^k_rs, with D_k^{rs} = g^{ra} D_ka^s
   T DG = T(0);
 #pragma unroll
@@ -138,11 +143,25 @@ __device__ __forceinline__ void bm_sources(const T alpha, const T g[6], const T 
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
-      for (int s = 0; s < 3; ++s) {
+      for (int s = kLean ? r : 0; s < 3; ++s) {
         const T Duu = gi[sym(r, 0)] * Dl[k][0][s] + gi[sym(r, 1)] * Dl[k][1][s] +
                       gi[sym(r, 2)] * Dl[k][2][s];
-        DG += Duu * Gam[k][sym(r, s)];
+        DG += (kLean && r != s ? T(2) : T(1)) * Duu * Gam[k][sym(r, s)];
       }
+  T Mdd[3][3];
+  if (kLean) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        T t = T(0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int r = 0; r < 3; ++r) t += Dl[i][k][r] * Dl[r][j][k];
+        Mdd[i][j] = t;
+      }
+  }
   const T bracket = -DG + (tr1[0] * tr1u[0] + tr1[1] * tr1u[1] + tr1[2] * tr1u[2]) -
                     T(2) * (Vu[0] * A[0] + Vu[1] * A[1] + Vu[2] * A[2]) + trK2 - trK * trK;
 
@@ -156,12 +175,20 @@ __device__ __forceinline__ void bm_sources(const T alpha, const T g[6], const T 
       T t = -T(2) * (K[sym(i, 0)] * Km[0][j] + K[sym(i, 1)] * Km[1][j] + K[sym(i, 2)] * Km[2][j]) +
             trK * K[q];
       // 2 D_ik^r D_rj^k + 2 D_jk^r D_ri^k ; Gamma^k_kr Gamma^r_ij - Gamma^k_ri Gamma^r_kj
+      if (kLean) {
+        t += T(2) * (Mdd[i][j] + Mdd[j][i]);
 #pragma unroll
-      for (int k = 0; k < 3; ++k)
+        for (int k = 0; k < 3; ++k)
 #pragma unroll
-        for (int r = 0; r < 3; ++r)
-          t += T(2) * (Dl[i][k][r] * Dl[r][j][k] + Dl[j][k][r] * Dl[r][i][k]) -
-               Gam[k][sym(r, i)] * Gam[r][sym(k, j)];
+          for (int r = 0; r < 3; ++r) t -= Gam[k][sym(r, i)] * Gam[r][sym(k, j)];
+      } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int r = 0; r < 3; ++r)
+            t += T(2) * (Dl[i][k][r] * Dl[r][j][k] + Dl[j][k][r] * Dl[r][i][k]) -
+                 Gam[k][sym(r, i)] * Gam[r][sym(k, j)];
+      }
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
         t += Gc[r] * Gam[r][q];
