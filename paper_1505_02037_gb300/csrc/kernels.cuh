@@ -504,18 +504,24 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : MINB) k_collide(const StepArgs
 #pragma unroll
       for (int k = 0; k < dim; ++k) b[k] = mv * a.beta[k];
     }
+    // FP64 (bound by its arithmetic): w_l (cf + c.b) as w_l cf + c.(w_l b),
+    // whose products repeat across velocities of equal weight and are formed
+    // once each, instead of one product per velocity
+    constexpr bool kLeanRelax = sizeof(C) == 8 && REP == kABS;
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
       const C v = v_[l];
-      C t = cf;
+      C t = kLeanRelax ? C(L::w(l)) * cf : cf;
       if (has_flux(F0) || vflux) {
 #pragma unroll
         for (int k = 0; k < dim; ++k) {
-          if (L::c(l, k) > 0) t += b[k];
-          if (L::c(l, k) < 0) t -= b[k];
+          const C bk = kLeanRelax ? C(L::w(l)) * b[k] : b[k];
+          if (L::c(l, k) > 0) t += bk;
+          if (L::c(l, k) < 0) t -= bk;
         }
       }
-      const C out = REP == kDEV ? fma(a.omc, v, t) : fma(a.omc, v, C(L::w(l)) * t);
+      const C out = REP == kDEV ? fma(a.omc, v, t)
+                                : (kLeanRelax ? fma(a.omc, v, t) : fma(a.omc, v, C(L::w(l)) * t));
       // Ping-pong: lanes past the last cell were clamped to it and write the
       // same bytes as its own lanes, so every store can be unconditional.
       if (LAYOUT == kPingPong)
@@ -663,17 +669,23 @@ __device__ __forceinline__ void collide_cell(const StepArgs<S, C>& a, int64_t c)
     C v_[Q];
 #pragma unroll
     for (int l = 0; l < Q; ++l) v_[l] = Codec<S>::load_coh(fb + read_off<Q, LAYOUT>(n, ps32, l));
+    // FP64: the same weight-first form as k_collide, so a batched run stays
+    // bitwise equal to the run on its own context
+    constexpr bool kLeanRelax = sizeof(C) == 8 && REP == kABS;
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
-      C t = cf;
+      C t = kLeanRelax ? C(L::w(l)) * cf : cf;
       if (has_flux(F)) {
 #pragma unroll
         for (int k = 0; k < dim; ++k) {
-          if (L::c(l, k) > 0) t += b[k];
-          if (L::c(l, k) < 0) t -= b[k];
+          const C bk = kLeanRelax ? C(L::w(l)) * b[k] : b[k];
+          if (L::c(l, k) > 0) t += bk;
+          if (L::c(l, k) < 0) t -= bk;
         }
       }
-      const C out = REP == kDEV ? fma(a.omc, v_[l], t) : fma(a.omc, v_[l], C(L::w(l)) * t);
+      const C out = REP == kDEV ? fma(a.omc, v_[l], t)
+                                : (kLeanRelax ? fma(a.omc, v_[l], t)
+                                              : fma(a.omc, v_[l], C(L::w(l)) * t));
       Codec<S>::store(ob + write_off<Q, LAYOUT>(n, ps32, l), out);
     }
   }
