@@ -167,17 +167,19 @@ int lbnr_ad_step(lbnr_ad_ctx* c, int64_t n) {
 
 int lbnr_ad_step_timed(lbnr_ad_ctx* c, int64_t n, double* ms_out) {
   if (!c || !ms_out) return ad_fail(c, LBNR_EINVAL, "null context or output");
-  cudaEvent_t e0, e1;
-  AD_TRY(c, cudaEventCreate(&e0));
-  AD_TRY(c, cudaEventCreate(&e1));
-  cudaEventRecord(e0, c->st);
-  int rc = lbnr_ad_step(c, n);
-  cudaEventRecord(e1, c->st);
-  cudaEventSynchronize(e1);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, c->st);
+  int rc = e == cudaSuccess ? lbnr_ad_step(c, n) : LBNR_OK;
+  if (e == cudaSuccess) e = cudaEventRecord(e1, c->st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
   float ms = 0;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess)
+    return ad_fail(c, LBNR_ECUDA, "step_timed: %s", cudaGetErrorString(e));
   *ms_out = ms;
   return rc;
 }

@@ -449,8 +449,15 @@ int lbnr_step_timed(lbnr_ctx* c, int64_t n, double* ms_out) {
   if (!c || !ms_out) return fail(c, LBNR_EINVAL, "null argument");
   if (n < 0) return fail(c, LBNR_EINVAL, "negative step count");
   if (!c->initialised) return fail(c, LBNR_ESTATE, "step before init");
-  cudaEvent_t ev[3];
-  for (auto& e : ev) CUDA_TRY(c, cudaEventCreate(&e));
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  for (auto& e : ev) {
+    const cudaError_t ce = cudaEventCreate(&e);
+    if (ce != cudaSuccess) {
+      for (auto& d : ev)
+        if (d) cudaEventDestroy(d);
+      return fail(c, LBNR_ECUDA, "timed step: %s", cudaGetErrorString(ce));
+    }
+  }
   double t_aux = 0, t_col = 0;
   int rc = LBNR_OK;
   for (int64_t i = 0; i < n && rc == LBNR_OK; ++i) {
