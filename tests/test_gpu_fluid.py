@@ -104,3 +104,26 @@ def test_fluid_off_is_vacuum(L):
     a.step(7)
     b.step(7)
     assert np.array_equal(a.distributions(), b.distributions())
+
+
+@pytest.mark.parametrize("with_field", [False, True])
+def test_fluid_with_shift_fp64_matches_oracle(L, oracle_mod, with_field):
+    """The fluid's term and the shift's terms together (constant shift, and
+    with a smooth static shift field), diagonal gauge wave on 12^3, 10 steps,
+    every 1+log slicing term, against the oracle at 1e-12."""
+    N, shape = 12, (12, 12, 12)
+    beta = (0.05, -0.03, 0.02)
+    field = W.smooth_shift(shape, 1 / N, 0.04, seed=44) if with_field else None
+    fields = W.gauge_wave(shape, 1 / N, 0.05, direction="xyz", beta=beta)
+    lat = L.Lattice(3, shape, 1.5, 1 / N, slicing=2)
+    lat.set_fluid(0.2, 1.0 / 3.0, 1.5)
+    lat.set_shift(beta)
+    if with_field:
+        lat.set_shift_field(field)
+    lat.init(fields)
+    lat.step(10)
+    o = oracle_mod.Oracle(3, shape, 1.5, 1 / N, slicing=2, fluid=(0.2, 1.0 / 3.0, 1.5),
+                          shift=beta, shift_field=field)
+    f = o.run(o.init(fields, t=1.5), 10, t=1.5)
+    assert rel(lat.distributions(), f, 0.05 * math.pi / 3) < TOL64
+    assert rel(lat.moments(), o.moments(f, t=1.5 + 10 / N), 0.05 * math.pi) < TOL64
