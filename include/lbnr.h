@@ -214,12 +214,16 @@ int lbnr_streaming(const lbnr_ctx* ctx);
  * The per-block partial sums live in one fixed array compiled into the
  * library (LBNR_NOALLOC_MAX_CELLS / 128 blocks x 22 doubles, 2.75 MiB); every
  * GPU that loads the library keeps it until the process exits. Lattices of
- * more than LBNR_NOALLOC_MAX_CELLS cells give LBNR_EINVAL. The first call on
- * a device looks up the array's device address (with that device current),
- * so make that first call before any stream capture. All calls share the
- * array: calls whose work overlaps on the GPU (different streams, or
- * different host threads) race and must be serialised by the caller. Errors
- * are reported through lbnr_last_error(NULL). */
+ * more than LBNR_NOALLOC_MAX_CELLS cells (or with any side above it) give
+ * LBNR_EINVAL. The first call on a device looks up the array's device
+ * address (with that device current) and keeps it for that device's context;
+ * after the context is reset (cudaDeviceReset) the next call looks it up
+ * again. So make the first call on each device, and the first after a reset,
+ * before any stream capture. d_fields, d_out and the stream must belong to
+ * the current device. All calls share the array: calls whose work overlaps on
+ * the GPU (different streams, or different host threads) race and must be
+ * serialised by the caller. Errors are reported through
+ * lbnr_last_error(NULL). */
 int lbnr_constraint_norms_noalloc(int vset, const lbnr_grid* grid, double dx,
                                   const double* d_fields, double* d_out, void* cuda_stream);
 

@@ -13,10 +13,12 @@
 //
 // The array lives in every GPU that loads the library until the process
 // exits. Its size bounds the lattice: at most kNoAllocMaxCells cells.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "../../include/lbnr.h"
 #include "dispatch.h"
@@ -36,9 +38,66 @@ constexpr int kMaxDevices = 64;
 // it later reads, so nothing has to start at zero.
 static __device__ __align__(256) double g_partials[kMaxBlocks * kPartialStride];
 
-// Device address of g_partials, looked up once per device (host code cannot
-// use the symbol itself: on the host it is only a stand-in).
-void* g_addr[kMaxDevices] = {nullptr};
+// Device address of g_partials, looked up once per device context (host code
+// cannot use the symbol itself: on the host it is only a stand-in). The entry
+// is keyed on the context's unique ID, so after a device reset (a new context,
+// into which the module is loaded again and where the array may sit at another
+// address) the next call looks the address up again instead of reusing a stale
+// pointer.
+struct SymbolSlot {
+  unsigned long long ctx_id;
+  void* addr;
+};
+SymbolSlot g_slot[kMaxDevices] = {};
+std::mutex g_slot_mu;
+
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext*);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long*);
+
+// Unique ID of the calling thread's current context; false when there is none
+// yet (the runtime creates it on the first call that needs it) or the driver
+// offers no way to ask.
+bool current_ctx_id(unsigned long long* id) {
+  static PfnCtxGetCurrent get_current = nullptr;
+  static PfnCtxGetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<PfnCtxGetCurrent>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<PfnCtxGetId>(p);
+  });
+  if (!get_current || !get_id) return false;
+  CUcontext c = nullptr;
+  if (get_current(&c) != CUDA_SUCCESS || !c) return false;
+  return get_id(c, id) == CUDA_SUCCESS;
+}
+
+// Device address of g_partials in the current device's context.
+cudaError_t partials_address(int dev, void** out) {
+  unsigned long long id = 0;
+  const bool have_id = current_ctx_id(&id);
+  std::lock_guard<std::mutex> lock(g_slot_mu);
+  if (have_id && g_slot[dev].addr && g_slot[dev].ctx_id == id) {
+    *out = g_slot[dev].addr;
+    return cudaSuccess;
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_partials);
+  if (e != cudaSuccess) return e;
+  if (!p) return cudaErrorInvalidSymbol;
+  // the lookup made the context current if it was not yet
+  if (!current_ctx_id(&id)) id = 0;
+  g_slot[dev].ctx_id = id;
+  g_slot[dev].addr = id ? p : nullptr;  // without an ID, look it up every call
+  *out = p;
+  return cudaSuccess;
+}
 
 __global__ void k_noalloc_final(const double* __restrict__ partials, int64_t nblk, int64_t cells,
                                 double* __restrict__ out) {
@@ -98,24 +157,23 @@ extern "C" int lbnr_constraint_norms_noalloc(int vset, const lbnr_grid* grid, do
       (vset == LBNR_D2Q9 && grid->nz != 1))
     return fail_na(LBNR_EINVAL, "lattice shape does not match the velocity set");
   if (!(dx > 0)) return fail_na(LBNR_EINVAL, "dx must be positive");
-  const int64_t cells = grid->nx * grid->ny * grid->nz;
-  if (grid->nx > kNoAllocMaxCells || grid->ny > kNoAllocMaxCells ||
-      grid->nz > kNoAllocMaxCells || cells > kNoAllocMaxCells)
+  // Each side first, then the product one factor at a time: every product
+  // formed is at most 2^21 * 2^21, so none can overflow.
+  const int64_t nx = grid->nx, ny = grid->ny, nz = grid->nz;
+  if (nx > kNoAllocMaxCells || ny > kNoAllocMaxCells || nz > kNoAllocMaxCells ||
+      nx * ny > kNoAllocMaxCells || nx * ny * nz > kNoAllocMaxCells)
     return fail_na(LBNR_EINVAL,
                    "lattice larger than LBNR_NOALLOC_MAX_CELLS (2^21 cells); use lbnr_constraints");
+  const int64_t cells = nx * ny * nz;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return fail_na(LBNR_ECUDA, "no usable current device");
-  if (!g_addr[dev]) {
-    // First call on this device: look up the array's device address.
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_partials);
-    if (e != cudaSuccess || !p) return fail_na(LBNR_ECUDA, cudaGetErrorString(e));
-    g_addr[dev] = p;
-  }
-  const Grid G = make_grid((int32_t)grid->nx, (int32_t)grid->ny, (int32_t)grid->nz, cells, cells);
-  double* partials = static_cast<double*>(g_addr[dev]);
+  void* addr = nullptr;
+  e = partials_address(dev, &addr);
+  if (e != cudaSuccess) return fail_na(LBNR_ECUDA, cudaGetErrorString(e));
+  const Grid G = make_grid((int32_t)nx, (int32_t)ny, (int32_t)nz, cells, cells);
+  double* partials = static_cast<double*>(addr);
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   switch (vset) {
     case LBNR_D1Q3: e = launch_norms<3>(d_fields, G, dx, partials, d_out, st); break;

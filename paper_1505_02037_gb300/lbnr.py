@@ -270,14 +270,21 @@ def lbnr_constraint_norms_noalloc(vset: int, grid: Grid, dx: float, d_fields, d_
     """Constraint norms of device-resident corrected fields without any device
     allocation (see include/lbnr.h). d_fields: CUDA float64 tensor [16, cells];
     d_out: CUDA float64 tensor [6]; stream: torch CUDA stream or None."""
+    import torch
     for t, n in ((d_fields, 16 * grid.nx * grid.ny * grid.nz), (d_out, 6)):
         if (not t.is_cuda or str(t.dtype) != "torch.float64" or not t.is_contiguous()
                 or t.numel() != n):
             raise TypeError("expected contiguous CUDA float64 tensors of the right size")
+    # the kernels run on the current device: both tensors and the stream must
+    # be on it
+    dev = d_fields.device
+    if d_out.device != dev or (stream is not None and stream.device != dev):
+        raise ValueError("d_fields, d_out and the stream must be on the same CUDA device")
     st = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
-    _check(library().lbnr_constraint_norms_noalloc(
-        int(vset), ctypes.byref(grid), float(dx), ctypes.c_void_p(d_fields.data_ptr()),
-        ctypes.c_void_p(d_out.data_ptr()), st))
+    with torch.cuda.device(dev):
+        _check(library().lbnr_constraint_norms_noalloc(
+            int(vset), ctypes.byref(grid), float(dx), ctypes.c_void_p(d_fields.data_ptr()),
+            ctypes.c_void_p(d_out.data_ptr()), st))
 
 
 def lbnr_destroy(ctx):

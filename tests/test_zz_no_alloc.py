@@ -28,7 +28,8 @@ def L():
     return lbnr
 
 
-@pytest.mark.parametrize("vset,shape", [(3, (20, 20, 20)), (2, (48, 48, 1)), (1, (300, 1, 1))])
+@pytest.mark.parametrize("vset,shape", [(3, (20, 20, 20)), (2, (48, 48, 1)), (1, (300, 1, 1)),
+                                        (3, (128, 128, 128))])
 def test_noalloc_norms_match_constraints_twice(L, vset, shape):
     import torch
     N = shape[0]
@@ -52,15 +53,22 @@ def test_noalloc_norms_match_constraints_twice(L, vset, shape):
     lat.close()
 
 
-def test_noalloc_rejects_lattices_beyond_its_array(L):
+@pytest.mark.parametrize("vset,shape", [
+    (3, (160, 160, 160)),               # 4,096,000 cells > 2^21
+    (1, (2 ** 21 + 1, 1, 1)),           # one cell past the limit along one axis
+    (3, (2 ** 21, 2 ** 21, 2 ** 21)),   # each side at the limit; the product is 2^63
+])
+def test_noalloc_rejects_lattices_beyond_its_array(L, vset, shape):
+    """Sizes past the array are refused before anything is launched (the
+    pointers given here are too small for the lattice and are never read)."""
     import ctypes
 
     import torch
-    big = L.Grid(160, 160, 160)  # 4,096,000 cells > 2^21
+    big = L.Grid(*shape)
     d = torch.empty(16, dtype=torch.float64, device="cuda")
     out = torch.empty(6, dtype=torch.float64, device="cuda")
     rc = L.library().lbnr_constraint_norms_noalloc(
-        3, ctypes.byref(big), 1 / 160, ctypes.c_void_p(d.data_ptr()),
+        vset, ctypes.byref(big), 1 / shape[0], ctypes.c_void_p(d.data_ptr()),
         ctypes.c_void_p(out.data_ptr()), None)
     assert rc == -1
     assert "LBNR_NOALLOC_MAX_CELLS" in L.library().lbnr_last_error(None).decode()
