@@ -50,6 +50,11 @@ def perturbed(f, seed=0):
     return f * (1 + rng.choice([-1.0, 1.0], size=f.shape) * 2.2e-16)
 
 
+def bar(spread):
+    """1e-12, or 4 x the oracle's own one-ulp spread where that is larger."""
+    return max(TOL64, 4 * spread)
+
+
 def with_derivatives(shape, N, A, t=0.0, direction="x"):
     return np.concatenate([W.gauge_wave(shape, 1 / N, A, t=t, direction=direction),
                            W.gauge_wave_derivatives(shape, 1 / N, A, t=t, direction=direction)]
@@ -80,12 +85,15 @@ def test_random_state_steps_fp64(L, oracle_mod, vset, shape, slicing):
     o = oracle_mod.Oracle(vset, shape, 0.8, 1 / shape[0], slicing=slicing)
     lat = L.ADLattice(vset, shape, 0.8, 1 / shape[0], slicing=slicing)
     lat.set_distributions(f0)
-    f = f0
+    f, fp = f0, perturbed(f0)
     for n in range(3):
         lat.step(1)
-        f = o.ad_step(f)
-        assert dist_err(lat.distributions(), f, 1e-2).max() < TOL64, n
-        assert field_err(lat.moments(), o.ad_moments(f), 1e-2).max() < TOL64, n
+        f, fp = o.ad_step(f), o.ad_step(fp)
+        # K and V floor: the random state's noise amplitude
+        spread_d = dist_err(fp, f, 1e-3).max()
+        spread_m = field_err(o.ad_moments(fp), o.ad_moments(f), 1e-3).max()
+        assert dist_err(lat.distributions(), f, 1e-3).max() <= bar(spread_d), n
+        assert field_err(lat.moments(), o.ad_moments(f), 1e-3).max() <= bar(spread_m), n
     lat.close()
 
 
@@ -108,10 +116,10 @@ def test_every_launch_form_gives_the_same_step(L, oracle_mod, storage):
         lat.close()
     for g in outs:
         if storage == "f64":
-            assert dist_err(g, ref, 1e-2).max() < TOL64
+            assert dist_err(g, ref, 1e-3).max() < TOL64
         else:
-            assert dist_err(g, outs[0], 1e-2).max() < 1e-5
-            assert dist_err(g, ref, 1e-2).max() < 1e-4
+            assert dist_err(g, outs[0], 1e-3).max() < 1e-5
+            assert dist_err(g, ref, 1e-3).max() < 1e-4
 
 
 @pytest.mark.parametrize("vset,shape,direction", [
