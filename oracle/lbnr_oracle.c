@@ -48,6 +48,18 @@
  *       of any constraint; with the reading it differs by exactly
  *       -(alpha/4) gamma_ij times the Hamiltonian constraint, which is how
  *       the paper describes the Einstein evolution system.
+ *   R17 Time level of the derivatives, variant LAG (deriv_mode 1): the
+ *       paper is silent on it. A_k and D_kij come from central differences
+ *       of the previous step's corrected alpha and gamma_ij (the initial
+ *       fields at the first step) instead of this step's rho~. Everything
+ *       else is R5. The state of a LAG run is the distributions plus those
+ *       7 corrected fields ("prev"), which each step returns for the next.
+ *   R18 Variant FIXED (deriv_mode 2), for measuring how much the explicit
+ *       evaluation of R5 matters: the moment rule rho = rho~ + dt S(rho)/2
+ *       taken as an equation and solved by fixed-point iteration over the
+ *       whole lattice, with A and D from the iterate's alpha and gamma, to a
+ *       relative change of 1e-15. The collision then uses S(rho), the flux
+ *       at rho and the equilibria at rho, all with those A and D.
  *   R16 Independently evolved A_k and D_kij (the original formulation the
  *       paper mentions and sets aside): with zero shift their equations
  *       follow from the definitions and the lapse and metric equations,
@@ -68,7 +80,7 @@ typedef struct {
   int32_t vset;       /* 1 = D1Q3, 2 = D2Q9, 3 = D3Q19 */
   int32_t slicing;    /* R9 */
   int32_t sources_on; /* 1 normally; 0 switches every source off (test flag) */
-  int32_t pad;
+  int32_t deriv_mode; /* 0 SYNC (R5), 1 LAG (R17), 2 FIXED (R18) */
   int64_t nx, ny, nz;
   double dx, dt, tau;
   /* Matter (Sec. "Expansion of flat universe"): a perfect fluid at rest in
@@ -494,6 +506,7 @@ static int check_params(const orc_params* p, vset_t* vs) {
   if (p->vset == 2 && p->nz != 1) return -1;
   if (!(p->tau > 0.5) || !(p->dx > 0) || !(p->dt > 0)) return -1;
   if (p->fluid_on && (!(p->t > 0) || !(p->fluid_t0 > 0))) return -1;
+  if (p->deriv_mode < 0 || p->deriv_mode > 2) return -1;
   return 0;
 }
 
@@ -590,10 +603,12 @@ static void pack_fluxes(const bm_rhs* r, const bm_state* s, double Fl[ORC_NF][3]
 }
 
 /* Steps 1-5 at one cell: given the uncorrected moments rho~ of all cells
- * (`mom`, [16][cells]), returns rho~ at this cell, the sources S~, the
- * corrected rho and the fluxes at rho. */
-static void cell_macro(const orc_params* p, const double* mom, int64_t cells, int64_t c,
-                       double rt[ORC_NF], double S[ORC_NF], double rho[ORC_NF],
+ * (`mom`, [16][cells]) and the fields the derivatives are taken from
+ * (`dsrc`: rho~ itself under R5, the previous step's corrected fields under
+ * R17; only alpha and gamma, planes 0..6, are read), returns rho~ at this
+ * cell, the sources S~, the corrected rho and the fluxes at rho. */
+static void cell_macro(const orc_params* p, const double* mom, const double* dsrc, int64_t cells,
+                       int64_t c, double rt[ORC_NF], double S[ORC_NF], double rho[ORC_NF],
                        double Fl[ORC_NF][3]) {
   double mrho, mP;
   matter_now(p, &mrho, &mP);
@@ -602,7 +617,7 @@ static void cell_macro(const orc_params* p, const double* mom, int64_t cells, in
   for (int F = 0; F < ORC_NF; ++F) rt[F] = mom[F * cells + c];
   bm_state s;
   bm_rhs r;
-  derivatives(p, mom, cells, x, y, z, s.A, s.D);
+  derivatives(p, dsrc, cells, x, y, z, s.A, s.D);
   shift_state(p, x, y, z, &s);
   unpack_fields(rt, &s);
   bm_point(&s, p->slicing, mrho, mP, &r);
@@ -615,6 +630,69 @@ static void cell_macro(const orc_params* p, const double* mom, int64_t cells, in
   unpack_fields(rho, &s);
   bm_point(&s, p->slicing, mrho, mP, &r);
   pack_fluxes(&r, &s, Fl);
+}
+
+/* Reading R18 at one cell: `rhos` ([16][cells]) holds the fixed point
+ * rho = rho~ + dt S(rho)/2 of every cell. The sources are evaluated at it,
+ * with A and D from its alpha and gamma; the corrected moments follow from
+ * the moment rule with those sources, and the fluxes are taken at them. */
+static void cell_macro_fixed(const orc_params* p, const double* mom, const double* rhos,
+                             int64_t cells, int64_t c, double rt[ORC_NF], double S[ORC_NF],
+                             double rho[ORC_NF], double Fl[ORC_NF][3]) {
+  double mrho, mP;
+  matter_now(p, &mrho, &mP);
+  int64_t x, y, z;
+  cell_coords(p, c, &x, &y, &z);
+  double v[ORC_NF];
+  for (int F = 0; F < ORC_NF; ++F) {
+    rt[F] = mom[F * cells + c];
+    v[F] = rhos[F * cells + c];
+  }
+  bm_state s;
+  bm_rhs r;
+  derivatives(p, rhos, cells, x, y, z, s.A, s.D);
+  shift_state(p, x, y, z, &s);
+  unpack_fields(v, &s);
+  bm_point(&s, p->slicing, mrho, mP, &r);
+  pack_sources(&r, S);
+  if (!p->sources_on)
+    for (int F = 0; F < ORC_NF; ++F) S[F] = 0;
+  for (int F = 0; F < ORC_NF; ++F) rho[F] = rt[F] + 0.5 * p->dt * S[F];
+  unpack_fields(rho, &s);
+  bm_point(&s, p->slicing, mrho, mP, &r);
+  pack_fluxes(&r, &s, Fl);
+}
+
+/* Reading R18 over the lattice: iterates rho <- rho~ + dt S(rho)/2 from
+ * rho = rho~, A and D from the iterate, until no value changes by more than
+ * 1e-15 of max(1, |rho|). out: [16][cells]. Returns -3 if 200 iterations do
+ * not get there, -2 on allocation failure. */
+static int fixed_point(const orc_params* p, const double* mom, int64_t cells, double* out) {
+  double* nxt = (double*)malloc(sizeof(double) * ORC_NF * cells);
+  if (!nxt) return -2;
+  memcpy(out, mom, sizeof(double) * ORC_NF * cells);
+  int rc = -3;
+  for (int it = 0; it < 200; ++it) {
+    double change = 0;
+#pragma omp parallel for schedule(static) reduction(max : change)
+    for (int64_t c = 0; c < cells; ++c) {
+      double rt[ORC_NF], S[ORC_NF], rho[ORC_NF], Fl[ORC_NF][3];
+      cell_macro_fixed(p, mom, out, cells, c, rt, S, rho, Fl);
+      for (int F = 0; F < ORC_NF; ++F) {
+        const double d = fabs(rho[F] - out[F * cells + c]) / fmax(1.0, fabs(rho[F]));
+        if (d > change) change = d;
+        nxt[F * cells + c] = rho[F];
+      }
+    }
+    memcpy(out, nxt, sizeof(double) * ORC_NF * cells);
+    if (!(change == change)) break; /* NaN */
+    if (change <= 1e-15) {
+      rc = 0;
+      break;
+    }
+  }
+  free(nxt);
+  return rc;
 }
 
 /* Equilibrium (Eqs. alfa .. ekst): w_l [rho + c_l . Flux / c_s^2]. */
@@ -668,13 +746,27 @@ int orc_init(const orc_params* p, const double* fields, double* f_out) {
   return bad ? -4 : 0;
 }
 
+/* Steps 1-5 at one cell in the context's derivative mode: `dsrc` is the
+ * previous step's corrected fields under R17, the fixed point under R18,
+ * and unused under R5. */
+static void macro_mode(const orc_params* p, const double* mom, const double* dsrc, int64_t cells,
+                       int64_t c, double rt[ORC_NF], double S[ORC_NF], double rho[ORC_NF],
+                       double Fl[ORC_NF][3]) {
+  if (p->deriv_mode == 2)
+    cell_macro_fixed(p, mom, dsrc, cells, c, rt, S, rho, Fl);
+  else
+    cell_macro(p, mom, p->deriv_mode == 1 ? dsrc : mom, cells, c, rt, S, rho, Fl);
+}
+
 /* Post-collision values f*_{F,l} at one cell (Eq. numlb right-hand side with
- * the source distributions, Eqs. alfa .. ekstsor). */
+ * the source distributions, Eqs. alfa .. ekstsor). Also returns the
+ * corrected moments (rho_out, which R17 hands to the next step). */
 static void collide_cell(const orc_params* p, const vset_t* vs, const double* f,
-                         const double* mom, int64_t cells, int64_t c,
-                         double fstar[ORC_NF][ORC_QMAX]) {
+                         const double* mom, const double* dsrc, int64_t cells, int64_t c,
+                         double fstar[ORC_NF][ORC_QMAX], double rho_out[ORC_NF]) {
   double rt[ORC_NF], S[ORC_NF], rho[ORC_NF], Fl[ORC_NF][3];
-  cell_macro(p, mom, cells, c, rt, S, rho, Fl);
+  macro_mode(p, mom, dsrc, cells, c, rt, S, rho, Fl);
+  for (int F = 0; F < ORC_NF; ++F) rho_out[F] = rho[F];
   const double src_fac = 1.0 - 1.0 / (2.0 * p->tau);
   for (int F = 0; F < ORC_NF; ++F)
     for (int l = 0; l < vs->Q; ++l) {
@@ -685,20 +777,57 @@ static void collide_cell(const orc_params* p, const vset_t* vs, const double* f,
     }
 }
 
+/* The derivative source of one step: NULL under R5, prev under R17 (which
+ * must then be given), the lattice's fixed point under R18 (allocated here;
+ * *owned tells the caller to free it). */
+static int mode_source(const orc_params* p, const double* mom, const double* prev,
+                       int64_t cells, const double** dsrc, double** owned) {
+  *dsrc = NULL;
+  *owned = NULL;
+  if (p->deriv_mode == 1) {
+    if (!prev) return -1;
+    *dsrc = prev;
+  } else if (p->deriv_mode == 2) {
+    double* fx = (double*)malloc(sizeof(double) * ORC_NF * cells);
+    if (!fx) return -2;
+    int rc = fixed_point(p, mom, cells, fx);
+    if (rc) {
+      free(fx);
+      return rc;
+    }
+    *dsrc = fx;
+    *owned = fx;
+  }
+  return 0;
+}
+
 /* One full step f(n) -> f(n+1): collide, then stream to x + c_l (periodic).
+ * prev_in / prev_out ([7][cells]: corrected alpha and gamma_ij) carry R17's
+ * lagged fields; both are ignored (and may be NULL) in the other modes.
  * Returns -4 if any output is not finite. */
-int orc_step(const orc_params* p, const double* f_in, double* f_out) {
+int orc_step_lag(const orc_params* p, const double* f_in, const double* prev_in, double* f_out,
+                 double* prev_out) {
   vset_t vs;
   if (check_params(p, &vs)) return -1;
+  if (p->deriv_mode == 1 && (!prev_in || !prev_out)) return -1;
   const int64_t cells = p->nx * p->ny * p->nz;
   double* mom = (double*)malloc(sizeof(double) * ORC_NF * cells);
   if (!mom) return -2;
   all_moments(&vs, cells, f_in, mom);
+  const double* dsrc;
+  double* owned;
+  int rc = mode_source(p, mom, prev_in, cells, &dsrc, &owned);
+  if (rc) {
+    free(mom);
+    return rc;
+  }
   int bad = 0;
 #pragma omp parallel for schedule(static) reduction(| : bad)
   for (int64_t c = 0; c < cells; ++c) {
-    double fstar[ORC_NF][ORC_QMAX];
-    collide_cell(p, &vs, f_in, mom, cells, c, fstar);
+    double fstar[ORC_NF][ORC_QMAX], rho[ORC_NF];
+    collide_cell(p, &vs, f_in, mom, dsrc, cells, c, fstar, rho);
+    if (p->deriv_mode == 1)
+      for (int F = 0; F < 7; ++F) prev_out[F * cells + c] = rho[F];
     int64_t x, y, z;
     cell_coords(p, c, &x, &y, &z);
     for (int l = 0; l < vs.Q; ++l) {
@@ -709,8 +838,15 @@ int orc_step(const orc_params* p, const double* f_in, double* f_out) {
       }
     }
   }
+  free(owned);
   free(mom);
   return bad ? -4 : 0;
+}
+
+/* One step under R5 or R18 (no lagged state). */
+int orc_step(const orc_params* p, const double* f_in, double* f_out) {
+  if (p->deriv_mode == 1) return -1;
+  return orc_step_lag(p, f_in, NULL, f_out, NULL);
 }
 
 /* n steps, alternating two caller-owned buffers; the result ends in f_io.
@@ -729,22 +865,36 @@ int orc_run(const orc_params* p, double* f_io, double* scratch, int64_t n) {
 }
 
 /* Corrected macroscopic fields rho = sum f + dt S~/2 for every cell,
- * out: [16][cells]. */
-int orc_moments(const orc_params* p, const double* f, double* out) {
+ * out: [16][cells], in the context's derivative mode (R17 reads the lagged
+ * fields prev [7][cells]; the other modes ignore it). */
+int orc_moments_lag(const orc_params* p, const double* f, const double* prev, double* out) {
   vset_t vs;
   if (check_params(p, &vs)) return -1;
   const int64_t cells = p->nx * p->ny * p->nz;
   double* mom = (double*)malloc(sizeof(double) * ORC_NF * cells);
   if (!mom) return -2;
   all_moments(&vs, cells, f, mom);
+  const double* dsrc;
+  double* owned;
+  int rc = mode_source(p, mom, prev, cells, &dsrc, &owned);
+  if (rc) {
+    free(mom);
+    return rc;
+  }
 #pragma omp parallel for schedule(static)
   for (int64_t c = 0; c < cells; ++c) {
     double rt[ORC_NF], S[ORC_NF], rho[ORC_NF], Fl[ORC_NF][3];
-    cell_macro(p, mom, cells, c, rt, S, rho, Fl);
+    macro_mode(p, mom, dsrc, cells, c, rt, S, rho, Fl);
     for (int F = 0; F < ORC_NF; ++F) out[F * cells + c] = rho[F];
   }
+  free(owned);
   free(mom);
   return 0;
+}
+
+int orc_moments(const orc_params* p, const double* f, double* out) {
+  if (p->deriv_mode == 1) return -1;
+  return orc_moments_lag(p, f, NULL, out);
 }
 
 /* One step evaluated only at the listed destination cells: out[n][16][Q] is
@@ -754,6 +904,7 @@ int orc_step_cells(const orc_params* p, const double* f_in, int64_t n, const int
                    double* out) {
   vset_t vs;
   if (check_params(p, &vs)) return -1;
+  if (p->deriv_mode != 0) return -1; /* reading R5 only */
   double mrho, mP;
   matter_now(p, &mrho, &mP);
   const int64_t cells = p->nx * p->ny * p->nz;
@@ -947,7 +1098,7 @@ int orc_constraint_fields(const orc_params* p, const double* rho, double* out_ce
  * out[22] = H_L2, H_inf, M_L2, M_inf, C_L2, C_inf, sum_x rho~_F (F = 0..15),
  * where X_L2 = sqrt(mean over cells of the squared (vector) norm) and
  * X_inf = max over cells and components of |X|. */
-int orc_constraints(const orc_params* p, const double* f, double* out) {
+int orc_constraints_lag(const orc_params* p, const double* f, const double* prev, double* out) {
   vset_t vs;
   if (check_params(p, &vs)) return -1;
   const int64_t cells = p->nx * p->ny * p->nz;
@@ -958,7 +1109,12 @@ int orc_constraints(const orc_params* p, const double* f, double* out) {
     free(cf);
     return -2;
   }
-  orc_moments(p, f, rho);
+  const int rc = orc_moments_lag(p, f, prev, rho);
+  if (rc) {
+    free(rho);
+    free(cf);
+    return rc;
+  }
   orc_constraint_fields(p, rho, cf);
   double h2 = 0, hi = 0, m2 = 0, mi = 0, c2 = 0, ci = 0;
   for (int64_t c = 0; c < cells; ++c) {
@@ -987,6 +1143,11 @@ int orc_constraints(const orc_params* p, const double* f, double* out) {
   free(rho);
   free(cf);
   return 0;
+}
+
+int orc_constraints(const orc_params* p, const double* f, double* out) {
+  if (p->deriv_mode == 1) return -1;
+  return orc_constraints_lag(p, f, NULL, out);
 }
 
 /* ------------------------------------------------------------------------ */

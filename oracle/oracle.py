@@ -38,7 +38,7 @@ class Params(ctypes.Structure):
         ("vset", ctypes.c_int32),
         ("slicing", ctypes.c_int32),
         ("sources_on", ctypes.c_int32),
-        ("pad", ctypes.c_int32),
+        ("deriv_mode", ctypes.c_int32),
         ("nx", ctypes.c_int64),
         ("ny", ctypes.c_int64),
         ("nz", ctypes.c_int64),
@@ -100,6 +100,12 @@ def lib():
             L.orc_constraint_fields.restype = ctypes.c_int
             L.orc_constraints.argtypes = [pp, dp, dp]
             L.orc_constraints.restype = ctypes.c_int
+            L.orc_step_lag.argtypes = [pp, dp, dp, dp, dp]
+            L.orc_step_lag.restype = ctypes.c_int
+            L.orc_moments_lag.argtypes = [pp, dp, dp, dp]
+            L.orc_moments_lag.restype = ctypes.c_int
+            L.orc_constraints_lag.argtypes = [pp, dp, dp, dp]
+            L.orc_constraints_lag.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -157,17 +163,23 @@ class Oracle:
     shift = (bx, by, bz): a constant, uniform shift beta^i (Sec. "Bona-Masso
     evolution equations" with B = 0); default zero. shift_field: a static
     shift field beta^i(x), [3][nz][ny][nx] (or [3][cells]), added to shift;
-    its B_k^i = d_k beta^i / 2 come from central differences."""
+    its B_k^i = d_k beta^i / 2 come from central differences.
+
+    deriv_mode: the time level of A_k and D_kij (the paper is silent): 0 SYNC,
+    this step's rho~ (reading R5); 1 LAG, the previous step's corrected alpha
+    and gamma (R17: the state is then (f, prev), prev [7][cells], see
+    lag_init / step_lag); 2 FIXED, the moment rule solved as an equation by
+    fixed-point iteration (R18)."""
 
     def __init__(self, vset, shape, tau, dx, dt=None, slicing=1, sources_on=True, fluid=None,
-                 shift=None, shift_field=None):
+                 shift=None, shift_field=None, deriv_mode=0):
         nx, ny, nz = shape
         self.vset = int(vset)
         self.Q = Q_OF[self.vset]
         self.shape = (int(nx), int(ny), int(nz))
         self.cells = nx * ny * nz
-        self.p = Params(self.vset, int(slicing), int(bool(sources_on)), 0, nx, ny, nz,
-                        float(dx), float(dx if dt is None else dt), float(tau))
+        self.p = Params(self.vset, int(slicing), int(bool(sources_on)), int(deriv_mode), nx, ny,
+                        nz, float(dx), float(dx if dt is None else dt), float(tau))
         self.t0 = 1.0
         if fluid is not None:
             rho0, w, t0 = fluid
@@ -217,6 +229,48 @@ class Oracle:
         f = np.ascontiguousarray(f, dtype=np.float64)
         out = np.zeros((NF, self.cells))
         _check(lib().orc_moments(ctypes.byref(self.p), _dp(f), _dp(out)), "moments")
+        return out
+
+    # --- lagged derivatives (deriv_mode 1, reading R17) ----------------------
+    def lag_init(self, fields: np.ndarray, t=None):
+        """(f, prev): the initial distributions (as init) and the lagged fields
+        of the first step, the initial alpha and gamma [7][cells]."""
+        fields = np.ascontiguousarray(fields, dtype=np.float64).reshape(NF, self.cells)
+        return self.init(fields, t), np.ascontiguousarray(fields[:7].copy())
+
+    def step_lag(self, f: np.ndarray, prev: np.ndarray, t=None):
+        """One step from (f, prev); returns the next (f, prev)."""
+        self._at(t)
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        prev = np.ascontiguousarray(prev, dtype=np.float64).reshape(7, self.cells)
+        out = np.zeros(self._f_shape())
+        pout = np.zeros((7, self.cells))
+        _check(lib().orc_step_lag(ctypes.byref(self.p), _dp(f), _dp(prev), _dp(out), _dp(pout)),
+               "step_lag")
+        return out, pout
+
+    def run_lag(self, f: np.ndarray, prev: np.ndarray, n: int, t=None):
+        """n steps from (f, prev); the state's time advances by dt per step."""
+        t0 = self.t0 if t is None else float(t)
+        for i in range(int(n)):
+            f, prev = self.step_lag(f, prev, t0 + i * self.p.dt)
+        return f, prev
+
+    def moments_lag(self, f: np.ndarray, prev: np.ndarray, t=None) -> np.ndarray:
+        self._at(t)
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        prev = np.ascontiguousarray(prev, dtype=np.float64).reshape(7, self.cells)
+        out = np.zeros((NF, self.cells))
+        _check(lib().orc_moments_lag(ctypes.byref(self.p), _dp(f), _dp(prev), _dp(out)),
+               "moments_lag")
+        return out
+
+    def constraints_lag(self, f: np.ndarray, prev: np.ndarray) -> np.ndarray:
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        prev = np.ascontiguousarray(prev, dtype=np.float64).reshape(7, self.cells)
+        out = np.zeros(22)
+        _check(lib().orc_constraints_lag(ctypes.byref(self.p), _dp(f), _dp(prev), _dp(out)),
+               "constraints_lag")
         return out
 
     def step_cells(self, f: np.ndarray, cells, t=None) -> np.ndarray:
