@@ -24,7 +24,6 @@ scaling is weak and value = units of all ranks / max time over ranks.
 from __future__ import annotations
 
 import argparse
-import hashlib
 import json
 import math
 import os
@@ -109,6 +108,8 @@ def parse():
     p.add_argument("--profile-steps", type=int, default=20)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-modes", action="store_true",
+                   help="skip the same-run LAG record and the one-crossing precision records")
     p.add_argument("--variant", default=None,
                    help="collide launch form by name (default: the autotuner's choice)")
     a = p.parse_args()
@@ -193,51 +194,37 @@ class ClockSampler:
                 "samples": len(self.samples)}
 
 
-# Sources the collide-and-stream kernels of the 3D lattice are built from.
-COLLIDE_SOURCES = ("collide_tma.cuh", "dispatch.h", "instantiate.cuh", "kernels.cuh",
-                   "lattice.cuh", "physics.cuh", "inst_q19_s0.cu", "inst_q19_s1.cu",
-                   "inst_q19_s2.cu", "inst_q19_s3.cu", "inst_q19_s4.cu")
+from paper_1505_02037_gb300.traffic_table import (  # noqa: E402
+    AD_SOURCES, COLLIDE_SOURCES, source_hash)
 
 
-# Sources the 37-field collide kernel is built from.
-AD_SOURCES = ("ad.cuh", "ad_q19_f32.cu", "dispatch.h", "kernels.cuh", "lattice.cuh",
-              "physics.cuh")
-
-
-def source_hash(files=COLLIDE_SOURCES):
-    h = hashlib.sha256()
-    d = os.path.join(ROOT, "paper_1505_02037_gb300", "csrc")
-    for n in sorted(files):
-        with open(os.path.join(d, n), "rb") as f:
-            h.update(n.encode() + f.read())
-    return h.hexdigest()[:16]
-
-
-def profile_entry(kernel_key, field):
-    """A per-cell figure from the committed ncu summaries, if it was taken on
-    the current kernel sources (else None)."""
+def _traffic_entry(kernel_key, files):
+    """The traffic table's entry for kernel_key if it was written by the
+    capture script for the current kernel sources (else None): an entry whose
+    hash differs, or that carries a hand-written note instead of a capture
+    hash, is not trusted."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             e = json.load(f).get(kernel_key)
     except OSError:
         return None
-    if not e or e.get("source_hash") != source_hash():
+    if not e or "sources_note" in e or e.get("source_hash") != source_hash(files):
         return None
-    return e.get(field)
+    return e
+
+
+def profile_entry(kernel_key, field):
+    """A per-cell figure from the committed ncu summaries, if it was taken on
+    the current kernel sources (else None)."""
+    e = _traffic_entry(kernel_key, COLLIDE_SOURCES)
+    return None if e is None else e.get(field)
 
 
 def traffic_for(kernel_key, cells, files=COLLIDE_SOURCES):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel sources (else None)."""
-    try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            t = json.load(f)
-    except OSError:
-        return None
-    e = t.get(kernel_key)
-    if not e or e.get("source_hash") != source_hash(files):
-        return None
-    return e["dram_bytes_per_cell"] * cells
+    e = _traffic_entry(kernel_key, files)
+    return None if e is None else e["dram_bytes_per_cell"] * cells
 
 
 def cpu_baseline(vset, storage, direction, A, tau, wave="gauge", seconds=12.0, beta=None,
@@ -673,6 +660,94 @@ def main_batched(args):
         dist.destroy_process_group()
 
 
+def timed_steps(lat, n):
+    """Milliseconds of n steps of lat (graph launches) by CUDA events on the
+    lattice's stream, synchronised on both sides."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(lat.stream)
+    lat.step(n)
+    e1.record(lat.stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def deriv_mode_records(args, line, fields, sync_ms, sync_col_ms, sync_aux_ms, vset, N, storage,
+                       wave, streaming):
+    """The same workload in the LAG derivative mode (reading R17): the collide
+    kernel writes the next step's stencil planes itself, so a step is one
+    kernel. Timed like the main run (same steps after the same warm-up)."""
+    from paper_1505_02037_gb300 import autotune, lbnr
+    lat = lbnr.Lattice(vset, (N, N, N), args.tau, 1 / N, storage=storage,
+                       slicing=lbnr.LBNR_GEODESIC if wave == "linear" else lbnr.LBNR_HARMONIC,
+                       streaming={"auto": lbnr.LBNR_STREAM_AUTO, "aa": lbnr.LBNR_STREAM_AA}[streaming],
+                       deriv_mode="lag")
+    lat.init(fields)
+    tuning = autotune.tune(lat)
+    lat.step(args.warmup)
+    ms = timed_steps(lat, args.steps) / args.steps
+    _, col = lat.step_timed(args.profile_steps)
+    col /= args.profile_steps
+    cells = N ** 3
+    s = BYTES[storage]
+    cb = 8 if storage == "f64" else 4
+    alg = cells * (2 * 16 * 19 * s + 14 * cb)  # f in + f out + lagged planes read and written
+    peak = line["roofline"].get("peak") if line["roofline"]["bound"] == "hbm" else \
+        line["roofline"]["hbm"]["peak"]
+    out = {
+        "sync": {"ms_per_step": sync_ms, "value": cells * 16 / (sync_ms * 1e-3) / 1e6,
+                 "kernels_per_step": 2, "k_aux_ms": sync_aux_ms, "k_collide_ms": sync_col_ms},
+        "lag": {"ms_per_step": ms, "value": cells * 16 / (ms * 1e-3) / 1e6, "kernels_per_step": 1,
+                "k_collide_ms": col, "launch_form": lat.variants[lat.variant],
+                "collide_hbm_frac": alg / (col * 1e-3) / 1e9 / peak,
+                "algorithmic_bytes_per_cell": alg / cells,
+                "autotune_ms_per_collide": tuning},
+        "note": "LAG takes A and D from the previous step's corrected alpha and gamma (the paper "
+                "is silent on the time level); both are first order",
+    }
+    lat.close()
+    return out
+
+
+def precision_records(args, N, device_index):
+    """FP64 against FP32 storage against FP32 deviation storage on the same
+    GPU in the same run: the x-aligned gauge wave with A = 0.01 on N^3 over one
+    crossing time (N steps) at tau = args.tau; for each, throughput and the
+    error against the closed-form solution at t = 1 (max over fields and cells,
+    relative to A), and the reduced forms' distance from the FP64 run."""
+    from paper_1505_02037_gb300 import autotune, lbnr
+    A, steps, cells = 0.01, N, N ** 3
+    fields = W.gauge_wave((N, N, N), 1 / N, A).reshape(16, cells)
+    exact = W.gauge_wave((N, 1, 1), 1 / N, A, t=steps / N).reshape(16, 1, N)
+    out, ref = {}, None
+    for storage in ("f64", "f32", "dev_f32"):
+        lat = lbnr.Lattice(3, (N, N, N), args.tau, 1 / N, storage=storage)
+        lat.init(fields)
+        autotune.tune(lat)
+        lat.init(fields)
+        ms = timed_steps(lat, steps)
+        finite = True
+        try:
+            m = lat.moments().reshape(16, N * N, N)
+        except lbnr.NonFiniteError:
+            finite, m = False, None
+        rec = {"value": cells * 16 * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps,
+               "launch_form": lat.variants[lat.variant], "finite": finite}
+        if finite:
+            rec["err_vs_analytic"] = float(np.abs(m - exact).max() / A)
+            if ref is None:
+                ref = m
+            else:
+                rec["err_vs_fp64"] = float(np.abs(m - ref).max() / A)
+        lat.close()
+        out[storage] = rec
+    out["speedup_vs_fp64"] = {k: out[k]["value"] / out["f64"]["value"] for k in ("f32", "dev_f32")}
+    out["workload"] = (f"3D gauge wave along x, D3Q19 {N}^3, A={A}, tau={args.tau}, "
+                       f"{steps} steps (one crossing time), ping-pong; errors relative to A")
+    return out
+
+
 def main():
     args = parse()
     if args.workload == "batched":
@@ -778,14 +853,16 @@ def main():
     roofline = hbm_roofline
     flops = profile_entry(tkey, "fp64_flops_per_cell") if storage == "f64" else None
     if flops is not None:
-        # FP64 is bound by the FP64 pipes: 152 SMs x 2 FP64 FMA per clock x
-        # 2 flops x 2.07 GHz = 1.26 TFLOP/s nominal
-        fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12
+        # FP64 is bound by the FP64 pipe: its peak is the rate a register
+        # FMA-chain kernel sustains on this GPU, measured here
+        fp64_peak = lbnr.lbnr_fp64_fma_rate(lat.stream)
         ach = flops * cells / (col_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "kernel": "k_collide (fused collide-and-stream, FP64)",
                     "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
-                    "peak_source": "FP64 units x clock (nominal)", "flops_per_cell": flops,
-                    "avg_launch_ms": col_ms, "traffic": traffic, "hbm": hbm_roofline}
+                    "peak_source": "measured in this run: FP64 FMA chains at full occupancy "
+                                   "(lbnr_fp64_fma_rate)",
+                    "flops_per_cell": flops, "avg_launch_ms": col_ms, "traffic": traffic,
+                    "hbm": hbm_roofline}
 
     value = units_all / (ms_max * 1e-3) / 1e6
     line = {
@@ -831,6 +908,14 @@ def main():
                        "h2d_bytes_per_step": hf.numel() * 8 / k,
                        "d2h_bytes_per_step": hout.numel() * 8 / k,
                        "steps_per_transfer": k}
+
+    if not args.no_modes and not beta and len(WORKLOADS[args.workload]) <= 8:
+        lat.close()
+        del lat
+        line["deriv_modes"] = deriv_mode_records(args, line, fields, ms_max / args.steps, col_ms,
+                                                 aux_ms, vset, N, storage, wave, streaming)
+        if storage in ("f32", "dev_f32") and wave == "gauge" and direction == "x":
+            line["precision_one_crossing"] = precision_records(args, N, local)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(

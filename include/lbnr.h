@@ -56,6 +56,16 @@ enum { LBNR_GEODESIC = 0, LBNR_HARMONIC = 1, LBNR_ONE_PLUS_LOG = 2 };
  * memory, else the in-place AA pattern (one copy). */
 enum { LBNR_STREAM_AUTO = 0, LBNR_STREAM_PINGPONG = 1, LBNR_STREAM_AA = 2 };
 
+/* Time level of A_k and D_kij, on which the paper is silent (Sec. "Lattice
+ * Boltzmann Model", moment rule; Sec. "Bona-Masso evolution equations",
+ * first-order derivatives). SYNC: central differences of this step's zeroth
+ * moments of alpha and gamma (a moment pass over their 7 Q planes, then the
+ * collide kernel). LAG: central differences of the previous step's
+ * corrected alpha and gamma (the initial fields at the first step), which
+ * the collide kernel itself writes for the next step: one kernel per step.
+ * Both are first order in dt; they differ by O(dt) per step. */
+enum { LBNR_DERIV_SYNC = 0, LBNR_DERIV_LAG = 1 };
+
 enum {
   LBNR_OK = 0,
   LBNR_EINVAL = -1,     /* bad argument: sizes, tau <= 1/2, dt != dx, NULL */
@@ -80,9 +90,11 @@ typedef struct {
                          (>= lbnr_workspace_bytes); it must outlive the
                          context. NULL: the library allocates its own. */
   uint64_t dev_bytes;
+  int32_t deriv_mode; /* LBNR_DERIV_SYNC (default) or LBNR_DERIV_LAG */
+  int32_t reserved;   /* 0 */
 } lbnr_opts;
 
-/* Fills o with the defaults: harmonic slicing, F64, AUTO, sources on. */
+/* Fills o with the defaults: harmonic slicing, F64, AUTO, sources on, SYNC. */
 void lbnr_default_opts(lbnr_opts* o);
 
 /* Device bytes a context needs for this grid, set and options (the
@@ -108,12 +120,14 @@ int lbnr_step(lbnr_ctx* ctx, int64_t n);
 /* Same work as lbnr_step(n), launched one kernel at a time with CUDA events
  * recorded around every launch on the context's stream; synchronises and
  * adds the elapsed milliseconds per kernel kind into ms_out[2]
- * (ms_out[0]: the moment pass feeding the derivative stencil, ms_out[1]: the
- * fused collide-and-stream kernel). For measurement. */
+ * (ms_out[0]: the moment pass feeding the derivative stencil, which LAG does
+ * not run, ms_out[1]: the fused collide-and-stream kernel). For
+ * measurement. */
 int lbnr_step_timed(lbnr_ctx* ctx, int64_t n, double* ms_out);
 
 /* Corrected macroscopic fields rho = sum_l f_l + dt S/2 (Sec. LBM), evaluated
- * in FP64 from the stored distributions, into host out[16][cells]. */
+ * in FP64 from the stored distributions, into host out[16][cells]. Under
+ * LAG the sources take A and D from the lagged fields, as the step does. */
 int lbnr_moments(lbnr_ctx* ctx, double* out);
 
 /* Constraint monitor, FP64 on the device, into host out[22]:
@@ -140,6 +154,21 @@ int lbnr_get_cells(lbnr_ctx* ctx, int64_t n, const int64_t* cells, double* out);
  * storage type). With lbnr_get_distributions this gives checkpoint/resume.
  * Keeps the step count. */
 int lbnr_set_distributions(lbnr_ctx* ctx, const double* in);
+
+/* LAG only: the lagged fields the next step differentiates, the corrected
+ * alpha and gamma_ij of the previous step (the initial fields before the
+ * first step), host out[7][cells] FP64 (decoded from the stencil planes: ln
+ * alpha and gamma, in the compute type). With lbnr_get_distributions this is
+ * a LAG run's whole state. LBNR_ESTATE under SYNC or before init. */
+int lbnr_get_lagged(lbnr_ctx* ctx, double* out);
+
+/* LAG only: replaces the lagged fields with host in[7][cells] (alpha > 0,
+ * gamma_ij), for checkpoint/resume with lbnr_set_distributions. LBNR_ESTATE
+ * under SYNC, LBNR_EINVAL for a non-positive or non-finite lapse. */
+int lbnr_set_lagged(lbnr_ctx* ctx, const double* in);
+
+/* The context's LBNR_DERIV_* mode (-1 for NULL). */
+int lbnr_deriv_mode(const lbnr_ctx* ctx);
 
 /* Synchronises and returns LBNR_ENONFINITE if any step so far produced a
  * non-finite moment, else LBNR_OK. */
@@ -187,7 +216,12 @@ int lbnr_set_shift_field(lbnr_ctx* ctx, const double* beta);
 
 /* Thread-to-cell layouts of the collide kernel available for this context's
  * set and storage (all give the same results): their number, a short name,
- * and the selection (default 0). Used by the autotuner. */
+ * and the selection (default 0). Used by the autotuner. Names: "P<n>-hold" /
+ * "P<n>-reread" (n threads per cell; distributions held in registers or read
+ * again), "tma-p<n>-nc<c>-k<k>-t<t>" (persistent, tensor-copy fed, c
+ * consumer warps). The forms fed by tensor copies read each tile's own cells
+ * only; at the odd step of the in-place pattern a register form runs in
+ * their place. */
 int lbnr_num_variants(const lbnr_ctx* ctx);
 const char* lbnr_variant_name(const lbnr_ctx* ctx, int variant);
 int lbnr_set_variant(lbnr_ctx* ctx, int variant);
@@ -197,6 +231,15 @@ int lbnr_set_variant(lbnr_ctx* ctx, int variant);
 int64_t lbnr_steps_done(const lbnr_ctx* ctx);
 int lbnr_q(const lbnr_ctx* ctx);
 int lbnr_streaming(const lbnr_ctx* ctx);
+
+/* The FP64 fused multiply-add rate the current device sustains, measured
+ * on the given stream (cudaStream_t, NULL = default) by a kernel of
+ * independent register-resident FMA chains at full occupancy, best of three
+ * timed launches after one warm-up; *tflops in TFLOP/s (2 flops per FMA).
+ * The FP64 lattice Boltzmann step is bound by that pipe, not by HBM, and its
+ * roofline is quoted against this figure. Synchronises the stream. Errors:
+ * LBNR_EINVAL (NULL output), LBNR_ECUDA; message in lbnr_last_error(NULL). */
+int lbnr_fp64_fma_rate(void* cuda_stream, double* tflops);
 
 /* Largest lattice lbnr_constraint_norms_noalloc accepts. */
 #define LBNR_NOALLOC_MAX_CELLS 2097152

@@ -16,7 +16,7 @@ def tune(lat, steps_per_trial: int = 4, trials: int = 2, verbose: bool = False) 
     """Chooses the fastest launch form for `lat` (a lbnr.Lattice that has
     been initialised). The trial steps advance the simulation like any other
     steps. Returns {name: ms per collide launch}."""
-    key = (lat.vset, lat.storage, lat.streaming, lat.shape)
+    key = (lat.vset, lat.storage, lat.streaming, lat.shape, lat.deriv_mode)
     names = lat.variants
     if key in _cache:
         lat.set_variant(_cache[key])

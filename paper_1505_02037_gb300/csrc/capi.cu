@@ -96,6 +96,10 @@ struct lbnr_ctx {
   bool own_mem = false;
   uint64_t bytes = 0;
   void* f[2] = {nullptr, nullptr};
+  // LAG (reading R17): stencil planes of the current step ([steps & 1]) and
+  // of the next, which the collide kernel writes; under R5 only [0] is used
+  // and k_aux refills it every step.
+  void* aux[2] = {nullptr, nullptr};
   LaunchCtx L;
   bool initialised = false;
   int64_t steps = 0;
@@ -141,7 +145,7 @@ static int fail(lbnr_ctx* c, int code, const char* fmt, ...) {
 namespace {
 
 struct Layout {
-  uint64_t f0, f1, aux, macro, aux64, partials, out22, flag, stage, total;
+  uint64_t f0, f1, aux, aux2, macro, aux64, partials, out22, flag, stage, total;
 };
 
 uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
@@ -167,10 +171,12 @@ int validate(const lbnr_grid* g, int vset, const lbnr_opts* o) {
   if (o->slicing < 0 || o->slicing > 2) return fail(nullptr, LBNR_EINVAL, "unknown slicing %d", o->slicing);
   if (o->streaming < 0 || o->streaming > 2)
     return fail(nullptr, LBNR_EINVAL, "unknown streaming %d", o->streaming);
+  if (o->deriv_mode != LBNR_DERIV_SYNC && o->deriv_mode != LBNR_DERIV_LAG)
+    return fail(nullptr, LBNR_EINVAL, "unknown derivative mode %d", o->deriv_mode);
   return LBNR_OK;
 }
 
-Layout layout_for(const lbnr_grid* g, int vset, int storage, int streaming) {
+Layout layout_for(const lbnr_grid* g, int vset, int storage, int streaming, int deriv_mode) {
   const int Q = q_of(vset);
   const uint64_t cells = (uint64_t)g->nx * g->ny * g->nz;
   const uint64_t ps = (cells + kTile - 1) / kTile * kTile;
@@ -185,6 +191,8 @@ Layout layout_for(const lbnr_grid* g, int vset, int storage, int streaming) {
   if (streaming == LBNR_STREAM_PINGPONG) off += fbytes;
   L.aux = off;
   off += align256(7 * cells * cb);
+  L.aux2 = off;
+  if (deriv_mode == LBNR_DERIV_LAG) off += align256(7 * cells * cb);
   L.macro = off;
   off += align256(16 * cells * 8);
   L.aux64 = off;
@@ -209,6 +217,20 @@ void* state_now(const lbnr_ctx* c) {
   return c->streaming == LBNR_STREAM_PINGPONG ? c->f[c->steps & 1] : c->f[0];
 }
 
+bool lagged(const lbnr_ctx* c) { return c->opts.deriv_mode == LBNR_DERIV_LAG; }
+
+// The launch context of the step that starts from step count `parity`: under
+// LAG the collide kernel reads the stencil planes of that step and writes
+// those of the next (no moment pass).
+LaunchCtx step_ctx(const lbnr_ctx* c, int64_t parity) {
+  LaunchCtx L = c->L;
+  if (lagged(c)) {
+    L.aux = c->aux[parity & 1];
+    L.aux_out = c->aux[(parity + 1) & 1];
+  }
+  return L;
+}
+
 // Enqueues one step starting from step parity `parity`.
 cudaError_t enqueue_step(lbnr_ctx* c, int64_t parity) {
   int layout;
@@ -221,9 +243,11 @@ cudaError_t enqueue_step(lbnr_ctx* c, int64_t parity) {
     layout = (parity & 1) ? 2 : 1;
     fin = fout = c->f[0];
   }
-  cudaError_t e = c->ops->aux(c->L, layout, fin);
+  const LaunchCtx L = step_ctx(c, parity);
+  cudaError_t e = cudaSuccess;
+  if (!lagged(c)) e = c->ops->aux(L, layout, fin);
   if (e != cudaSuccess) return e;
-  e = c->ops->step(c->L, layout, c->variant, fin, fout);
+  e = c->ops->step(L, layout, c->variant, fin, fout);
   if (e == cudaSuccess && c->L.clock) {
     k_tick<<<1, 1, 0, c->st>>>(const_cast<int64_t*>(c->L.clock));
     e = cudaGetLastError();
@@ -290,7 +314,7 @@ int lbnr_workspace_bytes(const lbnr_grid* grid, int vset, const lbnr_opts* opts,
   if (!out) return fail(nullptr, LBNR_EINVAL, "null output");
   if (opts->streaming == LBNR_STREAM_AUTO)
     return fail(nullptr, LBNR_EINVAL, "workspace size needs a fixed streaming pattern");
-  *out = layout_for(grid, vset, opts->storage, opts->streaming).total;
+  *out = layout_for(grid, vset, opts->storage, opts->streaming, opts->deriv_mode).total;
   return LBNR_OK;
 }
 
@@ -320,8 +344,8 @@ int lbnr_create(const lbnr_grid* grid, int vset, double tau, double dx, double d
   // streaming pattern
   int streaming = opts->streaming;
   lbnr_grid g = *grid;
-  const uint64_t need_pp = layout_for(&g, vset, opts->storage, LBNR_STREAM_PINGPONG).total;
-  const uint64_t need_aa = layout_for(&g, vset, opts->storage, LBNR_STREAM_AA).total;
+  const uint64_t need_pp =
+      layout_for(&g, vset, opts->storage, LBNR_STREAM_PINGPONG, opts->deriv_mode).total;
   if (streaming == LBNR_STREAM_AUTO) {
     if (opts->dev_buffer) {
       streaming = opts->dev_bytes >= need_pp ? LBNR_STREAM_PINGPONG : LBNR_STREAM_AA;
@@ -336,7 +360,7 @@ int lbnr_create(const lbnr_grid* grid, int vset, double tau, double dx, double d
     }
   }
   c->streaming = streaming;
-  const Layout Ly = layout_for(&g, vset, opts->storage, streaming);
+  const Layout Ly = layout_for(&g, vset, opts->storage, streaming, opts->deriv_mode);
   c->bytes = Ly.total;
   if (opts->dev_buffer) {
     if (opts->dev_bytes < Ly.total) {
@@ -383,6 +407,9 @@ int lbnr_create(const lbnr_grid* grid, int vset, double tau, double dx, double d
   L.slicing = opts->slicing;
   L.sources_on = opts->sources_on ? 1 : 0;
   L.aux = b + Ly.aux;
+  L.aux_out = nullptr;
+  c->aux[0] = b + Ly.aux;
+  c->aux[1] = opts->deriv_mode == LBNR_DERIV_LAG ? b + Ly.aux2 : nullptr;
   L.macro = reinterpret_cast<double*>(b + Ly.macro);
   L.aux64 = reinterpret_cast<double*>(b + Ly.aux64);
   L.partials = reinterpret_cast<double*>(b + Ly.partials);
@@ -415,6 +442,8 @@ int lbnr_init(lbnr_ctx* c, const double* fields) {
   if (c->L.clock)
     CUDA_TRY(c, cudaMemsetAsync(const_cast<int64_t*>(c->L.clock), 0, sizeof(int64_t), c->st));
   CUDA_TRY(c, c->ops->init(c->L, c->f[0]));
+  // LAG: the first step's derivatives come from the initial fields
+  if (lagged(c)) CUDA_TRY(c, c->ops->lag_from64(c->L, c->aux[0]));
   // the host array may be released as soon as we return
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
   c->steps = 0;
@@ -472,10 +501,11 @@ int lbnr_step_timed(lbnr_ctx* c, int64_t n, double* ms_out) {
       layout = (parity & 1) ? 2 : 1;
       fin = fout = c->f[0];
     }
+    const LaunchCtx L = step_ctx(c, parity);
     cudaError_t e = cudaEventRecord(ev[0], c->st);
-    if (e == cudaSuccess) e = c->ops->aux(c->L, layout, fin);
+    if (e == cudaSuccess && !lagged(c)) e = c->ops->aux(L, layout, fin);
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->st);
-    if (e == cudaSuccess) e = c->ops->step(c->L, layout, c->variant, fin, fout);
+    if (e == cudaSuccess) e = c->ops->step(L, layout, c->variant, fin, fout);
     if (e == cudaSuccess) e = cudaEventRecord(ev[2], c->st);
     if (e == cudaSuccess && c->L.clock) {
       k_tick<<<1, 1, 0, c->st>>>(const_cast<int64_t*>(c->L.clock));
@@ -505,6 +535,7 @@ int lbnr_moments(lbnr_ctx* c, double* out) {
   int64_t nb = 0;
   c->L.fluid_P_now = fluid_pressure_now(c);
   CUDA_TRY(c, c->ops->sum64(c->L, layout_now(c), state_now(c), &nb));
+  if (lagged(c)) CUDA_TRY(c, c->ops->lag_to64(c->L, c->aux[c->steps & 1], nullptr));
   CUDA_TRY(c, c->ops->correct64(c->L));
   CUDA_TRY(c, cudaMemcpyAsync(out, c->L.macro, sizeof(double) * 16 * (size_t)c->L.cells,
                               cudaMemcpyDeviceToHost, c->st));
@@ -520,6 +551,7 @@ int lbnr_constraints(lbnr_ctx* c, double* out) {
   int64_t nbs = 0, nbc = 0;
   c->L.fluid_P_now = fluid_pressure_now(c);
   CUDA_TRY(c, c->ops->sum64(c->L, layout_now(c), state_now(c), &nbs));
+  if (lagged(c)) CUDA_TRY(c, c->ops->lag_to64(c->L, c->aux[c->steps & 1], nullptr));
   CUDA_TRY(c, c->ops->correct64(c->L));
   CUDA_TRY(c, c->ops->constraints64(c->L, &nbc));
   CUDA_TRY(c, reduce_final(c->L.partials, nbc, nbs, c->L.cells, c->L.out22, c->st));
@@ -581,6 +613,33 @@ int lbnr_set_distributions(lbnr_ctx* c, const double* in) {
   c->initialised = true;
   return LBNR_OK;
 }
+
+int lbnr_get_lagged(lbnr_ctx* c, double* out) {
+  if (!c || !out) return fail(c, LBNR_EINVAL, "null argument");
+  if (!lagged(c)) return fail(c, LBNR_ESTATE, "the context does not use lagged derivatives");
+  if (!c->initialised) return fail(c, LBNR_ESTATE, "no state before init");
+  // decoded into the FP64 field planes (alpha, gamma) on the device, then copied
+  double* d = c->L.macro;
+  CUDA_TRY(c, c->ops->lag_to64(c->L, c->aux[c->steps & 1], d));
+  CUDA_TRY(c, cudaMemcpyAsync(out, d, sizeof(double) * 7 * (size_t)c->L.cells,
+                              cudaMemcpyDeviceToHost, c->st));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return LBNR_OK;
+}
+
+int lbnr_set_lagged(lbnr_ctx* c, const double* in) {
+  if (!c || !in) return fail(c, LBNR_EINVAL, "null argument");
+  if (!lagged(c)) return fail(c, LBNR_ESTATE, "the context does not use lagged derivatives");
+  for (int64_t i = 0; i < c->L.cells; ++i)
+    if (!(in[i] > 0) || !std::isfinite(in[i])) return fail(c, LBNR_EINVAL, "lapse must be positive");
+  CUDA_TRY(c, cudaMemcpyAsync(c->L.macro, in, sizeof(double) * 7 * (size_t)c->L.cells,
+                              cudaMemcpyHostToDevice, c->st));
+  CUDA_TRY(c, c->ops->lag_from64(c->L, c->aux[c->steps & 1]));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return LBNR_OK;
+}
+
+int lbnr_deriv_mode(const lbnr_ctx* c) { return c ? c->opts.deriv_mode : -1; }
 
 int lbnr_status(lbnr_ctx* c) {
   if (!c) return fail(c, LBNR_EINVAL, "null context");

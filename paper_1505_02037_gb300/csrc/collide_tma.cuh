@@ -244,10 +244,10 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
       if (valid && g == 0 && !isfinite(chk)) atomicOr(a.flag, 1);
     }
 
-    C alpha, gm[6], K[6], V[3];
-    unpack<REP, C>(rt, alpha, gm, K, V);
+    C alpha, gm[6], Kf[6], V[3];
+    unpack<REP, C>(rt, alpha, gm, Kf, V);
     C Sr[kNF];
-    bm_sources<C>(alpha, gm, K, V, A, D, a.slicing, Sr);
+    bm_sources<C>(alpha, gm, Kf, V, A, D, a.slicing, Sr);
     add_fluid(a, alpha, gm, Sr);
     if (!a.sources_on) {
 #pragma unroll
@@ -256,6 +256,7 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
     C rho[kNF];
 #pragma unroll
     for (int F = 0; F < kNF; ++F) rho[F] = rt[F] + a.half_dt * Sr[F];
+    if (a.aux_out && valid && g == 0) write_lagged<REP, C>(a.aux_out, cells, n.c, rho);
     C Fl[6][3];
     {
       C alpha2, g2[6], K2[6], V2[3];

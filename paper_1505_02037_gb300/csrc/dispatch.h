@@ -17,6 +17,8 @@ struct LaunchCtx {
   double dx, dt, tau;
   int slicing, sources_on;
   void* aux;        // 7 planes of the compute type (stencil input)
+  void* aux_out;    // LAG (reading R17): the step writes its corrected lapse and
+                    // metric here for the next step; nullptr under R5
   double* macro;    // 16 FP64 planes (fields, moments)
   double* aux64;    // 7 FP64 planes (stencil input of the FP64 kernels)
   double* partials; // per-block reduction partials, 22 doubles each
@@ -51,6 +53,10 @@ struct Ops {
   cudaError_t (*set_plane)(const LaunchCtx&, int layout, void* f, int F, int l, const double* in);
   cudaError_t (*get_cells)(const LaunchCtx&, int layout, const void* f, int64_t n,
                            const int64_t* idx, double* out);
+  // LAG: stencil planes `aux` from the FP64 fields in macro; and back to FP64
+  // (aux64, plus the fields alpha and gamma into out when it is not null)
+  cudaError_t (*lag_from64)(const LaunchCtx&, void* aux);
+  cudaError_t (*lag_to64)(const LaunchCtx&, const void* aux, double* out);
 };
 
 // One getter per (velocity set, storage), each in its own translation unit

@@ -137,7 +137,12 @@ struct Impl {
     constexpr bool H = x.hold;
     const int block = 128;
     const int64_t threads = P == 2 ? ((L.cells + 15) / 16) * 32 : L.cells;
-    k_collide<Q, S, C, REP, LAYOUT, P, H><<<grid_for(threads, block), block, 0, L.st>>>(a);
+    // the lagged-field writes cost registers: sized for 2 blocks per SM
+    if (a.aux_out)
+      k_collide<Q, S, C, REP, LAYOUT, P, H, 0, 2, true>
+          <<<grid_for(threads, block), block, 0, L.st>>>(a);
+    else
+      k_collide<Q, S, C, REP, LAYOUT, P, H><<<grid_for(threads, block), block, 0, L.st>>>(a);
     return cudaGetLastError();
   }
 
@@ -149,8 +154,12 @@ struct Impl {
   static cudaError_t launch_shifted(const LaunchCtx& L, const StepArgs<S, C>& a) {
     constexpr int MINB = sizeof(C) == 8 ? 3 : 2;
     const int block = 128;
-    k_collide<Q, S, C, REP, LAYOUT, 1, false, SHIFT, MINB>
-        <<<grid_for(L.cells, block), block, 0, L.st>>>(a);
+    if (a.aux_out)
+      k_collide<Q, S, C, REP, LAYOUT, 1, false, SHIFT, MINB, true>
+          <<<grid_for(L.cells, block), block, 0, L.st>>>(a);
+    else
+      k_collide<Q, S, C, REP, LAYOUT, 1, false, SHIFT, MINB>
+          <<<grid_for(L.cells, block), block, 0, L.st>>>(a);
     return cudaGetLastError();
   }
 
@@ -219,6 +228,7 @@ struct Impl {
     a.fin = static_cast<const S*>(fin);
     a.fout = static_cast<S*>(fout);
     a.aux = static_cast<const C*>(L.aux);
+    a.aux_out = static_cast<C*>(L.aux_out);
     a.flag = L.flag;
     a.G = make_grid(L.nx, L.ny, L.nz, L.cells, L.pstride);
     a.inv2dx = C(1.0 / (2.0 * L.dx));
@@ -347,10 +357,22 @@ struct Impl {
     return cudaGetLastError();
   }
 
+  static cudaError_t lag_from64(const LaunchCtx& L, void* aux) {
+    k_lag_from64<C, REP><<<grid_for(L.cells, 256), 256, 0, L.st>>>(L.macro, static_cast<C*>(aux),
+                                                                 L.cells);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t lag_to64(const LaunchCtx& L, const void* aux, double* out) {
+    k_lag_to64<C, REP><<<grid_for(L.cells, 256), 256, 0, L.st>>>(static_cast<const C*>(aux),
+                                                               L.aux64, out, L.cells);
+    return cudaGetLastError();
+  }
+
   static const Ops* ops() {
     static const Ops o = {VT::n,     &variant_name, &step,          &aux,       &init,
                           &sum64,    &correct64,    &constraints64, &get_plane, &set_plane,
-                          &get_cells};
+                          &get_cells, &lag_from64,  &lag_to64};
     return &o;
   }
 };

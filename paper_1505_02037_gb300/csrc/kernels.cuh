@@ -238,6 +238,10 @@ struct StepArgs {
   const S* fin;
   S* fout;
   const C* aux;  // 7 planes: ln(alpha~) or log1p(alpha~ - 1); gamma~ or gamma~ - delta
+  // Reading R17 (LAG): aux holds the previous step's corrected lapse and
+  // metric in that form, and the step writes its own corrected ones to
+  // aux_out for the next step. nullptr: aux holds this step's rho~ (R5).
+  C* aux_out;
   int* flag;     // set to 1 when a non-finite moment is seen
   Grid G;
   C inv2dx, inv4dx;  // 1/(2 dx), 1/(4 dx)
@@ -255,6 +259,17 @@ struct StepArgs {
   C beta[3];
   const double* beta_field;
 };
+
+// Reading R17: the corrected lapse and metric of this step, in the stencil
+// planes' form (ln alpha and gamma_ij; log1p(alpha - 1) and gamma_ij - delta_ij
+// from deviation moments), for the next step's derivatives.
+template <int REP, class C>
+__device__ __forceinline__ void write_lagged(C* __restrict__ aux_out, int64_t cells, uint32_t c,
+                                             const C rho[kNF]) {
+  aux_out[c] = REP == kDEV ? log1p(rho[0]) : log(rho[0]);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) aux_out[(size_t)(1 + q) * (size_t)cells + c] = rho[1 + q];
+}
 
 // Adds the fluid's term (P/2) gamma_ij to the sources of K_ij (alpha S_ij),
 // with P at the step being taken; nothing without matter. Kept apart from
@@ -362,8 +377,11 @@ __device__ __forceinline__ void unpack(const C m[kNF], C& alpha, C g[6], C K[6],
 // SHIFT: the shift terms are compiled in: 1 a constant shift (a.beta),
 // 2 a static field on top of it (a.beta_field, with its B terms). The
 // zero-shift forms (0) keep none of their code or registers. MINB: blocks
-// per SM the registers are sized for (without HOLD).
-template <int Q, class S, class C, int REP, int LAYOUT, int P, bool HOLD, int SHIFT = 0, int MINB = 3>
+// per SM the registers are sized for (without HOLD). LAGW: the form writes
+// the lagged fields of reading R17 to a.aux_out (compiled in only where
+// asked, so the other forms keep their registers).
+template <int Q, class S, class C, int REP, int LAYOUT, int P, bool HOLD, int SHIFT = 0, int MINB = 3,
+          bool LAGW = false>
 __global__ void __launch_bounds__(128, HOLD ? 1 : MINB) k_collide(const StepArgs<S, C> a) {
   using L = Lattice<Q>;
   constexpr int NJ = kNF / P;
@@ -441,6 +459,7 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : MINB) k_collide(const StepArgs
   C rho[kNF];  // ABS: rho; DEV: rho - rho_flat
 #pragma unroll
   for (int F = 0; F < kNF; ++F) rho[F] = rt[F] + a.half_dt * Sr[F];
+  if (LAGW && valid && g == 0) write_lagged<REP, C>(a.aux_out, cells, n.c, rho);
   C Fl[6][3];
   C Fv[SHIFT == 2 ? 3 : 1][3];  // V fluxes under a shift field
   {
@@ -781,6 +800,41 @@ __global__ void __launch_bounds__(128) k_init(const Init64Args<S> a) {
     }
   }
   if (bad) atomicOr(a.flag, 1);
+}
+
+// Reading R17: the stencil planes of the first step (lbnr_init) or of a
+// restored state (lbnr_set_lagged) from FP64 fields [>= 7][cells]: ln alpha
+// and gamma_ij, or log1p(alpha - 1) and gamma_ij - delta_ij in DEV form.
+template <class C, int REP>
+__global__ void __launch_bounds__(256) k_lag_from64(const double* __restrict__ fields,
+                                                    C* __restrict__ aux, int64_t cells) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cells) return;
+  const double al = fields[c];
+  aux[c] = REP == kDEV ? C(log1p(al - 1.0)) : C(log(al));
+#pragma unroll
+  for (int q = 0; q < 6; ++q)
+    aux[(1 + q) * cells + c] = C(fields[(1 + q) * cells + c] - (REP == kDEV ? flat_value(1 + q) : 0.0));
+}
+
+// Reading R17: the lagged stencil planes as FP64 ln alpha and gamma_ij
+// (aux64, what the FP64 moment and constraint kernels differentiate) and,
+// when out is given, as the fields alpha and gamma_ij [7][cells].
+template <class C, int REP>
+__global__ void __launch_bounds__(256) k_lag_to64(const C* __restrict__ aux,
+                                                  double* __restrict__ aux64, double* out,
+                                                  int64_t cells) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cells) return;
+  const double la = (double)aux[c];
+  aux64[c] = la;
+  if (out) out[c] = exp(la);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const double g = (double)aux[(1 + q) * cells + c] + (REP == kDEV ? flat_value(1 + q) : 0.0);
+    aux64[(1 + q) * cells + c] = g;
+    if (out) out[(1 + q) * cells + c] = g;
+  }
 }
 
 // Sums of all 16 fields in FP64 (rho~ -> macro), ln alpha~ / gamma~ (-> aux64),

@@ -19,6 +19,7 @@ LBNR_D1Q3, LBNR_D2Q9, LBNR_D3Q19 = 1, 2, 3
 LBNR_F64, LBNR_F32, LBNR_DEV_F32, LBNR_DEV_BF16, LBNR_DEV_F16 = 0, 1, 2, 3, 4
 LBNR_GEODESIC, LBNR_HARMONIC, LBNR_ONE_PLUS_LOG = 0, 1, 2
 LBNR_STREAM_AUTO, LBNR_STREAM_PINGPONG, LBNR_STREAM_AA = 0, 1, 2
+LBNR_DERIV_SYNC, LBNR_DERIV_LAG = 0, 1
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENONFINITE", -5: "ETIMEOUT",
           -6: "ESTATE"}
 Q_OF = {1: 3, 2: 9, 3: 19}
@@ -33,7 +34,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("slicing", ctypes.c_int32), ("storage", ctypes.c_int32),
                 ("streaming", ctypes.c_int32), ("sources_on", ctypes.c_int32),
                 ("cuda_stream", ctypes.c_void_p), ("dev_buffer", ctypes.c_void_p),
-                ("dev_bytes", ctypes.c_uint64)]
+                ("dev_bytes", ctypes.c_uint64), ("deriv_mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class RunDesc(ctypes.Structure):
@@ -83,6 +85,9 @@ def library(path: str | None = None):
     L.lbnr_step.argtypes = [vp, i64]
     L.lbnr_step_timed.argtypes = [vp, i64, dp]
     L.lbnr_status.argtypes = [vp]
+    L.lbnr_get_lagged.argtypes = [vp, dp]
+    L.lbnr_set_lagged.argtypes = [vp, dp]
+    L.lbnr_deriv_mode.argtypes = [vp]
     L.lbnr_steps_done.argtypes = [vp]
     L.lbnr_steps_done.restype = i64
     L.lbnr_q.argtypes = [vp]
@@ -94,6 +99,7 @@ def library(path: str | None = None):
     L.lbnr_set_fluid.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     L.lbnr_set_shift.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     L.lbnr_set_shift_field.argtypes = [vp, vp]
+    L.lbnr_fp64_fma_rate.argtypes = [vp, dp]
     L.lbnr_constraint_norms_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(Grid),
                                                  ctypes.c_double, vp, vp, vp]
     L.lbnr_default_batch_opts.argtypes = [ctypes.POINTER(BatchOpts)]
@@ -236,6 +242,14 @@ def lbnr_status(ctx):
     _check(library().lbnr_status(ctx), ctx)
 
 
+def lbnr_get_lagged(ctx, out):
+    _check(library().lbnr_get_lagged(ctx, _host_ptr(out)), ctx)
+
+
+def lbnr_set_lagged(ctx, arr):
+    _check(library().lbnr_set_lagged(ctx, _host_ptr(arr)), ctx)
+
+
 def lbnr_steps_done(ctx) -> int:
     return library().lbnr_steps_done(ctx)
 
@@ -285,6 +299,14 @@ def lbnr_constraint_norms_noalloc(vset: int, grid: Grid, dx: float, d_fields, d_
         _check(library().lbnr_constraint_norms_noalloc(
             int(vset), ctypes.byref(grid), float(dx), ctypes.c_void_p(d_fields.data_ptr()),
             ctypes.c_void_p(d_out.data_ptr()), st))
+
+
+def lbnr_fp64_fma_rate(stream=None) -> float:
+    """Measured FP64 FMA rate of the current device in TFLOP/s."""
+    out = ctypes.c_double(0)
+    st = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+    _check(library().lbnr_fp64_fma_rate(st, ctypes.byref(out)))
+    return out.value
 
 
 def lbnr_destroy(ctx):
@@ -358,7 +380,8 @@ class Lattice:
     """
 
     def __init__(self, vset, shape, tau, dx, dt=None, slicing=LBNR_HARMONIC, storage="f64",
-                 streaming=LBNR_STREAM_AUTO, sources_on=True, stream=None, device=None):
+                 streaming=LBNR_STREAM_AUTO, sources_on=True, stream=None, device=None,
+                 deriv_mode=LBNR_DERIV_SYNC):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("lbnr needs a CUDA device; there is no CPU path")
@@ -379,6 +402,7 @@ class Lattice:
         o.slicing = int(slicing)
         o.storage = int(self.storage)
         o.sources_on = int(bool(sources_on))
+        o.deriv_mode = {"sync": LBNR_DERIV_SYNC, "lag": LBNR_DERIV_LAG}.get(deriv_mode, deriv_mode)
         o.cuda_stream = ctypes.c_void_p(self.stream.cuda_stream)
         if streaming == LBNR_STREAM_AUTO:
             o.streaming = LBNR_STREAM_PINGPONG
@@ -460,6 +484,21 @@ class Lattice:
 
     def status(self):
         lbnr_status(self.ctx)
+
+    def lagged(self):
+        """LAG: the lagged fields [7][cells] (alpha, gamma_ij) the next step
+        differentiates."""
+        out = np.empty((7, self.cells))
+        lbnr_get_lagged(self.ctx, out)
+        return out
+
+    def set_lagged(self, prev):
+        lbnr_set_lagged(self.ctx, np.ascontiguousarray(np.asarray(prev, dtype=np.float64)
+                                                       .reshape(7, self.cells)))
+
+    @property
+    def deriv_mode(self):
+        return library().lbnr_deriv_mode(self.ctx)
 
     @property
     def steps_done(self):

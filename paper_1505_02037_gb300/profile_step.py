@@ -28,7 +28,7 @@ def main(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--storage", default="f32")
     p.add_argument("--n", type=int, default=128)
-    p.add_argument("--variant", type=int, default=0)
+    p.add_argument("--variant", default="0", help="launch form: index or name")
     p.add_argument("--steps", type=int, default=4)
     p.add_argument("--vset", type=int, default=3)
     p.add_argument("--tau", type=float, default=4.5)
@@ -49,10 +49,12 @@ def main(argv=None):
     n = a.n
     shape = (n, n, n) if a.vset == 3 else ((n, n, 1) if a.vset == 2 else (n, 1, 1))
     lat = lbnr.Lattice(a.vset, shape, a.tau, 1 / n, storage=a.storage, streaming=a.streaming)
-    if a.variant >= len(lat.variants):
+    v = lat.variants.index(a.variant) if a.variant in lat.variants else (
+        int(a.variant) if a.variant.isdigit() else -1)
+    if not 0 <= v < len(lat.variants):
         print(f"no launch form {a.variant}; have {lat.variants}")
         return 2
-    lat.set_variant(a.variant)
+    lat.set_variant(v)
     beta = tuple(float(v) for v in a.shift.split(",")) if a.shift else None
     if beta:
         lat.set_shift(beta)
@@ -73,8 +75,8 @@ def ad_main(a):
     n = a.n
     shape = (n, n, n) if a.vset == 3 else ((n, n, 1) if a.vset == 2 else (n, 1, 1))
     lat = lbnr.ADLattice(a.vset, shape, a.tau, 1 / n, storage=a.storage)
-    if a.variant >= 0:
-        lat.set_form(a.variant)
+    if int(a.variant) >= 0:
+        lat.set_form(int(a.variant))
     lat.init(W.gauge_wave(shape, 1 / n, 0.1))
     lat.step(a.steps)
     lat.status()

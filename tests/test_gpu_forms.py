@@ -64,13 +64,17 @@ def bar(spread):
 # ---------------------------------------------------------------------------
 # FP64: every form at the 1e-12 bar
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("vset,shape", [(1, (333, 1, 1)), (2, (37, 23, 1)), (3, (37, 9, 5)),
-                                        (3, (2, 5, 3))])
+# Ragged lattices (a partial last tile of 32 cells) and lattices whose x
+# extent is a multiple of 32 (one tile per row, and several).
+SHAPES = [(1, (333, 1, 1)), (2, (37, 23, 1)), (3, (37, 9, 5)), (3, (2, 5, 3)),
+          (1, (96, 1, 1)), (2, (64, 9, 1)), (3, (64, 5, 3)), (3, (32, 3, 2))]
+
+
+@pytest.mark.parametrize("vset,shape", SHAPES)
 @pytest.mark.parametrize("streaming", [1, 2])
 def test_every_form_fp64_random_state(L, oracle_mod, vset, shape, streaming):
-    """Seeded random near-flat state (every term of the step active), ragged
-    lattices (tiles of 32 cells with a partial last tile), 3 steps in every
-    launch form."""
+    """Seeded random near-flat state (every term of the step active), 3 steps
+    in every launch form."""
     Q = {1: 3, 2: 9, 3: 19}[vset]
     _, w = oracle_mod.velocity_set(vset)
     f0 = W.random_distributions(Q, w, shape, seed=4000 + vset)
@@ -123,10 +127,11 @@ def test_every_form_fp64_diagonal_gauge_wave(L, oracle_mod, vset, N, direction):
 # Reduced precision: every form, one step at a time from the stored state
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("storage", REDUCED)
-@pytest.mark.parametrize("vset,shape", [(1, (1000, 1, 1)), (2, (45, 29, 1)), (3, (37, 9, 5))])
+@pytest.mark.parametrize("vset,shape", [(1, (1000, 1, 1)), (2, (45, 29, 1)), (3, (37, 9, 5)),
+                                        (1, (1024, 1, 1)), (2, (64, 29, 1)), (3, (64, 9, 5))])
 @pytest.mark.parametrize("streaming", [1, 2])
 def test_every_form_reduced_precision_one_step(L, oracle_mod, storage, vset, shape, streaming):
-    """Seeded random near-flat state on ragged lattices; two single steps in
+    """Seeded random near-flat state on ragged and row-aligned lattices; two single steps in
     every form (in place: the even and the odd layout), each against the
     oracle's step from the GPU's stored values, within the derived bound."""
     Q = {1: 3, 2: 9, 3: 19}[vset]

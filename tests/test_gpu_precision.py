@@ -26,6 +26,28 @@ The factor 3 is the margin. The x-aligned 3D run equals the 1D run to round-off
 (pinned on the oracle), so the 1D oracle at the same N is the reference for
 any 3D lattice. With LBNR_REPORT_DIR set, every measured error (against the
 oracle and against the analytic solution) is also written as JSON.
+
+Those K_s are fitted to GB300 runs, so they guard against regressions. The
+bound every run is asserted against first is derived from the arithmetic
+(the per-step terms of onestep_bound.py, summed over a cell's moments):
+with u_s the storage's unit roundoff and u that of FP32, t_l the values a
+moment sum adds (f_l, or f_l - w_l rho_flat in deviation storage), S_ag the
+largest sum_l |t_l| over the lapse and metric fields and S_all over all 16,
+
+  e_0 = u_s S_all / A                           (rounding the initial state)
+  e_1 = [9 omega c_F N (u_s + (Q - 1) u) S_ag + u_s S_all] / A   (each step)
+
+where the lapse and metric moments carry (u_s + (Q-1) u) S_ag (the stored
+state's rounding and the FP32 sum), central differences turn that into
+errors 3 N times larger in alpha(4 D + A), the flux of the K equilibria
+(3 omega c.F) passes them on with c_F = sum_l w_l sum_k |c_lk|, and the
+output is rounded once more. Then
+
+    error after n steps  <=  3 (lambda^n e_0 + e_1 sum_{k<n} lambda^k).
+
+It takes every rounding at its worst (Q - 1 roundings in one sum, every
+stencil error aligned), so it lies one to two orders above the fitted
+bound; it holds without reference to the kernel under test.
 """
 import json
 import math
@@ -85,6 +107,36 @@ def bound(storage, three_d, N, tau, n, lam):
     return 3 * k * (N / (2 * math.pi)) / tau * growth
 
 
+U_S = {"dev_bf16": 2.0 ** -8, "dev_f16": 2.0 ** -11, "dev_f32": 2.0 ** -24, "f32": 2.0 ** -24}
+U_C = 2.0 ** -24
+FLAT = np.array([1.0, 1, 0, 0, 1, 0, 1] + [0.0] * 9)
+
+
+def derived_errors(oracle_mod, storage, vset, N, tau, f0=None, A_=A):
+    """(e_0, e_1) of the derived bound (module docstring), relative to A,
+    from the initial distributions f0 of the run [16][Q][cells] (by default
+    those of the x-aligned gauge wave, whose profile every row repeats)."""
+    c, w = oracle_mod.velocity_set(vset)
+    Q = len(w)
+    if f0 is None:
+        f0 = oracle_mod.Oracle(vset, (N, 1, 1), tau, 1 / N).init(
+            W.gauge_wave((N, 1, 1), 1 / N, A_))
+    t = f0 - (np.asarray(w).reshape(1, Q, 1) * FLAT.reshape(16, 1, 1)
+              if storage.startswith("dev") else 0)
+    s_ag = np.abs(t[:7]).sum(axis=1).max()
+    s_all = np.abs(t).sum(axis=1).max()
+    c_flux = float((np.asarray(w) * np.abs(np.asarray(c)).sum(axis=1)).sum())
+    us = U_S[storage]
+    e0 = us * s_all / A_
+    e1 = (9 / tau * c_flux * N * (us + (Q - 1) * U_C) * s_ag + us * s_all) / A_
+    return e0, e1
+
+
+def derived_bound(e0, e1, n, lam):
+    growth = n if abs(lam - 1) < 1e-12 else (lam ** n - 1) / (lam - 1)
+    return 3 * (lam ** n * e0 + e1 * growth)
+
+
 def oracle_moments(oracle_mod, N, tau, steps):
     o = oracle_mod.Oracle(1, (N, 1, 1), tau, 1 / N)
     f = o.init(W.gauge_wave((N, 1, 1), 1 / N, A))
@@ -100,6 +152,7 @@ def check(L, oracle_mod, storage, vset, N, tau, steps):
     three_d = vset == 3
     shape = (N, N, N) if three_d else (N, 1, 1)
     lam = amplification(oracle_mod, tau)
+    e0, e1 = derived_errors(oracle_mod, storage, vset, N, tau)
     ref = oracle_moments(oracle_mod, N, tau, steps)
     lat = L.Lattice(vset, shape, tau, 1 / N, storage=storage)
     lat.init(W.gauge_wave(shape, 1 / N, A))
@@ -114,10 +167,12 @@ def check(L, oracle_mod, storage, vset, N, tau, steps):
         err_exact = float(np.abs(m - exact).max() / A)
         oracle_exact = float(np.abs(ref[n][:, None, :] - exact).max() / A)
         b = bound(storage, three_d, N, tau, n, lam)
+        db = derived_bound(e0, e1, n, lam)
         REPORT.append(dict(storage=storage, vset=vset, N=N, tau=tau, step=n, lam=lam,
-                           err_vs_oracle=err, bound=b, err_vs_analytic=err_exact,
-                           oracle_err_vs_analytic=oracle_exact))
-        assert err <= b, (storage, vset, N, tau, n, err, b)
+                           err_vs_oracle=err, bound=b, derived_bound=db,
+                           err_vs_analytic=err_exact, oracle_err_vs_analytic=oracle_exact))
+        assert err <= db, ("derived", storage, vset, N, tau, n, err, db)
+        assert err <= b, ("fitted", storage, vset, N, tau, n, err, b)
     lat.close()
 
 
@@ -183,4 +238,32 @@ def test_every_launch_form_at_full_size(L, oracle_mod, storage):
         REPORT.append(dict(storage=storage, vset=3, N=N, tau=tau, step=n, form=name,
                            err_vs_oracle=err, bound=b))
         assert err <= b, (name, err, b)
+    lat.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "dev_f32", "dev_f16", "dev_bf16"])
+@pytest.mark.parametrize("tau", [0.8, 1.5])
+def test_reduced_precision_diagonal_wave_within_derived_bound(L, oracle_mod, storage, tau):
+    """The gauge wave along the (1,1,1) diagonal on 32^3 (every metric
+    component and every stencil direction active), 1 and 10 steps against
+    the D3Q19 oracle at the same size, within the derived bound."""
+    N = 32
+    shape = (N, N, N)
+    fields = W.gauge_wave(shape, 1 / N, A, direction="xyz")
+    lam = amplification(oracle_mod, tau)
+    o = oracle_mod.Oracle(3, shape, tau, 1 / N)
+    f = o.init(fields)
+    e0, e1 = derived_errors(oracle_mod, storage, 3, N, tau, f0=f)
+    lat = L.Lattice(3, shape, tau, 1 / N, storage=storage)
+    lat.init(fields)
+    done = 0
+    for n in (1, 10):
+        f = o.run(f, n - done)
+        lat.step(n - done)
+        done = n
+        err = float(np.abs(lat.moments() - o.moments(f)).max() / A)
+        db = derived_bound(e0, e1, n, lam)
+        REPORT.append(dict(storage=storage, vset=3, N=N, tau=tau, step=n, wave="diagonal",
+                           err_vs_oracle=err, derived_bound=db))
+        assert err <= db, (storage, tau, n, err, db)
     lat.close()
