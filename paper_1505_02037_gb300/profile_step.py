@@ -65,7 +65,7 @@ def main(argv=None):
     lat.status()
     ms = lat.step_timed(4)
     form = ("P1-reread-shiftfield" if a.shift_field else
-            "P1-reread-shift" if beta else lat.variants[a.variant])
+            "P1-reread-shift" if beta else lat.variants[v])
     print(f"{a.storage} n={n} vset={a.vset} {form}: "
           f"ms per step aux {ms[0] / 4:.4f} collide {ms[1] / 4:.4f}")
     return 0

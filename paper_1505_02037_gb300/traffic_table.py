@@ -58,8 +58,9 @@ def read_ncu_csv(path, kernel_substring):
         key = row["ID"]
         unit = row.get("Metric Unit", "")
         v = float(row["Metric Value"].replace(",", ""))
+        # bytes as bytes, durations in milliseconds
         scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "nsecond": 1e-6,
-                 "usecond": 1e-3, "msecond": 1.0}.get(unit, 1.0)
+                 "ns": 1e-6, "usecond": 1e-3, "us": 1e-3, "msecond": 1.0, "ms": 1.0}.get(unit, 1.0)
         launches.setdefault(key, {})[row["Metric Name"]] = v * scale
     return list(launches.values())
 
@@ -90,6 +91,13 @@ def main(argv=None):
              "captured_on": a.captured_on, "command": a.command}
     if a.flops_per_cell is not None:
         entry["fp64_flops_per_cell"] = a.flops_per_cell
+    ops = {k: m.get(f"smsp__sass_thread_inst_executed_op_{k}_pred_on.sum")
+           for k in ("dadd", "dmul", "dfma")}
+    if all(v is not None for v in ops.values()):
+        # FP64 flops with a fused multiply-add counted as two
+        entry["fp64_instructions_per_cell"] = round(sum(ops.values()) / a.cells, 1)
+        entry["fp64_flops_per_cell"] = round((ops["dadd"] + ops["dmul"] + 2 * ops["dfma"]) /
+                                             a.cells, 1)
     table = {}
     if os.path.exists(a.out):
         with open(a.out) as f:
