@@ -108,6 +108,9 @@ def parse():
     p.add_argument("--profile-steps", type=int, default=20)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--deriv", default="sync", choices=["sync", "lag"],
+                   help="time level of A and D for the batched workload (lag: one pass and "
+                        "one team barrier per step)")
     p.add_argument("--no-modes", action="store_true",
                    help="skip the same-run LAG record and the one-crossing precision records")
     p.add_argument("--variant", default=None,
@@ -564,7 +567,7 @@ def main_batched(args):
     hnp = host.numpy()
     for i, r in enumerate(specs):
         hnp[offs[i]:offs[i + 1]] = W.ensemble_fields(r).reshape(-1)
-    b = lbnr.Batch(specs, storage="dev_f32", replan=True)
+    b = lbnr.Batch(specs, storage="dev_f32", replan=True, deriv_mode=args.deriv)
 
     def init_all():
         for i in range(len(specs)):
@@ -601,7 +604,10 @@ def main_batched(args):
     units = float(sum(c * 16 * t for c, t in zip(cells, taken)))
     ms_max, units_all = over_ranks(ms, units, world, dev)
     qs = [3 if r["vset"] == 1 else 9 for r in specs]
-    alg = float(sum(c * t * (2 * 16 * q * 4 + 7 * 4) for c, t, q in zip(cells, taken, qs)))
+    # distributions in and out, and the stencil planes (read once under SYNC;
+    # read and written under LAG)
+    aux_b = 14 * 4 if args.deriv == "lag" else 7 * 4
+    alg = float(sum(c * t * (2 * 16 * q * 4 + aux_b) for c, t, q in zip(cells, taken, qs)))
     peaks, peak_kind = measured_peaks()
     peak = float(peaks["hbm_gbs"])
     achieved = alg / (ms * 1e-3) / 1e9
@@ -619,11 +625,12 @@ def main_batched(args):
                        cell_steps_taken=int(taken @ np.array(cells)),
                        cell_steps_configured=int(sum(c * r["steps_total"]
                                                      for c, r in zip(cells, specs))),
-                       runs_nonfinite=nonfinite, runs_timed_out=sum(1 for x in per if x == -5)),
+                       runs_nonfinite=nonfinite, runs_timed_out=sum(1 for x in per if x == -5),
+                       deriv_mode=args.deriv),
         "roofline": {"bound": "hbm", "kernel": "k_batch (persistent ensemble kernel)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": f"hbm_gbs of {peak_kind}",
-                     "algorithmic_bytes_per_cell_step": "2*16*Q*4 + 7*4 (Q = 3 or 9)",
+                     "algorithmic_bytes_per_cell_step": "2*16*Q*4 + 7*4 (LAG: 14*4), Q = 3 or 9",
                      "avg_launch_ms": ms / (args.steps * sub), "traffic": None},
         "gpu_launches": args.steps * sub,
         "launch_form": f"block {plan['block']} x grid {plan['grid']}, "
@@ -734,6 +741,18 @@ def precision_records(args, N, device_index):
             finite, m = False, None
         rec = {"value": cells * 16 * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps,
                "launch_form": lat.variants[lat.variant], "finite": finite}
+        if storage == "f64":
+            # the FP64 step is bound by the FP64 pipe: its collide kernel's
+            # flops (ncu count per cell) against the rate measured here
+            flops = profile_entry(f"k_collide:gauge3d-{N}-f64:{rec['launch_form']}",
+                                  "fp64_flops_per_cell")
+            _, col = lat.step_timed(4)
+            peak = lbnr.lbnr_fp64_fma_rate(lat.stream)
+            rec["collide_ms"] = col / 4
+            rec["fp64_peak_tflops_measured"] = peak
+            if flops is not None:
+                ach = flops * cells / (col / 4 * 1e-3) / 1e12
+                rec["alu"] = {"flops_per_cell": flops, "achieved_tflops": ach, "frac": ach / peak}
         if finite:
             rec["err_vs_analytic"] = float(np.abs(m - exact).max() / A)
             if ref is None:

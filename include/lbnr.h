@@ -305,10 +305,15 @@ typedef struct {
   int32_t replan;       /* 1: every lbnr_batch_run first calls
                            lbnr_batch_replan (and so waits for the work
                            before it); 0 (default): plan once */
+  int32_t deriv_mode;   /* LBNR_DERIV_SYNC (default): per step a moment pass,
+                           a team barrier, the collide pass and a barrier;
+                           LBNR_DERIV_LAG: the collide pass (it writes the
+                           next step's stencil planes) and one barrier */
+  int32_t reserved;     /* 0 */
 } lbnr_batch_opts;
 
 /* Fills o with the defaults: DEV_F32, 256 threads, all resident blocks,
- * sources on, 2 s wait limit, no dropped arrival, no re-planning. */
+ * sources on, 2 s wait limit, no dropped arrival, no re-planning, SYNC. */
 void lbnr_default_batch_opts(lbnr_batch_opts* o);
 
 /* Validates the runs, allocates every run's two distribution buffers and

@@ -20,6 +20,9 @@
 //
 // Kernel: for each step of a run the team's CTAs split the cells, run the
 // moment pass, meet at a team barrier, run the collide pass, and meet again.
+// With lagged derivatives (reading R17) a step is the collide pass alone,
+// reading the stencil planes the previous step wrote and writing the next
+// ones into the run's second plane set, and one team barrier.
 // A team barrier is a per-run counter: each CTA adds one and waits until
 // the counter reaches the number of arrivals expected so far. The wait is
 // bounded (globaltimer); on time-out the run's status gets bit 1 and its
@@ -46,6 +49,7 @@ namespace {
 struct BatchRun {
   void* f[2];
   void* aux;
+  void* aux2;  // LAG: the second set of stencil planes (nullptr otherwise)
   Grid G;
   double tau, dx;
   int64_t steps;
@@ -109,7 +113,7 @@ __device__ bool team_sync(const BatchParams& p, const Assign& A, int k) {
   return ok != 0;
 }
 
-template <int Q, class S, class C, int REP>
+template <int Q, class S, class C, int REP, bool LAG>
 __device__ void run_steps(const BatchParams& p, const BatchRun& R, const Assign& A) {
   // every field read once into registers (a runtime index into a copy of the
   // descriptor would put it in local memory)
@@ -136,6 +140,7 @@ __device__ void run_steps(const BatchParams& p, const BatchRun& R, const Assign&
   a.beta[0] = a.beta[1] = a.beta[2] = C(0);
   a.beta_field = nullptr;
   C* const aux = static_cast<C*>(R.aux);
+  C* const aux2 = static_cast<C*>(R.aux2);
   const int64_t cells = a.G.cells;
   const int64_t B = blockDim.x;
   // A run that went non-finite or timed out in an earlier launch stays where
@@ -148,14 +153,21 @@ __device__ void run_steps(const BatchParams& p, const BatchRun& R, const Assign&
     const bool odd = ((start + s) & 1) != 0;
     a.fin = odd ? f1 : f0;
     a.fout = const_cast<S*>(odd ? f0 : f1);
-    for (int64_t base = A.rank * B; base < cells; base += (int64_t)A.team * B) {
-      const int64_t c = base + threadIdx.x;
-      if (c < cells) aux_cell<Q, S, C, REP, kPingPong>(a.fin, aux, a.G, c);
+    if (LAG) {
+      // the stencil planes of this step (written by the previous one) and of
+      // the next, alternating with the step parity like the distributions
+      a.aux = odd ? aux2 : aux;
+      a.aux_out = odd ? aux : aux2;
+    } else {
+      for (int64_t base = A.rank * B; base < cells; base += (int64_t)A.team * B) {
+        const int64_t c = base + threadIdx.x;
+        if (c < cells) aux_cell<Q, S, C, REP, kPingPong>(a.fin, aux, a.G, c);
+      }
+      if (!team_sync(p, A, k++)) return;
     }
-    if (!team_sync(p, A, k++)) return;
     for (int64_t base = A.rank * B; base < cells; base += (int64_t)A.team * B) {
       const int64_t c = base + threadIdx.x;
-      if (c < cells) collide_cell<Q, S, C, REP, kPingPong>(a, c);
+      if (c < cells) collide_cell<Q, S, C, REP, kPingPong, LAG>(a, c);
     }
     if (!team_sync(p, A, k++)) return;
     ++s;
@@ -186,7 +198,7 @@ struct BatchForm<2> {
   static constexpr int kThreads = 128, kMinBlocks = 4;
 };
 
-template <class S, int REP, int FORM>
+template <class S, int REP, int FORM, bool LAG>
 __global__ void __launch_bounds__(BatchForm<FORM>::kThreads, BatchForm<FORM>::kMinBlocks)
     k_batch(const BatchParams p) {
   using C = typename std::conditional<sizeof(S) == 8, double, float>::type;
@@ -201,20 +213,20 @@ __global__ void __launch_bounds__(BatchForm<FORM>::kThreads, BatchForm<FORM>::kM
     const Assign A = p.work[i];
     const BatchRun& R = p.runs[A.run];
     if (R.q == 3)
-      run_steps<3, S, C, REP>(p, R, A);
+      run_steps<3, S, C, REP, LAG>(p, R, A);
     else
-      run_steps<9, S, C, REP>(p, R, A);
+      run_steps<9, S, C, REP, LAG>(p, R, A);
   }
 }
 
-template <int FORM>
+template <int FORM, bool LAG>
 void* batch_kernel_form(int storage) {
   switch (storage) {
-    case LBNR_F64: return (void*)k_batch<double, kABS, FORM>;
-    case LBNR_F32: return (void*)k_batch<float, kABS, FORM>;
-    case LBNR_DEV_F32: return (void*)k_batch<float, kDEV, FORM>;
-    case LBNR_DEV_BF16: return (void*)k_batch<__nv_bfloat16, kDEV, FORM>;
-    case LBNR_DEV_F16: return (void*)k_batch<__half, kDEV, FORM>;
+    case LBNR_F64: return (void*)k_batch<double, kABS, FORM, LAG>;
+    case LBNR_F32: return (void*)k_batch<float, kABS, FORM, LAG>;
+    case LBNR_DEV_F32: return (void*)k_batch<float, kDEV, FORM, LAG>;
+    case LBNR_DEV_BF16: return (void*)k_batch<__nv_bfloat16, kDEV, FORM, LAG>;
+    case LBNR_DEV_F16: return (void*)k_batch<__half, kDEV, FORM, LAG>;
     default: return nullptr;
   }
 }
@@ -226,9 +238,16 @@ int form_for(int block, int per_sm) {
   return per_sm == 4 ? 2 : 1;
 }
 
-void* batch_kernel(int storage, int form) {
-  return form == 0 ? batch_kernel_form<0>(storage)
-                   : form == 1 ? batch_kernel_form<1>(storage) : batch_kernel_form<2>(storage);
+template <bool LAG>
+void* batch_kernel_mode(int storage, int form) {
+  return form == 0 ? batch_kernel_form<0, LAG>(storage)
+                   : form == 1 ? batch_kernel_form<1, LAG>(storage)
+                               : batch_kernel_form<2, LAG>(storage);
+}
+
+void* batch_kernel(int storage, int form, int deriv_mode) {
+  return deriv_mode == LBNR_DERIV_LAG ? batch_kernel_mode<true>(storage, form)
+                                      : batch_kernel_mode<false>(storage, form);
 }
 
 int qv(int vset) { return vset == LBNR_D1Q3 ? 3 : vset == LBNR_D2Q9 ? 9 : 0; }
@@ -370,7 +389,7 @@ int configure(lbnr_batch* b, int block, int ctas_per_sm) {
   if (block != 128 && block != 256) return bfail(b, LBNR_EINVAL, "block must be 128 or 256");
   if (ctas_per_sm < 0 || ctas_per_sm > 4) return bfail(b, LBNR_EINVAL, "ctas_per_sm must be 0..4");
   const int form = form_for(block, ctas_per_sm);
-  void* kern = batch_kernel(b->opts.storage, form);
+  void* kern = batch_kernel(b->opts.storage, form, b->opts.deriv_mode);
   // the kernel uses no shared memory to speak of: give the SM's unified
   // cache to L1
   BTRY(b, cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
@@ -424,7 +443,8 @@ cudaError_t enqueue_batch(lbnr_batch* b, BatchParams& p) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   void* args[] = {&p};
-  return cudaLaunchKernelExC(&cfg, batch_kernel(b->opts.storage, b->form), args);
+  return cudaLaunchKernelExC(&cfg, batch_kernel(b->opts.storage, b->form, b->opts.deriv_mode),
+                             args);
 }
 
 }  // namespace
@@ -440,13 +460,17 @@ void lbnr_default_batch_opts(lbnr_batch_opts* o) {
   o->sources_on = 1;
   o->wait_limit_ns = 2000000000ll;
   o->test_drop_arrival_run = -1;
+  o->deriv_mode = LBNR_DERIV_SYNC;
 }
 
 int lbnr_batch_create(int nruns, const lbnr_run_desc* runs, const lbnr_batch_opts* opts,
                       lbnr_batch** out) {
   if (!out || !runs || !opts || nruns < 1) return bfail(nullptr, LBNR_EINVAL, "bad argument");
   *out = nullptr;
-  if (!batch_kernel(opts->storage, 0)) return bfail(nullptr, LBNR_EINVAL, "unknown storage");
+  if (!batch_kernel(opts->storage, 0, LBNR_DERIV_SYNC))
+    return bfail(nullptr, LBNR_EINVAL, "unknown storage");
+  if (opts->deriv_mode != LBNR_DERIV_SYNC && opts->deriv_mode != LBNR_DERIV_LAG)
+    return bfail(nullptr, LBNR_EINVAL, "unknown derivative mode");
   for (int r = 0; r < nruns; ++r) {
     const lbnr_run_desc& d = runs[r];
     if (qv(d.vset) == 0) return bfail(nullptr, LBNR_EINVAL, "batched runs are D1Q3 or D2Q9");
@@ -466,6 +490,7 @@ int lbnr_batch_create(int nruns, const lbnr_run_desc* runs, const lbnr_batch_opt
   const size_t sb = storage_bytes(opts->storage);
   const size_t cb = storage_is_fp64(opts->storage) ? 8 : 4;
   // lay out every run's two buffers and stencil planes in one allocation
+  const bool lag = opts->deriv_mode == LBNR_DERIV_LAG;
   std::vector<size_t> off_f(nruns), off_aux(nruns);
   size_t off = 0;
   for (int r = 0; r < nruns; ++r) {
@@ -475,7 +500,7 @@ int lbnr_batch_create(int nruns, const lbnr_run_desc* runs, const lbnr_batch_opt
     off_f[r] = off;
     off += ((size_t)2 * 16 * qv(runs[r].vset) * ps * sb + 255) & ~(size_t)255;
     off_aux[r] = off;
-    off += ((size_t)7 * cells * cb + 255) & ~(size_t)255;
+    off += (((size_t)7 * cells * cb + 255) & ~(size_t)255) * (lag ? 2 : 1);
   }
   const size_t stage_off = off;
   off += ((size_t)16 * b->max_cells * 8 + 255) & ~(size_t)255;
@@ -497,6 +522,7 @@ int lbnr_batch_create(int nruns, const lbnr_run_desc* runs, const lbnr_batch_opt
     h.f[0] = base + off_f[r];
     h.f[1] = base + off_f[r] + (size_t)16 * qv(d.vset) * ps * sb;
     h.aux = base + off_aux[r];
+    h.aux2 = lag ? base + off_aux[r] + (((size_t)7 * cells * cb + 255) & ~(size_t)255) : nullptr;
     h.G = make_grid((int32_t)d.grid.nx, (int32_t)d.grid.ny, 1, cells, ps);
     h.tau = d.tau;
     h.dx = d.dx;
@@ -569,6 +595,8 @@ int lbnr_batch_init(lbnr_batch* b, int run, const double* fields) {
   const Ops* o = ops_for_run(d.vset, b->opts.storage);
   BTRY(b, cudaMemsetAsync(b->d_status + run, 0, sizeof(int), b->st));
   BTRY(b, o->init(L, h.f[0]));
+  // LAG: the first step's derivatives come from the initial fields
+  if (b->opts.deriv_mode == LBNR_DERIV_LAG) BTRY(b, o->lag_from64(L, h.aux));
   BTRY(b, cudaMemsetAsync(b->d_done + run, 0, sizeof(int64_t), b->st));
   BTRY(b, cudaStreamSynchronize(b->st));
   b->done[run] = 0;

@@ -628,7 +628,7 @@ __device__ __forceinline__ void derivatives_coh(const Nbr& n, int64_t cells,
   }
 }
 
-template <int Q, class S, class C, int REP, int LAYOUT>
+template <int Q, class S, class C, int REP, int LAYOUT, bool LAGW = false>
 __device__ __forceinline__ void collide_cell(const StepArgs<S, C>& a, int64_t c) {
   using L = Lattice<Q>;
   constexpr int dim = L::kDim;
@@ -668,6 +668,7 @@ __device__ __forceinline__ void collide_cell(const StepArgs<S, C>& a, int64_t c)
   C rho[kNF];
 #pragma unroll
   for (int F = 0; F < kNF; ++F) rho[F] = rt[F] + a.half_dt * Sr[F];
+  if (LAGW) write_lagged<REP, C>(a.aux_out, cells, n.c, rho);
   C Fl[6][3];
   {
     C alpha2, g2[6], K2[6], V2[3];

@@ -47,7 +47,8 @@ class BatchOpts(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("sources_on", ctypes.c_int32),
                 ("cuda_stream", ctypes.c_void_p), ("wait_limit_ns", ctypes.c_int64),
-                ("test_drop_arrival_run", ctypes.c_int32), ("replan", ctypes.c_int32)]
+                ("test_drop_arrival_run", ctypes.c_int32), ("replan", ctypes.c_int32),
+                ("deriv_mode", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class LbnrError(RuntimeError):
@@ -525,7 +526,7 @@ class Batch:
 
     def __init__(self, runs, storage="dev_f32", block=256, ctas_per_sm=0, sources_on=True,
                  wait_limit_ns=2_000_000_000, drop_arrival_run=-1, replan=False, stream=None,
-                 device=None):
+                 device=None, deriv_mode=LBNR_DERIV_SYNC):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("lbnr needs a CUDA device; there is no CPU path")
@@ -552,6 +553,7 @@ class Batch:
         o.wait_limit_ns = int(wait_limit_ns)
         o.test_drop_arrival_run = int(drop_arrival_run)
         o.replan = int(bool(replan))
+        o.deriv_mode = {"sync": LBNR_DERIV_SYNC, "lag": LBNR_DERIV_LAG}.get(deriv_mode, deriv_mode)
         self.storage = o.storage
         self.b = lbnr_batch_create(descs, o)
 

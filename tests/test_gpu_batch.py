@@ -296,3 +296,32 @@ def test_ensemble_configuration_first_16_runs(L, oracle_mod):
         lat.close()
     b64.close()
     b32.close()
+
+
+@pytest.mark.parametrize("teams", [False, True])
+def test_batch_lag_fp64_matches_oracle(L, oracle_mod, teams):
+    """Lagged derivatives (reading R17) in the batch: a step is the collide
+    pass alone (it writes the next step's stencil planes) and one team
+    barrier. Each run of a mixed ensemble, and of one whose large runs are
+    split over teams of blocks, equals the oracle's LAG run to the FP64 bar."""
+    runs = team_ensemble() if teams else small_ensemble(n=8, seed=13)
+    kw = dict(block=256, ctas_per_sm=1) if teams else {}
+    b = make_batch(L, runs, storage="f64", deriv_mode="lag", **kw)
+    if teams:
+        t = b.plan()["teams"]
+        assert t[0] > 1 and t[1] > 1
+    b.run()
+    rc, per = b.status()
+    assert rc == 0 and per == [0] * len(runs)
+    for i, r in enumerate(runs):
+        assert b.steps_done(i) == r["steps"]
+        o = oracle_mod.Oracle(r["vset"], r["shape"], r["tau"], r["dx"],
+                              slicing=r.get("slicing", 1), deriv_mode=1)
+        f0, p0 = o.lag_init(W.ensemble_fields(r))
+        f, _ = o.run_lag(f0, p0, r["steps"])
+        fp, _ = o.run_lag(perturbed(f0), p0, r["steps"])
+        kscale = math.pi * r["A"]
+        spread = dist_err(fp, f, kscale).max()
+        err = dist_err(b.distributions(i), f, kscale).max()
+        assert err <= max(TOL64, 4 * spread), (i, r, err, spread)
+    b.close()
