@@ -270,6 +270,17 @@ inline unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b
 constexpr int kTileCells = 32;
 constexpr int kPlanesPerBox = kNFA;  // 37*Q planes = Q boxes of 37
 
+// 2D tensor copy of one box (x = cell, y = plane) into shared memory,
+// completing on the mbarrier.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int32_t x,
+                                            int32_t y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
 template <class S>
 __host__ __device__ constexpr uint32_t tma_stage(int Q) {
   return (uint32_t)(kNFA * Q * kTileCells * sizeof(S));
@@ -495,6 +506,19 @@ __global__ void __launch_bounds__(32 * (NS * P + 1), 1)
   }
 }
 
+// One distribution plane of the 37-field state (plane layout: all cells of
+// one (F, l) contiguous) to FP64 and back.
+template <class S>
+__global__ void k_ad_get_plane(const S* __restrict__ plane, double* __restrict__ out, int64_t cells) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < cells) out[c] = (double)Codec<S>::load_keep(plane + c);
+}
+template <class S>
+__global__ void k_ad_set_plane(S* __restrict__ plane, const double* __restrict__ in, int64_t cells) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < cells) Codec<S>::store(plane + c, (decltype(Codec<S>::load(plane)))in[c]);
+}
+
 // cuTensorMapEncodeTiled through the runtime's driver entry point.
 inline PFN_cuTensorMapEncodeTiled_v12000 ad_tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -591,14 +615,14 @@ struct Ops {
   }
   static cudaError_t get_plane(const Grid& G, const void* f, int F, int l, double* out,
                                cudaStream_t st) {
-    k_get_plane<Q, S, kABS, kPingPong><<<blocks_for(G.cells, 256), 256, 0, st>>>(
-        static_cast<const S*>(f), out, G, F, l);
+    k_ad_get_plane<S><<<blocks_for(G.cells, 256), 256, 0, st>>>(
+        static_cast<const S*>(f) + (size_t)(F * Q + l) * G.pstride, out, G.cells);
     return cudaGetLastError();
   }
   static cudaError_t set_plane(const Grid& G, void* f, int F, int l, const double* in,
                                cudaStream_t st) {
-    k_set_plane<Q, S, kABS, kPingPong><<<blocks_for(G.cells, 256), 256, 0, st>>>(
-        static_cast<S*>(f), in, G, F, l);
+    k_ad_set_plane<S><<<blocks_for(G.cells, 256), 256, 0, st>>>(
+        static_cast<S*>(f) + (size_t)(F * Q + l) * G.pstride, in, G.cells);
     return cudaGetLastError();
   }
 };

@@ -158,7 +158,7 @@ int validate(const lbnr_grid* g, int vset, const lbnr_opts* o) {
   if (g->nx > (1 << 30) || g->ny > (1 << 30) || g->nz > (1 << 30))
     return fail(nullptr, LBNR_EINVAL, "grid side too large");
   {
-    // 32-bit cell indices, and 32-bit offsets inside a field's Q planes
+    // 32-bit cell indices; a buffer of at most 2^32 values per field
     const uint64_t cells = (uint64_t)g->nx * g->ny * g->nz;
     const uint64_t ps = (cells + kTile - 1) / kTile * kTile;
     if (cells >= (1ull << 31) || (uint64_t)q_of(vset) * ps >= (1ull << 32))
@@ -423,7 +423,7 @@ int lbnr_create(const lbnr_grid* grid, int vset, double tau, double dx, double d
   L.beta[0] = L.beta[1] = L.beta[2] = 0;
   L.shift_on = 0;
   L.beta_field = nullptr;
-  // zero everything once: the plane padding must hold finite values
+  // zero everything once: the padding cells of the last tile must hold finite values
   cudaError_t e = cudaMemsetAsync(c->base, 0, Ly.total, c->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
   if (e != cudaSuccess) {

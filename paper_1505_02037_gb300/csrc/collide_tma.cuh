@@ -2,11 +2,11 @@
 // (same arithmetic as k_collide in kernels.cuh: Eq. numlb with the
 // equilibria and sources of Eqs. alfa-ekstsor and rho = sum f + dt S/2).
 //
-// One persistent CTA per SM. Warp NC (the producer) streams tiles of
-// TC consecutive cells into a ring of NS shared-memory stages: every
-// distribution plane of a tile is one row of the stage, and the whole stage
-// (16*Q rows) arrives through one or two 2D tensor copies
-// (cp.async.bulk.tensor) that signal a "full" mbarrier. Consumer warps
+// One persistent CTA per SM. Warp NC (the producer) streams tiles of 32
+// consecutive cells into a ring of NS shared-memory stages: in the
+// tile-blocked layout a tile's 16 Q rows of 32 values are one contiguous
+// block, and the whole stage arrives through one bulk copy (cp.async.bulk)
+// that signals a "full" mbarrier. Consumer warps
 // 0..NC-1 each take whole tiles: two lanes per cell, each lane owning 8 of
 // the 16 fields. A consumer sums its moments from shared memory, swaps them
 // with its partner lane, evaluates the Bona-Masso sources and fluxes, then
@@ -69,21 +69,20 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_
     if (global_ns() - t0 > limit_ns) return false;
   }
 }
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int32_t x,
-                                            int32_t y, uint32_t bar) {
+// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
+// from global to shared memory, completing on the mbarrier.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint32_t bar) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar)
       : "memory");
 }
 
 template <int Q>
 struct TmaShape {
   static constexpr int kPlanes = kNF * Q;
-  static constexpr int kBoxes = (kPlanes + 255) / 256;  // a TMA box side is at most 256
-  static constexpr int kPlanesPerBox = kPlanes / kBoxes;
-  static_assert(kPlanes % kBoxes == 0, "planes must split evenly into boxes");
 };
 
 template <class S>
@@ -94,7 +93,7 @@ __host__ __device__ constexpr uint32_t tma_smem_bytes(uint32_t stage_bytes, int 
   return 1024u + stage_bytes * (uint32_t)NS;
 }
 
-// TC cells per tile (16 or 32); P lanes per cell (P = 2: each lane owns 8
+// TC = 32 cells per tile; P lanes per cell (P = 2: each lane owns 8
 // fields and partner lanes swap moments; P = 1: one lane per cell, all 16
 // fields). A tile is consumed by WPT = TC / (32/P) warps together (a group);
 // there are NP = NC/WPT groups, and each group owns K
@@ -105,7 +104,7 @@ __host__ __device__ constexpr uint32_t tma_smem_bytes(uint32_t stage_bytes, int 
 // the awaited one.
 template <int Q, class S, class C, int REP, int LAYOUT, int NC, int K, int TC, int P>
 __global__ void __launch_bounds__(32 * (NC + 1), 1)
-    k_collide_tma(const StepArgs<S, C> a, const __grid_constant__ CUtensorMap tmap, int64_t ntiles) {
+    k_collide_tma(const StepArgs<S, C> a, int64_t ntiles) {
   static_assert(LAYOUT == kPingPong || LAYOUT == kAAEven, "reads must be local");
   static_assert(P == 1 || P == 2, "one or two lanes per cell");
   constexpr int CPW = 32 / P;    // cells per consumer warp
@@ -113,7 +112,7 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
   constexpr int WPT = TC / CPW;  // warps per tile
   constexpr int NP = NC / WPT;
   constexpr int NS = NP * K;
-  static_assert(TC == 16 || TC == 32, "tile of 16 or 32 cells");
+  static_assert(TC == kTileCells, "a stage is one tile of the tile-blocked layout");
   static_assert(TC % CPW == 0, "a tile holds whole warps of cells");
   static_assert(NC % WPT == 0 && K >= 1, "whole warp groups per tile");
   using L = Lattice<Q>;
@@ -121,8 +120,8 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
   constexpr int T = TC;
   constexpr int dim = L::kDim;
   constexpr uint32_t ROWB = T * sizeof(S);
-  constexpr uint32_t BOXB = TS::kPlanesPerBox * ROWB;
   constexpr uint32_t STAGEB = TS::kPlanes * ROWB;
+  static_assert(STAGEB % 16 == 0, "bulk copies move multiples of 16 bytes");
   constexpr uint64_t kLimitNs = 2000000000ull;
 
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -161,10 +160,8 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
         }
         const uint32_t fb = smem_u32(&bars[s]);
         mbar_expect_tx(fb, STAGEB);
-        const uint32_t dst = smem_u32(stages + (size_t)s * STAGEB);
-#pragma unroll
-        for (int b = 0; b < TS::kBoxes; ++b)
-          tma_load_2d(dst + b * BOXB, &tmap, (int32_t)(tile * T), b * TS::kPlanesPerBox, fb);
+        bulk_load(smem_u32(stages + (size_t)s * STAGEB), a.fin + (size_t)tile * TS::kPlanes * T,
+                  STAGEB, fb);
         issued = j + 1;
       }
       // Leave only when every copy this warp started has landed: the last
@@ -187,8 +184,6 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
   const int half = warp % WPT;
   const int ci = half * CPW + (P == 2 ? (lane & 15) : lane);
   const int64_t cells = a.G.cells;
-  const int64_t ps = a.G.pstride;
-  const uint32_t ps32 = (uint32_t)ps;
   for (int64_t m = 0;; ++m) {
     const int64_t j = grp + m * NP;
     if (j >= my) break;
@@ -199,10 +194,6 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
     const bool valid = cell < cells;
     const int64_t c = valid ? cell : cells - 1;
     const Nbr n = make_nbr(a.G, c);
-    // destination offset of each velocity inside a field's block of planes
-    uint32_t woff[Q];
-#pragma unroll
-    for (int l = 0; l < Q; ++l) woff[l] = write_off<Q, LAYOUT>(n, ps32, l);
     // stencil loads first: their latency overlaps the wait for the stage
     C A[3], D[3][6];
     derivatives<Q, C>(n, cells, a.aux, a.inv2dx, a.inv4dx, A, D);
@@ -217,11 +208,10 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
 #pragma unroll
     for (int jj = 0; jj < NJ; ++jj) {
       const int F = g ? field_of(P, 1, jj) : field_of(P, 0, jj);
-      const S* row = st + (F * Q) * T + ci;
       C sum = C(0);
 #pragma unroll
       for (int l = 0; l < Q; ++l) {
-        const C v = (C)row[l * T];
+        const C v = (C)st[(l * kNF + F) * T + ci];
         sum += REP == kDEV ? C(L::w(l)) * v : v;
       }
       mine[jj] = sum;
@@ -275,11 +265,9 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
 #pragma unroll
         for (int k = 0; k < dim; ++k) b[k] = three_omega * (g ? Fl[F1 - kK][k] : Fl[F0 - kK][k]);
       }
-      const S* row = st + (F * Q) * T + ci;
-      S* ob = a.fout + field_base<Q>(F, ps);
 #pragma unroll
       for (int l = 0; l < Q; ++l) {
-        const C v = (C)row[l * T];
+        const C v = (C)st[(l * kNF + F) * T + ci];
         C t = cf;
         if (has_flux(F0)) {
 #pragma unroll
@@ -289,7 +277,7 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
           }
         }
         const C out = REP == kDEV ? fma(a.omc, v, t) : fma(a.omc, v, C(L::w(l)) * t);
-        Codec<S>::store_if(ob + woff[l], out, valid);
+        Codec<S>::store_if(a.fout + write_index<Q, LAYOUT>(n, F, l), out, valid);
       }
     }
     __syncwarp();

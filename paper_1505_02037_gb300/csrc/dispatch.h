@@ -8,12 +8,12 @@
 namespace lbnr {
 
 constexpr uint64_t kStageBytes = 1ull << 20;
-constexpr int64_t kTile = 32;  // plane padding: a multiple of every TMA tile width
+constexpr int64_t kTile = 32;  // cells per tile of the tile-blocked distribution layout
 
 struct LaunchCtx {
   int32_t nx, ny, nz;
   int64_t cells;
-  int64_t pstride;  // distribution plane stride: cells rounded up to kTile
+  int64_t pstride;  // cells rounded up to whole tiles (kTile)
   double dx, dt, tau;
   int slicing, sources_on;
   void* aux;        // 7 planes of the compute type (stencil input)

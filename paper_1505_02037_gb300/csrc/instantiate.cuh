@@ -2,7 +2,6 @@
 #pragma once
 
 #include "dispatch.h"
-#include <cudaTypedefs.h>
 
 #include "collide_tma.cuh"
 #include "kernels.cuh"
@@ -13,9 +12,10 @@ namespace lbnr {
 // kind 0: one thread block per 128 threads, P threads per cell; HOLD keeps a
 //         thread's distributions in registers between the moment pass and
 //         the update pass (else they are read again, from cache). Any layout.
-// kind 1: TMA-fed persistent kernel (collide_tma.cuh) with NC consumer warps
-//         and NS shared-memory stages; local reads only, so at the odd AA
-//         step it hands over to the form named by `fallback`.
+// kind 1: bulk-copy-fed persistent kernel (collide_tma.cuh) with NC consumer
+//         warps and NS shared-memory stages of one 32-cell tile; local reads
+//         only, so at the odd AA step it hands over to the form named by
+//         `fallback`.
 struct VariantSpec {
   int kind, P;
   bool hold;
@@ -51,44 +51,6 @@ LBNR_VARIANTS(9, 2, 2, {1, 1, false, 8, 2, 32}, {1, 2, false, 8, 3, 32}, {0, 1, 
 LBNR_VARIANTS(19, 2, 2, {1, 2, false, 8, 2, 32}, {1, 1, false, 8, 1, 32},
               {0, 1, false, 0, 0, 0}, {0, 2, false, 0, 0, 0}, {0, 2, true, 0, 0, 0})
 #undef LBNR_VARIANTS
-
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no
-// link-time dependency on libcuda).
-inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
-template <class S>
-constexpr CUtensorMapDataType tma_dtype() {
-  return sizeof(S) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
-                        : (sizeof(S) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                          : CU_TENSOR_MAP_DATA_TYPE_UINT16);
-}
-
-// 2D view of a distribution buffer: x = cell (stride 1), y = plane
-// (stride pstride); boxes of tile_cells x (planes per box).
-template <int Q, class S>
-cudaError_t encode_planes(const void* base, int64_t pstride, int tile_cells, CUtensorMap* map) {
-  auto fn = tensor_map_encoder();
-  if (!fn) return cudaErrorNotSupported;
-  const cuuint64_t dims[2] = {(cuuint64_t)pstride, (cuuint64_t)TmaShape<Q>::kPlanes};
-  const cuuint64_t strides[1] = {(cuuint64_t)pstride * sizeof(S)};
-  const cuuint32_t box[2] = {(cuuint32_t)tile_cells, (cuuint32_t)TmaShape<Q>::kPlanesPerBox};
-  const cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, tma_dtype<S>(), 2, const_cast<void*>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                  CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
 
 inline int sm_count() {
   static int n = 0;
@@ -168,7 +130,7 @@ struct Impl {
     constexpr VariantSpec x = VT::v[VI];
     constexpr int NC = x.nc > 0 ? x.nc : 1;
     constexpr int K = x.k > 0 ? x.k : 1;
-    constexpr int TC = x.tc > 0 ? x.tc : 16;
+    constexpr int TC = x.tc > 0 ? x.tc : kTileCells;
     constexpr int P = x.P;
     constexpr int NS = NC / (TC / (32 / P)) * K;
     constexpr uint32_t smem = tma_smem_bytes(tma_stage_bytes<S>(Q, TC), NS);
@@ -176,12 +138,9 @@ struct Impl {
     auto kern = k_collide_tma<Q, S, C, REP, LAYOUT, NC, K, TC, P>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    CUtensorMap map;
-    e = encode_planes<Q, S>(a.fin, L.pstride, TC, &map);
-    if (e != cudaSuccess) return e;
     const int64_t ntiles = L.pstride / TC;
     const int64_t grid = ntiles < sm_count() ? ntiles : sm_count();
-    kern<<<(unsigned)grid, 32 * (NC + 1), smem, L.st>>>(a, map, ntiles);
+    kern<<<(unsigned)grid, 32 * (NC + 1), smem, L.st>>>(a, ntiles);
     return cudaGetLastError();
   }
 
