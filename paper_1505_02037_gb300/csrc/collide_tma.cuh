@@ -117,6 +117,9 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
   static_assert(NC % WPT == 0 && K >= 1, "whole warp groups per tile");
   using L = Lattice<Q>;
   using TS = TmaShape<Q>;
+  // 16-bit storage, one lane per cell: whole words (two fields) at a time
+  constexpr bool WORDS = P == 1 && Codec<S>::kV == 2;
+  using W = typename Codec<S>::W;
   constexpr int T = TC;
   constexpr int dim = L::kDim;
   constexpr uint32_t ROWB = T * sizeof(S);
@@ -205,16 +208,33 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
 
     // moments of this lane's fields
     C mine[NJ];
+    if constexpr (WORDS) {
+      // one 32-bit word, two fields, per shared-memory read
 #pragma unroll
-    for (int jj = 0; jj < NJ; ++jj) {
-      const int F = g ? field_of(P, 1, jj) : field_of(P, 0, jj);
-      C sum = C(0);
+      for (int m = 0; m < NJ / 2; ++m) {
+        C s0 = C(0), s1 = C(0);
 #pragma unroll
-      for (int l = 0; l < Q; ++l) {
-        const C v = (C)st[(l * kNF + F) * T + ci];
-        sum += REP == kDEV ? C(L::w(l)) * v : v;
+        for (int l = 0; l < Q; ++l) {
+          C v[2];
+          Codec<S>::unpack(*reinterpret_cast<const W*>(st + fidx<Q, S>((uint32_t)ci, 2 * m, l)), v);
+          s0 += REP == kDEV ? C(L::w(l)) * v[0] : v[0];
+          s1 += REP == kDEV ? C(L::w(l)) * v[1] : v[1];
+        }
+        mine[2 * m] = s0;
+        mine[2 * m + 1] = s1;
       }
-      mine[jj] = sum;
+    } else {
+#pragma unroll
+      for (int jj = 0; jj < NJ; ++jj) {
+        const int F = g ? field_of(P, 1, jj) : field_of(P, 0, jj);
+        C sum = C(0);
+#pragma unroll
+        for (int l = 0; l < Q; ++l) {
+          const C v = (C)st[fidx<Q, S>((uint32_t)ci, F, l)];
+          sum += REP == kDEV ? C(L::w(l)) * v : v;
+        }
+        mine[jj] = sum;
+      }
     }
     C rt[kNF];
 #pragma unroll
@@ -255,29 +275,62 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
     }
     const C three_omega = C(3) * a.omega;
 
+    if constexpr (WORDS) {
 #pragma unroll
-    for (int jj = 0; jj < NJ; ++jj) {
-      const int F0 = field_of(P, 0, jj), F1 = field_of(P, 1, jj);
-      const int F = g ? F1 : F0;
-      const C cf = a.omega * (g ? rho[F1] : rho[F0]) + a.sigma * (g ? Sr[F1] : Sr[F0]);
-      C b[3] = {C(0), C(0), C(0)};
-      if (has_flux(F0)) {
+      for (int m = 0; m < NJ / 2; ++m) {
+        C cf[2], b[2][3];
 #pragma unroll
-        for (int k = 0; k < dim; ++k) b[k] = three_omega * (g ? Fl[F1 - kK][k] : Fl[F0 - kK][k]);
+        for (int i = 0; i < 2; ++i) {
+          const int F = 2 * m + i;
+          cf[i] = a.omega * rho[F] + a.sigma * Sr[F];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) b[i][k] = has_flux(F) ? three_omega * Fl[F - kK][k] : C(0);
+        }
+#pragma unroll
+        for (int l = 0; l < Q; ++l) {
+          C v[2], out[2];
+          Codec<S>::unpack(*reinterpret_cast<const W*>(st + fidx<Q, S>((uint32_t)ci, 2 * m, l)), v);
+#pragma unroll
+          for (int i = 0; i < 2; ++i) {
+            C t = cf[i];
+            if (has_flux(2 * m + i)) {
+#pragma unroll
+              for (int k = 0; k < dim; ++k) {
+                if (L::c(l, k) > 0) t += b[i][k];
+                if (L::c(l, k) < 0) t -= b[i][k];
+              }
+            }
+            out[i] = REP == kDEV ? fma(a.omc, v[i], t) : fma(a.omc, v[i], C(L::w(l)) * t);
+          }
+          WordIO<S>::stw_if(a.fout + write_index<Q, LAYOUT, S>(n, 2 * m, l), Codec<S>::pack(out),
+                            valid);
+        }
       }
+    } else {
 #pragma unroll
-      for (int l = 0; l < Q; ++l) {
-        const C v = (C)st[(l * kNF + F) * T + ci];
-        C t = cf;
+      for (int jj = 0; jj < NJ; ++jj) {
+        const int F0 = field_of(P, 0, jj), F1 = field_of(P, 1, jj);
+        const int F = g ? F1 : F0;
+        const C cf = a.omega * (g ? rho[F1] : rho[F0]) + a.sigma * (g ? Sr[F1] : Sr[F0]);
+        C b[3] = {C(0), C(0), C(0)};
         if (has_flux(F0)) {
 #pragma unroll
-          for (int k = 0; k < dim; ++k) {
-            if (L::c(l, k) > 0) t += b[k];
-            if (L::c(l, k) < 0) t -= b[k];
-          }
+          for (int k = 0; k < dim; ++k) b[k] = three_omega * (g ? Fl[F1 - kK][k] : Fl[F0 - kK][k]);
         }
-        const C out = REP == kDEV ? fma(a.omc, v, t) : fma(a.omc, v, C(L::w(l)) * t);
-        Codec<S>::store_if(a.fout + write_index<Q, LAYOUT>(n, F, l), out, valid);
+#pragma unroll
+        for (int l = 0; l < Q; ++l) {
+          const C v = (C)st[fidx<Q, S>((uint32_t)ci, F, l)];
+          C t = cf;
+          if (has_flux(F0)) {
+#pragma unroll
+            for (int k = 0; k < dim; ++k) {
+              if (L::c(l, k) > 0) t += b[k];
+              if (L::c(l, k) < 0) t -= b[k];
+            }
+          }
+          const C out = REP == kDEV ? fma(a.omc, v, t) : fma(a.omc, v, C(L::w(l)) * t);
+          Codec<S>::store_if(a.fout + write_index<Q, LAYOUT, S>(n, F, l), out, valid);
+        }
       }
     }
     __syncwarp();

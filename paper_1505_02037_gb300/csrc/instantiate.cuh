@@ -100,11 +100,19 @@ struct Impl {
     const int block = 128;
     const int64_t threads = P == 2 ? ((L.cells + 15) / 16) * 32 : L.cells;
     // the lagged-field writes cost registers: sized for 2 blocks per SM
-    if (a.aux_out)
-      k_collide<Q, S, C, REP, LAYOUT, P, H, 0, 2, true>
-          <<<grid_for(threads, block), block, 0, L.st>>>(a);
-    else
-      k_collide<Q, S, C, REP, LAYOUT, P, H><<<grid_for(threads, block), block, 0, L.st>>>(a);
+    if constexpr (P == 1 && Codec<S>::kV == 2) {
+      // 16-bit storage, one thread per cell: word by word
+      if (a.aux_out)
+        k_collide_w<Q, S, C, REP, LAYOUT, H, 2, true><<<grid_for(threads, block), block, 0, L.st>>>(a);
+      else
+        k_collide_w<Q, S, C, REP, LAYOUT, H><<<grid_for(threads, block), block, 0, L.st>>>(a);
+    } else {
+      if (a.aux_out)
+        k_collide<Q, S, C, REP, LAYOUT, P, H, 0, 2, true>
+            <<<grid_for(threads, block), block, 0, L.st>>>(a);
+      else
+        k_collide<Q, S, C, REP, LAYOUT, P, H><<<grid_for(threads, block), block, 0, L.st>>>(a);
+    }
     return cudaGetLastError();
   }
 

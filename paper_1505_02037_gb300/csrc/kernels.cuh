@@ -46,6 +46,9 @@ template <class S>
 struct Codec;
 template <>
 struct Codec<double> {
+  // one value per distribution word (see the layout below)
+  static constexpr int kV = 1;
+  using W = double;
   __device__ static __forceinline__ double load(const double* p) { return __ldcs(p); }
   __device__ static __forceinline__ double load_keep(const double* p) { return __ldg(p); }
   __device__ static __forceinline__ double load_coh(const double* p) { return __ldcg(p); }
@@ -59,6 +62,8 @@ struct Codec<double> {
 };
 template <>
 struct Codec<float> {
+  static constexpr int kV = 1;
+  using W = float;
   __device__ static __forceinline__ float load(const float* p) { return __ldcs(p); }
   __device__ static __forceinline__ float load_keep(const float* p) { return __ldg(p); }
   __device__ static __forceinline__ float load_coh(const float* p) { return __ldcg(p); }
@@ -71,6 +76,17 @@ struct Codec<float> {
 };
 template <>
 struct Codec<__nv_bfloat16> {
+  // two values per word: fields 2m (low half) and 2m + 1 (high half)
+  static constexpr int kV = 2;
+  using W = uint32_t;
+  __device__ static __forceinline__ void unpack(W w, float* v) {
+    v[0] = __uint_as_float(w << 16);  // bfloat16 -> float is exact: the top half of the float
+    v[1] = __uint_as_float(w & 0xffff0000u);
+  }
+  __device__ static __forceinline__ W pack(const float* v) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v[0], v[1]);
+    return (W)__bfloat16_as_ushort(h.x) | ((W)__bfloat16_as_ushort(h.y) << 16);
+  }
   __device__ static __forceinline__ float load(const __nv_bfloat16* p) {
     return __bfloat162float(__ldcs(p));
   }
@@ -92,6 +108,16 @@ struct Codec<__nv_bfloat16> {
 };
 template <>
 struct Codec<__half> {
+  static constexpr int kV = 2;
+  using W = uint32_t;
+  __device__ static __forceinline__ void unpack(W w, float* v) {
+    v[0] = __half2float(__ushort_as_half((unsigned short)(w & 0xffffu)));
+    v[1] = __half2float(__ushort_as_half((unsigned short)(w >> 16)));
+  }
+  __device__ static __forceinline__ W pack(const float* v) {
+    const __half2 h = __floats2half2_rn(v[0], v[1]);
+    return (W)__half_as_ushort(h.x) | ((W)__half_as_ushort(h.y) << 16);
+  }
   __device__ static __forceinline__ float load(const __half* p) { return __half2float(__ldcs(p)); }
   __device__ static __forceinline__ float load_keep(const __half* p) {
     return __half2float(__ldg(p));
@@ -102,6 +128,31 @@ struct Codec<__half> {
     const unsigned short b = __half_as_ushort(__float2half_rn(v));
     asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %2, 0;\n @p st.global.cs.b16 [%0], %1;\n}\n" ::"l"(p),
                  "h"(b), "r"((int)q)
+                 : "memory");
+  }
+};
+
+// Whole distribution words of the 16-bit storage types: ldw streams
+// (evict-first), ldw_keep takes the read-only path, ldw_coh reads coherently
+// through L2; stw streams a word out, stw_if under a predicate.
+template <class S>
+struct WordIO {
+  using W = uint32_t;
+  __device__ static __forceinline__ W ldw(const S* p) {
+    return __ldcs(reinterpret_cast<const unsigned int*>(p));
+  }
+  __device__ static __forceinline__ W ldw_keep(const S* p) {
+    return __ldg(reinterpret_cast<const unsigned int*>(p));
+  }
+  __device__ static __forceinline__ W ldw_coh(const S* p) {
+    return __ldcg(reinterpret_cast<const unsigned int*>(p));
+  }
+  __device__ static __forceinline__ void stw(S* p, W w) {
+    __stcs(reinterpret_cast<unsigned int*>(p), w);
+  }
+  __device__ static __forceinline__ void stw_if(S* p, W w, bool q) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %2, 0;\n @p st.global.cs.b32 [%0], %1;\n}\n" ::"l"(p),
+                 "r"(w), "r"((int)q)
                  : "memory");
   }
 };
@@ -184,11 +235,13 @@ __device__ __forceinline__ Nbr make_nbr(const Grid& G, int64_t c64) {
 
 // Distribution layout in HBM: tile-blocked. The 16 Q values of the 32
 // consecutive cells of a tile form one contiguous block, ordered by velocity,
-// then field, then cell: f_{F,l}(c) of a buffer sits at
-//   ((c / 32) 16 Q + l 16 + F) 32 + c % 32.
-// A warp's 32 cells of one (F, l) are one aligned 32-value row, the 16 fields
-// of one velocity are 16 consecutive rows, and a tile's whole state is one
-// block. With one plane per (F, l) instead (all cells of a plane contiguous),
+// then field word, then cell. A word holds kV consecutive fields of one
+// (cell, velocity): kV = 2 for 16-bit storage (fields 2m, 2m+1 side by side in
+// 32 bits), else 1. With W = 16 / kV words per velocity, f_{F,l}(c) sits at
+//   (((c / 32) W Q + l W + F / kV) 32 + c % 32) kV + F % kV.
+// A warp's 32 cells of one (word, l) are one aligned row of 32 words, the
+// fields of one velocity are W consecutive rows, and a tile's whole state is
+// one block. With one plane per (F, l) instead (all cells of a plane contiguous),
 // the 600-odd tiles in flight on the GPU touch 16 Q separate DRAM regions
 // each, and the step ran 11 % slower (256^3 D3Q19 FP32 on GB300).
 constexpr int kTileCells = 32;
@@ -199,9 +252,11 @@ __device__ __forceinline__ void opaque(uint32_t (&v)[N]) {
 #pragma unroll
   for (int i = 0; i < N; ++i) asm volatile("" : "+r"(v[i]));
 }
-template <int Q>
+template <int Q, class S>
 __host__ __device__ __forceinline__ size_t fidx(uint32_t c, int F, int l) {
-  return ((size_t)(c >> 5) * (size_t)(kNF * Q) + (size_t)(l * kNF + F)) * kTileCells + (c & 31u);
+  constexpr int V = Codec<S>::kV;
+  return (((size_t)(c >> 5) * (size_t)(kNF / V * Q) + (size_t)(l * (kNF / V) + F / V)) * kTileCells +
+          (c & 31u)) * V + (size_t)(F % V);
 }
 // Where f_{F,l}(x) of the current state lives, for each streaming layout:
 // cell read_cell(l), velocity slot read_slot(l), the same for every field.
@@ -214,9 +269,9 @@ template <int LAYOUT>
 __host__ __device__ constexpr int read_slot(int l) {
   return LAYOUT == kAAOdd ? opposite(l) : l;
 }
-template <int Q, int LAYOUT>
+template <int Q, int LAYOUT, class S>
 __device__ __forceinline__ size_t read_index(const Nbr& n, int F, int l) {
-  return fidx<Q>(read_cell<Q, LAYOUT>(n, l), F, read_slot<LAYOUT>(l));
+  return fidx<Q, S>(read_cell<Q, LAYOUT>(n, l), F, read_slot<LAYOUT>(l));
 }
 // Where f*_{F,l}(x) goes.
 template <int Q, int LAYOUT>
@@ -228,9 +283,9 @@ template <int LAYOUT>
 __host__ __device__ constexpr int write_slot(int l) {
   return LAYOUT == kAAEven ? opposite(l) : l;
 }
-template <int Q, int LAYOUT>
+template <int Q, int LAYOUT, class S>
 __device__ __forceinline__ size_t write_index(const Nbr& n, int F, int l) {
-  return fidx<Q>(write_cell<Q, LAYOUT>(n, l), F, write_slot<LAYOUT>(l));
+  return fidx<Q, S>(write_cell<Q, LAYOUT>(n, l), F, write_slot<LAYOUT>(l));
 }
 
 // ---------------------------------------------------------------------------
@@ -439,7 +494,7 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : MINB) k_collide(const StepArgs
     for (int l = 0; l < Q; ++l) {
       // In place (AA) the buffer is written by this kernel: re-read values
       // must come through coherent loads, never the read-only path.
-      const S* src = a.fin + fidx<Q>(rc[l], F, read_slot<LAYOUT>(l));
+      const S* src = a.fin + fidx<Q, S>(rc[l], F, read_slot<LAYOUT>(l));
       const C v = HOLD ? Codec<S>::load(src)
                   : LAYOUT == kPingPong ? Codec<S>::load_keep(src) : Codec<S>::load_coh(src);
       if (HOLD) fv[HOLD ? j : 0][HOLD ? l : 0] = v;
@@ -530,7 +585,7 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : MINB) k_collide(const StepArgs
     C v_[Q];
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
-      const S* src = a.fin + fidx<Q>(rc[l], F, read_slot<LAYOUT>(l));
+      const S* src = a.fin + fidx<Q, S>(rc[l], F, read_slot<LAYOUT>(l));
       // the second read is the last use: streaming (evict-first) load
       v_[l] = HOLD ? fv[HOLD ? j : 0][HOLD ? l : 0]
               : LAYOUT == kPingPong ? Codec<S>::load(src) : Codec<S>::load_coh(src);
@@ -571,11 +626,132 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : MINB) k_collide(const StepArgs
                                 : (kLeanRelax ? fma(a.omc, v, t) : fma(a.omc, v, C(L::w(l)) * t));
       // Ping-pong: lanes past the last cell were clamped to it and write the
       // same bytes as its own lanes, so every store can be unconditional.
-      S* dst = a.fout + fidx<Q>(wc[l], F, write_slot<LAYOUT>(l));
+      S* dst = a.fout + fidx<Q, S>(wc[l], F, write_slot<LAYOUT>(l));
       if (LAYOUT == kPingPong)
         Codec<S>::store(dst, out);
       else
         Codec<S>::store_if(dst, out, valid);
+    }
+  }
+}
+
+// From one cell's zeroth moments rt and stencil derivatives A, D: the
+// sources S at rt, the corrected moments rho = rt + dt/2 S (the moment rule
+// of the forced scheme) and the fluxes at rho.
+template <int Q, class S, class C, int REP>
+__device__ __forceinline__ void cell_terms(const StepArgs<S, C>& a, const C rt[kNF], const C A[3],
+                                           const C D[3][6], C rho[kNF], C Sr[kNF], C Fl[6][3]) {
+  constexpr int dim = Lattice<Q>::kDim;
+  C alpha, gm[6], K[6], V[3];
+  unpack<REP, C>(rt, alpha, gm, K, V);
+  bm_sources<C>(alpha, gm, K, V, A, D, a.slicing, Sr);
+  add_fluid(a, alpha, gm, Sr);
+  if (!a.sources_on) {
+#pragma unroll
+    for (int F = 0; F < kNF; ++F) Sr[F] = C(0);
+  }
+#pragma unroll
+  for (int F = 0; F < kNF; ++F) rho[F] = rt[F] + a.half_dt * Sr[F];
+  C alpha2, g2[6], K2[6], V2[3];
+  unpack<REP, C>(rho, alpha2, g2, K2, V2);
+  bm_flux<C, dim>(alpha2, g2, V2, A, D, Fl);
+}
+
+// ---------------------------------------------------------------------------
+// k_collide_w: one thread per cell for 16-bit storage, word by word
+// ---------------------------------------------------------------------------
+// The step of k_collide (P = 1, no shift) with every load and store moving a
+// whole 32-bit word, fields 2m and 2m + 1 of one (cell, velocity): half the
+// memory instructions of value-by-value access. HOLD keeps the 8 Q words of
+// a cell in registers between the passes.
+template <int Q, class S, class C, int REP, int LAYOUT, bool HOLD, int MINB = 3, bool LAGW = false>
+__global__ void __launch_bounds__(128, HOLD ? 1 : MINB) k_collide_w(const StepArgs<S, C> a) {
+  using L = Lattice<Q>;
+  using IO = WordIO<S>;
+  using W = typename IO::W;
+  constexpr int V = Codec<S>::kV;
+  static_assert(V == 2, "word access is for 16-bit storage");
+  constexpr int NW = kNF / V;
+  const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = cell < a.G.cells;
+  const int64_t c = valid ? cell : a.G.cells - 1;
+  const int64_t cells = a.G.cells;
+  const Nbr n = make_nbr(a.G, c);
+
+  // Pass 1: zeroth moments, two fields per load (ascending l).
+  W hw[HOLD ? NW : 1][HOLD ? Q : 1];
+  C rt[kNF];
+#pragma unroll
+  for (int m = 0; m < NW; ++m) {
+    C s0 = C(0), s1 = C(0);
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+      // in place (AA) the buffer is written by this kernel: coherent loads
+      const S* src = a.fin + read_index<Q, LAYOUT, S>(n, V * m, l);
+      const W w = HOLD ? IO::ldw(src) : LAYOUT == kPingPong ? IO::ldw_keep(src) : IO::ldw_coh(src);
+      if (HOLD) hw[HOLD ? m : 0][HOLD ? l : 0] = w;
+      C v[2];
+      Codec<S>::unpack(w, v);
+      s0 += REP == kDEV ? C(L::w(l)) * v[0] : v[0];
+      s1 += REP == kDEV ? C(L::w(l)) * v[1] : v[1];
+    }
+    rt[V * m] = s0;
+    rt[V * m + 1] = s1;
+  }
+  {
+    C chk = C(0);
+#pragma unroll
+    for (int F = 0; F < kNF; ++F) chk += rt[F];
+    if (valid && !isfinite(chk)) atomicOr(a.flag, 1);
+  }
+
+  C A[3], D[3][6];
+  derivatives<Q, C>(n, cells, a.aux, a.inv2dx, a.inv4dx, A, D);
+  C rho[kNF], Sr[kNF], Fl[6][3];
+  cell_terms<Q, S, C, REP>(a, rt, A, D, rho, Sr, Fl);
+  if (LAGW && valid) write_lagged<REP, C>(a.aux_out, cells, n.c, rho);
+  const C three_omega = C(3) * a.omega;
+
+  // Pass 2: relax, add the source, stream; all Q words of a field pair are
+  // read before any is written (in place they share the Q locations).
+#pragma unroll
+  for (int m = 0; m < NW; ++m) {
+    W vw[Q];
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+      const S* src = a.fin + read_index<Q, LAYOUT, S>(n, V * m, l);
+      vw[l] = HOLD ? hw[HOLD ? m : 0][HOLD ? l : 0]
+              : LAYOUT == kPingPong ? IO::ldw(src) : IO::ldw_coh(src);
+    }
+    C cf[2], b[2][3];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int F = V * m + i;
+      cf[i] = a.omega * rho[F] + a.sigma * Sr[F];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) b[i][k] = has_flux(F) ? three_omega * Fl[F - kK][k] : C(0);
+    }
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+      C v[2], out[2];
+      Codec<S>::unpack(vw[l], v);
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        C t = cf[i];
+        if (has_flux(V * m + i)) {
+#pragma unroll
+          for (int k = 0; k < L::kDim; ++k) {
+            if (L::c(l, k) > 0) t += b[i][k];
+            if (L::c(l, k) < 0) t -= b[i][k];
+          }
+        }
+        out[i] = REP == kDEV ? fma(a.omc, v[i], t) : fma(a.omc, v[i], C(L::w(l)) * t);
+      }
+      S* dst = a.fout + write_index<Q, LAYOUT, S>(n, V * m, l);
+      if (LAYOUT == kPingPong)
+        IO::stw(dst, Codec<S>::pack(out));
+      else
+        IO::stw_if(dst, Codec<S>::pack(out), valid);
     }
   }
 }
@@ -594,7 +770,7 @@ __global__ void __launch_bounds__(256) k_aux(const S* __restrict__ f, C* __restr
     C s = C(0);
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
-      const C v = Codec<S>::load_keep(f + read_index<Q, LAYOUT>(n, F, l));
+      const C v = Codec<S>::load_keep(f + read_index<Q, LAYOUT, S>(n, F, l));
       s += REP == kDEV ? C(L::w(l)) * v : v;
     }
     if (F == 0) s = REP == kDEV ? log1p(s) : log(s);
@@ -618,7 +794,7 @@ __device__ __forceinline__ void aux_cell(const S* __restrict__ f, C* __restrict_
     C s = C(0);
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
-      const C v = Codec<S>::load_coh(f + read_index<Q, LAYOUT>(n, F, l));
+      const C v = Codec<S>::load_coh(f + read_index<Q, LAYOUT, S>(n, F, l));
       s += REP == kDEV ? C(L::w(l)) * v : v;
     }
     if (F == 0) s = REP == kDEV ? log1p(s) : log(s);
@@ -662,7 +838,7 @@ __device__ __forceinline__ void collide_cell(const StepArgs<S, C>& a, int64_t c)
     C s = C(0);
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
-      const C v = Codec<S>::load_coh(a.fin + read_index<Q, LAYOUT>(n, F, l));
+      const C v = Codec<S>::load_coh(a.fin + read_index<Q, LAYOUT, S>(n, F, l));
       s += REP == kDEV ? C(L::w(l)) * v : v;
     }
     rt[F] = s;
@@ -705,7 +881,7 @@ __device__ __forceinline__ void collide_cell(const StepArgs<S, C>& a, int64_t c)
     }
     C v_[Q];
 #pragma unroll
-    for (int l = 0; l < Q; ++l) v_[l] = Codec<S>::load_coh(a.fin + read_index<Q, LAYOUT>(n, F, l));
+    for (int l = 0; l < Q; ++l) v_[l] = Codec<S>::load_coh(a.fin + read_index<Q, LAYOUT, S>(n, F, l));
     // FP64: the same weight-first form as k_collide, so a batched run stays
     // bitwise equal to the run on its own context
     constexpr bool kLeanRelax = sizeof(C) == 8 && REP == kABS;
@@ -723,7 +899,7 @@ __device__ __forceinline__ void collide_cell(const StepArgs<S, C>& a, int64_t c)
       const C out = REP == kDEV ? fma(a.omc, v_[l], t)
                                 : (kLeanRelax ? fma(a.omc, v_[l], t)
                                               : fma(a.omc, v_[l], C(L::w(l)) * t));
-      Codec<S>::store(a.fout + write_index<Q, LAYOUT>(n, F, l), out);
+      Codec<S>::store(a.fout + write_index<Q, LAYOUT, S>(n, F, l), out);
     }
   }
 }
@@ -814,7 +990,7 @@ __global__ void __launch_bounds__(128) k_init(const Init64Args<S> a) {
       else
         v = L::w(l) * (r[F] + 3.0 * cf) - a.half_dt * L::w(l) * Sr[F];
       bad |= !isfinite(v);
-      Codec<S>::store(a.f + fidx<Q>((uint32_t)c, F, l), (decltype(Codec<S>::load(a.f)))v);
+      Codec<S>::store(a.f + fidx<Q, S>((uint32_t)c, F, l), (decltype(Codec<S>::load(a.f)))v);
     }
   }
   if (bad) atomicOr(a.flag, 1);
@@ -879,7 +1055,7 @@ __global__ void __launch_bounds__(256) k_sum64(const S* __restrict__ f, double* 
         float hi = 0.f, lo = 0.f;
 #pragma unroll
         for (int l = 0; l < Q; ++l) {
-          const float v = Codec<S>::load_keep(f + read_index<Q, LAYOUT>(n, F, l));
+          const float v = Codec<S>::load_keep(f + read_index<Q, LAYOUT, S>(n, F, l));
           const float t = __fadd_rn(hi, v);
           const float bp = __fsub_rn(t, hi);
           const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(v, bp));
@@ -891,7 +1067,7 @@ __global__ void __launch_bounds__(256) k_sum64(const S* __restrict__ f, double* 
 #pragma unroll
         for (int l = 0; l < Q; ++l) {
           const double v =
-              (double)Codec<S>::load_keep(f + read_index<Q, LAYOUT>(n, F, l));
+              (double)Codec<S>::load_keep(f + read_index<Q, LAYOUT, S>(n, F, l));
           s += REP == kDEV ? L::w(l) * v : v;
         }
       }
@@ -1147,7 +1323,7 @@ __global__ void k_get_plane(const S* __restrict__ f, double* __restrict__ out, G
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= G.cells) return;
   const Nbr n = make_nbr(G, c);
-  const double v = (double)Codec<S>::load_keep(f + read_index<Q, LAYOUT>(n, F, l));
+  const double v = (double)Codec<S>::load_keep(f + read_index<Q, LAYOUT, S>(n, F, l));
   double w = 0;
 #pragma unroll
   for (int ll = 0; ll < Q; ++ll)
@@ -1166,7 +1342,7 @@ __global__ void k_set_plane(S* __restrict__ f, const double* __restrict__ in, Gr
   for (int ll = 0; ll < Q; ++ll)
     if (ll == l) w = L::w(ll);
   const double v = REP == kDEV ? in[c] / w - flat_value(F) : in[c];
-  Codec<S>::store(f + read_index<Q, LAYOUT>(n, F, l), (decltype(Codec<S>::load(f)))v);
+  Codec<S>::store(f + read_index<Q, LAYOUT, S>(n, F, l), (decltype(Codec<S>::load(f)))v);
 }
 
 // Distributions of selected cells: out[i][F][l] = f_{F,l}(idx[i]) in FP64.
@@ -1181,7 +1357,7 @@ __global__ void k_get_cells(const S* __restrict__ f, const int64_t* __restrict__
   const Nbr nb = make_nbr(G, idx[i]);
 #pragma unroll
   for (int l = 0; l < Q; ++l) {
-    const double v = (double)Codec<S>::load_keep(f + read_index<Q, LAYOUT>(nb, F, l));
+    const double v = (double)Codec<S>::load_keep(f + read_index<Q, LAYOUT, S>(nb, F, l));
     out[(i * kNF + F) * Q + l] = REP == kDEV ? L::w(l) * (v + flat_value(F)) : v;
   }
 }
