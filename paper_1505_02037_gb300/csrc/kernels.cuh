@@ -31,6 +31,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "lattice.cuh"
 #include "physics.cuh"
 
@@ -62,8 +64,14 @@ struct Codec<double> {
 };
 template <>
 struct Codec<float> {
-  static constexpr int kV = 1;
-  using W = float;
+  // two values per word: fields 2m (.x) and 2m + 1 (.y)
+  static constexpr int kV = 2;
+  using W = float2;
+  __device__ static __forceinline__ void unpack(W w, float* v) {
+    v[0] = w.x;
+    v[1] = w.y;
+  }
+  __device__ static __forceinline__ W pack(const float* v) { return make_float2(v[0], v[1]); }
   __device__ static __forceinline__ float load(const float* p) { return __ldcs(p); }
   __device__ static __forceinline__ float load_keep(const float* p) { return __ldg(p); }
   __device__ static __forceinline__ float load_coh(const float* p) { return __ldcg(p); }
@@ -132,29 +140,39 @@ struct Codec<__half> {
   }
 };
 
-// Whole distribution words of the 16-bit storage types: ldw streams
-// (evict-first), ldw_keep takes the read-only path, ldw_coh reads coherently
-// through L2; stw streams a word out, stw_if under a predicate.
+// Whole distribution words (two values): ldw streams (evict-first),
+// ldw_keep takes the read-only path, ldw_coh reads coherently through L2;
+// stw streams a word out, stw_if under a predicate.
 template <class S>
 struct WordIO {
-  using W = uint32_t;
-  __device__ static __forceinline__ W ldw(const S* p) {
-    return __ldcs(reinterpret_cast<const unsigned int*>(p));
-  }
+  using W = typename Codec<S>::W;
+  static constexpr bool k64 = sizeof(W) == 8;  // FP32 pairs; else 16-bit pairs
+  using R = typename std::conditional<k64, float2, unsigned int>::type;
+  __device__ static __forceinline__ W ldw(const S* p) { return as_w(__ldcs(reinterpret_cast<const R*>(p))); }
   __device__ static __forceinline__ W ldw_keep(const S* p) {
-    return __ldg(reinterpret_cast<const unsigned int*>(p));
+    return as_w(__ldg(reinterpret_cast<const R*>(p)));
   }
   __device__ static __forceinline__ W ldw_coh(const S* p) {
-    return __ldcg(reinterpret_cast<const unsigned int*>(p));
+    return as_w(__ldcg(reinterpret_cast<const R*>(p)));
   }
-  __device__ static __forceinline__ void stw(S* p, W w) {
-    __stcs(reinterpret_cast<unsigned int*>(p), w);
-  }
+  __device__ static __forceinline__ void stw(S* p, W w) { __stcs(reinterpret_cast<R*>(p), as_r(w)); }
   __device__ static __forceinline__ void stw_if(S* p, W w, bool q) {
-    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %2, 0;\n @p st.global.cs.b32 [%0], %1;\n}\n" ::"l"(p),
-                 "r"(w), "r"((int)q)
-                 : "memory");
+    if constexpr (k64) {
+      const float2 r = as_r(w);
+      asm volatile(
+          "{\n .reg .pred p;\n setp.ne.b32 p, %3, 0;\n @p st.global.cs.v2.f32 [%0], {%1, %2};\n}\n" ::"l"(p),
+          "f"(r.x), "f"(r.y), "r"((int)q)
+          : "memory");
+    } else {
+      asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %2, 0;\n @p st.global.cs.b32 [%0], %1;\n}\n" ::"l"(p),
+                   "r"(as_r(w)), "r"((int)q)
+                   : "memory");
+    }
   }
+
+ private:
+  __device__ static __forceinline__ W as_w(R r) { return *reinterpret_cast<W*>(&r); }
+  __device__ static __forceinline__ R as_r(W w) { return *reinterpret_cast<R*>(&w); }
 };
 
 // Flat-space value of field F (alpha = 1, gamma = delta, K = V = 0).
@@ -670,7 +688,7 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : MINB) k_collide_w(const StepAr
   using IO = WordIO<S>;
   using W = typename IO::W;
   constexpr int V = Codec<S>::kV;
-  static_assert(V == 2, "word access is for 16-bit storage");
+  static_assert(V == 2, "word access is for two-value words");
   constexpr int NW = kNF / V;
   const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = cell < a.G.cells;
