@@ -117,8 +117,9 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
   static_assert(NC % WPT == 0 && K >= 1, "whole warp groups per tile");
   using L = Lattice<Q>;
   using TS = TmaShape<Q>;
-  // 16-bit storage, one lane per cell: whole words (two fields) at a time
-  constexpr bool WORDS = P == 1 && Codec<S>::kV == 2;
+  // one lane per cell: whole words (kV fields) at a time
+  constexpr int VW = Codec<S>::kV;  // fields per word
+  constexpr bool WORDS = P == 1 && VW > 1;
   using W = typename Codec<S>::W;
   constexpr int T = TC;
   constexpr int dim = L::kDim;
@@ -209,19 +210,21 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
     // moments of this lane's fields
     C mine[NJ];
     if constexpr (WORDS) {
-      // one 32-bit word, two fields, per shared-memory read
+      // one word, kV fields, per shared-memory read
 #pragma unroll
-      for (int m = 0; m < NJ / 2; ++m) {
-        C s0 = C(0), s1 = C(0);
+      for (int m = 0; m < NJ / VW; ++m) {
+        C sum[VW];
+#pragma unroll
+        for (int i = 0; i < VW; ++i) sum[i] = C(0);
 #pragma unroll
         for (int l = 0; l < Q; ++l) {
-          C v[2];
-          Codec<S>::unpack(*reinterpret_cast<const W*>(st + fidx<Q, S>((uint32_t)ci, 2 * m, l)), v);
-          s0 += REP == kDEV ? C(L::w(l)) * v[0] : v[0];
-          s1 += REP == kDEV ? C(L::w(l)) * v[1] : v[1];
+          C v[VW];
+          Codec<S>::unpack(*reinterpret_cast<const W*>(st + fidx<Q, S>((uint32_t)ci, VW * m, l)), v);
+#pragma unroll
+          for (int i = 0; i < VW; ++i) sum[i] += REP == kDEV ? C(L::w(l)) * v[i] : v[i];
         }
-        mine[2 * m] = s0;
-        mine[2 * m + 1] = s1;
+#pragma unroll
+        for (int i = 0; i < VW; ++i) mine[VW * m + i] = sum[i];
       }
     } else {
 #pragma unroll
@@ -277,23 +280,23 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
 
     if constexpr (WORDS) {
 #pragma unroll
-      for (int m = 0; m < NJ / 2; ++m) {
-        C cf[2], b[2][3];
+      for (int m = 0; m < NJ / VW; ++m) {
+        C cf[VW], b[VW][3];
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
-          const int F = 2 * m + i;
+        for (int i = 0; i < VW; ++i) {
+          const int F = VW * m + i;
           cf[i] = a.omega * rho[F] + a.sigma * Sr[F];
 #pragma unroll
           for (int k = 0; k < 3; ++k) b[i][k] = has_flux(F) ? three_omega * Fl[F - kK][k] : C(0);
         }
 #pragma unroll
         for (int l = 0; l < Q; ++l) {
-          C v[2], out[2];
-          Codec<S>::unpack(*reinterpret_cast<const W*>(st + fidx<Q, S>((uint32_t)ci, 2 * m, l)), v);
+          C v[VW], out[VW];
+          Codec<S>::unpack(*reinterpret_cast<const W*>(st + fidx<Q, S>((uint32_t)ci, VW * m, l)), v);
 #pragma unroll
-          for (int i = 0; i < 2; ++i) {
+          for (int i = 0; i < VW; ++i) {
             C t = cf[i];
-            if (has_flux(2 * m + i)) {
+            if (has_flux(VW * m + i)) {
 #pragma unroll
               for (int k = 0; k < dim; ++k) {
                 if (L::c(l, k) > 0) t += b[i][k];
@@ -302,7 +305,7 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
             }
             out[i] = REP == kDEV ? fma(a.omc, v[i], t) : fma(a.omc, v[i], C(L::w(l)) * t);
           }
-          WordIO<S>::stw_if(a.fout + write_index<Q, LAYOUT, S>(n, 2 * m, l), Codec<S>::pack(out),
+          WordIO<S>::stw_if(a.fout + write_index<Q, LAYOUT, S>(n, VW * m, l), Codec<S>::pack(out),
                             valid);
         }
       }

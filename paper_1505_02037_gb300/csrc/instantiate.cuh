@@ -100,8 +100,8 @@ struct Impl {
     const int block = 128;
     const int64_t threads = P == 2 ? ((L.cells + 15) / 16) * 32 : L.cells;
     // the lagged-field writes cost registers: sized for 2 blocks per SM
-    if constexpr (P == 1 && Codec<S>::kV == 2) {
-      // 16-bit storage, one thread per cell: word by word
+    if constexpr (P == 1 && Codec<S>::kV > 1) {
+      // one thread per cell, word by word
       if (a.aux_out)
         k_collide_w<Q, S, C, REP, LAYOUT, H, 2, true><<<grid_for(threads, block), block, 0, L.st>>>(a);
       else

@@ -64,14 +64,16 @@ struct Codec<double> {
 };
 template <>
 struct Codec<float> {
-  // two values per word: fields 2m (.x) and 2m + 1 (.y)
-  static constexpr int kV = 2;
-  using W = float2;
+  // four values per word: fields 4m .. 4m + 3 (.x .. .w)
+  static constexpr int kV = 4;
+  using W = float4;
   __device__ static __forceinline__ void unpack(W w, float* v) {
     v[0] = w.x;
     v[1] = w.y;
+    v[2] = w.z;
+    v[3] = w.w;
   }
-  __device__ static __forceinline__ W pack(const float* v) { return make_float2(v[0], v[1]); }
+  __device__ static __forceinline__ W pack(const float* v) { return make_float4(v[0], v[1], v[2], v[3]); }
   __device__ static __forceinline__ float load(const float* p) { return __ldcs(p); }
   __device__ static __forceinline__ float load_keep(const float* p) { return __ldg(p); }
   __device__ static __forceinline__ float load_coh(const float* p) { return __ldcg(p); }
@@ -84,16 +86,21 @@ struct Codec<float> {
 };
 template <>
 struct Codec<__nv_bfloat16> {
-  // two values per word: fields 2m (low half) and 2m + 1 (high half)
-  static constexpr int kV = 2;
-  using W = uint32_t;
+  // four values per word: fields 4m .. 4m + 3, lowest half first
+  static constexpr int kV = 4;
+  using W = uint2;
   __device__ static __forceinline__ void unpack(W w, float* v) {
-    v[0] = __uint_as_float(w << 16);  // bfloat16 -> float is exact: the top half of the float
-    v[1] = __uint_as_float(w & 0xffff0000u);
+    // bfloat16 -> float is exact: the top half of the float
+    v[0] = __uint_as_float(w.x << 16);
+    v[1] = __uint_as_float(w.x & 0xffff0000u);
+    v[2] = __uint_as_float(w.y << 16);
+    v[3] = __uint_as_float(w.y & 0xffff0000u);
   }
   __device__ static __forceinline__ W pack(const float* v) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(v[0], v[1]);
-    return (W)__bfloat16_as_ushort(h.x) | ((W)__bfloat16_as_ushort(h.y) << 16);
+    const __nv_bfloat162 h0 = __floats2bfloat162_rn(v[0], v[1]);
+    const __nv_bfloat162 h1 = __floats2bfloat162_rn(v[2], v[3]);
+    return make_uint2((uint32_t)__bfloat16_as_ushort(h0.x) | ((uint32_t)__bfloat16_as_ushort(h0.y) << 16),
+                      (uint32_t)__bfloat16_as_ushort(h1.x) | ((uint32_t)__bfloat16_as_ushort(h1.y) << 16));
   }
   __device__ static __forceinline__ float load(const __nv_bfloat16* p) {
     return __bfloat162float(__ldcs(p));
@@ -116,15 +123,19 @@ struct Codec<__nv_bfloat16> {
 };
 template <>
 struct Codec<__half> {
-  static constexpr int kV = 2;
-  using W = uint32_t;
+  static constexpr int kV = 4;
+  using W = uint2;
   __device__ static __forceinline__ void unpack(W w, float* v) {
-    v[0] = __half2float(__ushort_as_half((unsigned short)(w & 0xffffu)));
-    v[1] = __half2float(__ushort_as_half((unsigned short)(w >> 16)));
+    v[0] = __half2float(__ushort_as_half((unsigned short)(w.x & 0xffffu)));
+    v[1] = __half2float(__ushort_as_half((unsigned short)(w.x >> 16)));
+    v[2] = __half2float(__ushort_as_half((unsigned short)(w.y & 0xffffu)));
+    v[3] = __half2float(__ushort_as_half((unsigned short)(w.y >> 16)));
   }
   __device__ static __forceinline__ W pack(const float* v) {
-    const __half2 h = __floats2half2_rn(v[0], v[1]);
-    return (W)__half_as_ushort(h.x) | ((W)__half_as_ushort(h.y) << 16);
+    const __half2 h0 = __floats2half2_rn(v[0], v[1]);
+    const __half2 h1 = __floats2half2_rn(v[2], v[3]);
+    return make_uint2((uint32_t)__half_as_ushort(h0.x) | ((uint32_t)__half_as_ushort(h0.y) << 16),
+                      (uint32_t)__half_as_ushort(h1.x) | ((uint32_t)__half_as_ushort(h1.y) << 16));
   }
   __device__ static __forceinline__ float load(const __half* p) { return __half2float(__ldcs(p)); }
   __device__ static __forceinline__ float load_keep(const __half* p) {
@@ -145,34 +156,25 @@ struct Codec<__half> {
 // stw streams a word out, stw_if under a predicate.
 template <class S>
 struct WordIO {
-  using W = typename Codec<S>::W;
-  static constexpr bool k64 = sizeof(W) == 8;  // FP32 pairs; else 16-bit pairs
-  using R = typename std::conditional<k64, float2, unsigned int>::type;
-  __device__ static __forceinline__ W ldw(const S* p) { return as_w(__ldcs(reinterpret_cast<const R*>(p))); }
-  __device__ static __forceinline__ W ldw_keep(const S* p) {
-    return as_w(__ldg(reinterpret_cast<const R*>(p)));
-  }
-  __device__ static __forceinline__ W ldw_coh(const S* p) {
-    return as_w(__ldcg(reinterpret_cast<const R*>(p)));
-  }
-  __device__ static __forceinline__ void stw(S* p, W w) { __stcs(reinterpret_cast<R*>(p), as_r(w)); }
+  using W = typename Codec<S>::W;  // float4 (FP32) or uint2 (16-bit)
+  __device__ static __forceinline__ W ldw(const S* p) { return __ldcs(reinterpret_cast<const W*>(p)); }
+  __device__ static __forceinline__ W ldw_keep(const S* p) { return __ldg(reinterpret_cast<const W*>(p)); }
+  __device__ static __forceinline__ W ldw_coh(const S* p) { return __ldcg(reinterpret_cast<const W*>(p)); }
+  __device__ static __forceinline__ void stw(S* p, W w) { __stcs(reinterpret_cast<W*>(p), w); }
   __device__ static __forceinline__ void stw_if(S* p, W w, bool q) {
-    if constexpr (k64) {
-      const float2 r = as_r(w);
+    if constexpr (sizeof(W) == 16) {
       asm volatile(
-          "{\n .reg .pred p;\n setp.ne.b32 p, %3, 0;\n @p st.global.cs.v2.f32 [%0], {%1, %2};\n}\n" ::"l"(p),
-          "f"(r.x), "f"(r.y), "r"((int)q)
+          "{\n .reg .pred p;\n setp.ne.b32 p, %5, 0;\n"
+          " @p st.global.cs.v4.f32 [%0], {%1, %2, %3, %4};\n}\n" ::"l"(p),
+          "f"(w.x), "f"(w.y), "f"(w.z), "f"(w.w), "r"((int)q)
           : "memory");
     } else {
-      asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %2, 0;\n @p st.global.cs.b32 [%0], %1;\n}\n" ::"l"(p),
-                   "r"(as_r(w)), "r"((int)q)
-                   : "memory");
+      asm volatile(
+          "{\n .reg .pred p;\n setp.ne.b32 p, %3, 0;\n @p st.global.cs.v2.b32 [%0], {%1, %2};\n}\n" ::"l"(p),
+          "r"(w.x), "r"(w.y), "r"((int)q)
+          : "memory");
     }
   }
-
- private:
-  __device__ static __forceinline__ W as_w(R r) { return *reinterpret_cast<W*>(&r); }
-  __device__ static __forceinline__ R as_r(W w) { return *reinterpret_cast<R*>(&w); }
 };
 
 // Flat-space value of field F (alpha = 1, gamma = delta, K = V = 0).
@@ -688,7 +690,7 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : MINB) k_collide_w(const StepAr
   using IO = WordIO<S>;
   using W = typename IO::W;
   constexpr int V = Codec<S>::kV;
-  static_assert(V == 2, "word access is for two-value words");
+  static_assert(V > 1 && kNF % V == 0, "word access: several fields per word");
   constexpr int NW = kNF / V;
   const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = cell < a.G.cells;
@@ -701,20 +703,22 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : MINB) k_collide_w(const StepAr
   C rt[kNF];
 #pragma unroll
   for (int m = 0; m < NW; ++m) {
-    C s0 = C(0), s1 = C(0);
+    C sum[V];
+#pragma unroll
+    for (int i = 0; i < V; ++i) sum[i] = C(0);
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
       // in place (AA) the buffer is written by this kernel: coherent loads
       const S* src = a.fin + read_index<Q, LAYOUT, S>(n, V * m, l);
       const W w = HOLD ? IO::ldw(src) : LAYOUT == kPingPong ? IO::ldw_keep(src) : IO::ldw_coh(src);
       if (HOLD) hw[HOLD ? m : 0][HOLD ? l : 0] = w;
-      C v[2];
+      C v[V];
       Codec<S>::unpack(w, v);
-      s0 += REP == kDEV ? C(L::w(l)) * v[0] : v[0];
-      s1 += REP == kDEV ? C(L::w(l)) * v[1] : v[1];
+#pragma unroll
+      for (int i = 0; i < V; ++i) sum[i] += REP == kDEV ? C(L::w(l)) * v[i] : v[i];
     }
-    rt[V * m] = s0;
-    rt[V * m + 1] = s1;
+#pragma unroll
+    for (int i = 0; i < V; ++i) rt[V * m + i] = sum[i];
   }
   {
     C chk = C(0);
@@ -741,9 +745,9 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : MINB) k_collide_w(const StepAr
       vw[l] = HOLD ? hw[HOLD ? m : 0][HOLD ? l : 0]
               : LAYOUT == kPingPong ? IO::ldw(src) : IO::ldw_coh(src);
     }
-    C cf[2], b[2][3];
+    C cf[V], b[V][3];
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < V; ++i) {
       const int F = V * m + i;
       cf[i] = a.omega * rho[F] + a.sigma * Sr[F];
 #pragma unroll
@@ -751,10 +755,10 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : MINB) k_collide_w(const StepAr
     }
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
-      C v[2], out[2];
+      C v[V], out[V];
       Codec<S>::unpack(vw[l], v);
 #pragma unroll
-      for (int i = 0; i < 2; ++i) {
+      for (int i = 0; i < V; ++i) {
         C t = cf[i];
         if (has_flux(V * m + i)) {
 #pragma unroll
