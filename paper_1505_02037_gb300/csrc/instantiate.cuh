@@ -99,14 +99,15 @@ struct Impl {
     constexpr bool H = x.hold;
     const int block = 128;
     const int64_t threads = P == 2 ? ((L.cells + 15) / 16) * 32 : L.cells;
-    // the lagged-field writes cost registers: sized for 2 blocks per SM
     if constexpr (P == 1 && Codec<S>::kV > 1) {
-      // one thread per cell, word by word
+      // one thread per cell, word by word (3 blocks per SM with or without
+      // the lagged-field writes)
       if (a.aux_out)
-        k_collide_w<Q, S, C, REP, LAYOUT, H, 2, true><<<grid_for(threads, block), block, 0, L.st>>>(a);
+        k_collide_w<Q, S, C, REP, LAYOUT, H, 3, true><<<grid_for(threads, block), block, 0, L.st>>>(a);
       else
         k_collide_w<Q, S, C, REP, LAYOUT, H><<<grid_for(threads, block), block, 0, L.st>>>(a);
     } else {
+      // the lagged-field writes cost registers: sized for 2 blocks per SM
       if (a.aux_out)
         k_collide<Q, S, C, REP, LAYOUT, P, H, 0, 2, true>
             <<<grid_for(threads, block), block, 0, L.st>>>(a);

@@ -810,18 +810,29 @@ template <int Q, class S, class C, int REP, int LAYOUT>
 __device__ __forceinline__ void aux_cell(const S* __restrict__ f, C* __restrict__ aux,
                                          const Grid& G, int64_t c) {
   using L = Lattice<Q>;
+  constexpr int V = Codec<S>::kV;
+  constexpr int NW = (7 + V - 1) / V;  // the words holding fields 0..6
   const Nbr n = make_nbr(G, c);
+  C s[NW * V];
 #pragma unroll
-  for (int F = 0; F < 7; ++F) {
-    C s = C(0);
+  for (int F = 0; F < NW * V; ++F) s[F] = C(0);
+#pragma unroll
+  for (int m = 0; m < NW; ++m) {
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
-      const C v = Codec<S>::load_coh(f + read_index<Q, LAYOUT, S>(n, F, l));
-      s += REP == kDEV ? C(L::w(l)) * v : v;
+      const S* src = f + read_index<Q, LAYOUT, S>(n, V * m, l);
+      C v[V];
+      if constexpr (V > 1)
+        Codec<S>::unpack(WordIO<S>::ldw_coh(src), v);
+      else
+        v[0] = Codec<S>::load_coh(src);
+#pragma unroll
+      for (int i = 0; i < V; ++i) s[V * m + i] += REP == kDEV ? C(L::w(l)) * v[i] : v[i];
     }
-    if (F == 0) s = REP == kDEV ? log1p(s) : log(s);
-    aux[(int64_t)F * G.cells + c] = s;
   }
+  s[0] = REP == kDEV ? log1p(s[0]) : log(s[0]);
+#pragma unroll
+  for (int F = 0; F < 7; ++F) aux[(int64_t)F * G.cells + c] = s[F];
 }
 
 template <int Q, class C>
@@ -853,17 +864,24 @@ __device__ __forceinline__ void collide_cell(const StepArgs<S, C>& a, int64_t c)
   using L = Lattice<Q>;
   constexpr int dim = L::kDim;
   const int64_t cells = a.G.cells;
+  constexpr int VW = Codec<S>::kV;  // fields per distribution word
   const Nbr n = make_nbr(a.G, c);
   C rt[kNF];
 #pragma unroll
-  for (int F = 0; F < kNF; ++F) {
-    C s = C(0);
+  for (int F = 0; F < kNF; ++F) rt[F] = C(0);
+#pragma unroll
+  for (int m = 0; m < kNF / VW; ++m) {
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
-      const C v = Codec<S>::load_coh(a.fin + read_index<Q, LAYOUT, S>(n, F, l));
-      s += REP == kDEV ? C(L::w(l)) * v : v;
+      const S* src = a.fin + read_index<Q, LAYOUT, S>(n, VW * m, l);
+      C v[VW];
+      if constexpr (VW > 1)
+        Codec<S>::unpack(WordIO<S>::ldw_coh(src), v);
+      else
+        v[0] = Codec<S>::load_coh(src);
+#pragma unroll
+      for (int i = 0; i < VW; ++i) rt[VW * m + i] += REP == kDEV ? C(L::w(l)) * v[i] : v[i];
     }
-    rt[F] = s;
   }
   {
     C chk = C(0);
@@ -893,35 +911,76 @@ __device__ __forceinline__ void collide_cell(const StepArgs<S, C>& a, int64_t c)
     bm_flux<C, dim>(alpha2, g2, V2, A, D, Fl);
   }
   const C three_omega = C(3) * a.omega;
+  // FP64: the same weight-first form as k_collide, so a batched run stays
+  // bitwise equal to the run on its own context
+  constexpr bool kLeanRelax = sizeof(C) == 8 && REP == kABS;
+  if constexpr (VW == 1) {
+    // value by value, in k_collide's own expression form (the compiler
+    // contracts products into fused multiply-adds the same way in both)
 #pragma unroll
-  for (int F = 0; F < kNF; ++F) {
-    const C cf = a.omega * rho[F] + a.sigma * Sr[F];
-    C b[3] = {C(0), C(0), C(0)};
-    if (has_flux(F)) {
-#pragma unroll
-      for (int k = 0; k < dim; ++k) b[k] = three_omega * Fl[F - kK][k];
-    }
-    C v_[Q];
-#pragma unroll
-    for (int l = 0; l < Q; ++l) v_[l] = Codec<S>::load_coh(a.fin + read_index<Q, LAYOUT, S>(n, F, l));
-    // FP64: the same weight-first form as k_collide, so a batched run stays
-    // bitwise equal to the run on its own context
-    constexpr bool kLeanRelax = sizeof(C) == 8 && REP == kABS;
-#pragma unroll
-    for (int l = 0; l < Q; ++l) {
-      C t = kLeanRelax ? C(L::w(l)) * cf : cf;
+    for (int F = 0; F < kNF; ++F) {
+      const C cf = a.omega * rho[F] + a.sigma * Sr[F];
+      C b[3] = {C(0), C(0), C(0)};
       if (has_flux(F)) {
 #pragma unroll
-        for (int k = 0; k < dim; ++k) {
-          const C bk = kLeanRelax ? C(L::w(l)) * b[k] : b[k];
-          if (L::c(l, k) > 0) t += bk;
-          if (L::c(l, k) < 0) t -= bk;
-        }
+        for (int k = 0; k < dim; ++k) b[k] = three_omega * Fl[F - kK][k];
       }
-      const C out = REP == kDEV ? fma(a.omc, v_[l], t)
-                                : (kLeanRelax ? fma(a.omc, v_[l], t)
-                                              : fma(a.omc, v_[l], C(L::w(l)) * t));
-      Codec<S>::store(a.fout + write_index<Q, LAYOUT, S>(n, F, l), out);
+      C v_[Q];
+#pragma unroll
+      for (int l = 0; l < Q; ++l) v_[l] = Codec<S>::load_coh(a.fin + read_index<Q, LAYOUT, S>(n, F, l));
+#pragma unroll
+      for (int l = 0; l < Q; ++l) {
+        C t = kLeanRelax ? C(L::w(l)) * cf : cf;
+        if (has_flux(F)) {
+#pragma unroll
+          for (int k = 0; k < dim; ++k) {
+            const C bk = kLeanRelax ? C(L::w(l)) * b[k] : b[k];
+            if (L::c(l, k) > 0) t += bk;
+            if (L::c(l, k) < 0) t -= bk;
+          }
+        }
+        const C out = REP == kDEV ? fma(a.omc, v_[l], t)
+                                  : (kLeanRelax ? fma(a.omc, v_[l], t)
+                                                : fma(a.omc, v_[l], C(L::w(l)) * t));
+        Codec<S>::store(a.fout + write_index<Q, LAYOUT, S>(n, F, l), out);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < kNF / VW; ++m) {
+      C cf[VW], b[VW][3];
+#pragma unroll
+      for (int i = 0; i < VW; ++i) {
+        const int F = VW * m + i;
+        cf[i] = a.omega * rho[F] + a.sigma * Sr[F];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) b[i][k] = has_flux(F) ? three_omega * Fl[F - kK][k] : C(0);
+      }
+      typename Codec<S>::W vw[Q];
+#pragma unroll
+      for (int l = 0; l < Q; ++l) {
+        const S* src = a.fin + read_index<Q, LAYOUT, S>(n, VW * m, l);
+        vw[l] = WordIO<S>::ldw_coh(src);
+      }
+#pragma unroll
+      for (int l = 0; l < Q; ++l) {
+        C v[VW], out[VW];
+        Codec<S>::unpack(vw[l], v);
+#pragma unroll
+        for (int i = 0; i < VW; ++i) {
+          C t = cf[i];
+          if (has_flux(VW * m + i)) {
+#pragma unroll
+            for (int k = 0; k < dim; ++k) {
+              if (L::c(l, k) > 0) t += b[i][k];
+              if (L::c(l, k) < 0) t -= b[i][k];
+            }
+          }
+          out[i] = REP == kDEV ? fma(a.omc, v[i], t) : fma(a.omc, v[i], C(L::w(l)) * t);
+        }
+        S* dst = a.fout + write_index<Q, LAYOUT, S>(n, VW * m, l);
+        WordIO<S>::stw(dst, Codec<S>::pack(out));
+      }
     }
   }
 }
