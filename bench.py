@@ -198,7 +198,7 @@ class ClockSampler:
 
 
 from paper_1505_02037_gb300.traffic_table import (  # noqa: E402
-    AD_SOURCES, COLLIDE_SOURCES, source_hash)
+    AD_SOURCES, BATCH_SOURCES, COLLIDE_SOURCES, source_hash)
 
 
 def _traffic_entry(kernel_key, files):
@@ -310,6 +310,15 @@ def run_reference(args):
 # Batched ensemble
 # ---------------------------------------------------------------------------
 ENSEMBLE_SEED = 150502037
+
+
+E2E_REPEATS = 3
+
+
+def median_of(fn, repeats=E2E_REPEATS):
+    """Median of `repeats` wall times from fn() (host-to-device bandwidth
+    from pinned memory varies from one copy to the next)."""
+    return statistics.median(fn() for _ in range(repeats))
 
 
 def batched_config(world_rank_seed_note=""):
@@ -511,22 +520,25 @@ def main_ad(args):
     }
     if not args.no_e2e:
         hf = torch.from_numpy(fields.copy()).pin_memory()
-        hout = np.empty((AD_NF, cells))
         k = args.steps
-        barrier()
-        t0 = time.perf_counter()
-        lat.init(hf.numpy())
-        lat.step(k)
-        try:
-            hout = lat.moments()
-        except lbnr.NonFiniteError:
-            pass
-        barrier()
-        el = time.perf_counter() - t0
-        el, u = over_ranks(el, cells * AD_NF * k, world, dev)
+
+        def once():
+            barrier()
+            t0 = time.perf_counter()
+            lat.init(hf.numpy())
+            lat.step(k)
+            try:
+                lat.moments()
+            except lbnr.NonFiniteError:
+                pass
+            barrier()
+            return time.perf_counter() - t0
+
+        el, u = over_ranks(median_of(once), cells * AD_NF * k, world, dev)
         line["e2e"] = {"value": u / el / 1e6, "unit": "Mcell*var/s",
                        "h2d_bytes_per_step": hf.numel() * 8 / k,
-                       "d2h_bytes_per_step": hout.size * 8 / k, "steps_per_transfer": k}
+                       "d2h_bytes_per_step": AD_NF * cells * 8 / k, "steps_per_transfer": k,
+                       "repeats": E2E_REPEATS, "statistic": "median wall time"}
     lat.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         value, done, el, cores = ad_oracle_rate(args, 48)
@@ -631,7 +643,12 @@ def main_batched(args):
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": f"hbm_gbs of {peak_kind}",
                      "algorithmic_bytes_per_cell_step": "2*16*Q*4 + 7*4 (LAG: 14*4), Q = 3 or 9",
-                     "avg_launch_ms": ms / (args.steps * sub), "traffic": None},
+                     "avg_launch_ms": ms / (args.steps * sub),
+                     # per-cell-step DRAM bytes of the same kernel on 16 D2Q9
+                     # 256^2 runs, scaled to this run's cell-steps per launch
+                     "traffic": traffic_for(f"k_batch:batched:{args.deriv}",
+                                            float(taken @ np.array(cells)) / (args.steps * sub),
+                                            BATCH_SOURCES)},
         "gpu_launches": args.steps * sub,
         "launch_form": f"block {plan['block']} x grid {plan['grid']}, "
                        f"graph={'yes' if plan['graphed'] else 'no'}, "
@@ -642,20 +659,24 @@ def main_batched(args):
     if not args.no_e2e:
         # through the public API from pinned host fields: init every run,
         # K launches, read back every run's status and step count
-        barrier()
-        t0 = time.perf_counter()
-        init_all()
-        for _ in range(args.steps * sub):
-            b.run()
-        rc2, per2 = b.status()
-        barrier()
-        el = time.perf_counter() - t0
+        def once():
+            barrier()
+            t0 = time.perf_counter()
+            init_all()
+            for _ in range(args.steps * sub):
+                b.run()
+            b.status()
+            barrier()
+            return time.perf_counter() - t0
+
+        el = median_of(once)
         taken2 = np.array([b.steps_done(i) for i in range(len(specs))], dtype=np.int64)
         u2 = float(sum(c * 16 * t for c, t in zip(cells, taken2)))
         el, u2 = over_ranks(el, u2, world, dev)
         line["e2e"] = {"value": u2 / el / 1e6, "unit": "Mcell*var/s",
                        "h2d_bytes_per_step": host.numel() * 8 / args.steps,
-                       "d2h_bytes_per_step": len(specs) * (4 + 8) / args.steps}
+                       "d2h_bytes_per_step": len(specs) * (4 + 8) / args.steps,
+                       "repeats": E2E_REPEATS, "statistic": "median wall time"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, sample = oracle_rate_on_ensemble(specs, 12.0)
         line["cpu_baseline"] = {"value": rate, "unit": "Mcell*var/s", "cores": cores,
@@ -709,6 +730,8 @@ def deriv_mode_records(args, line, fields, sync_ms, sync_col_ms, sync_aux_ms, vs
                 "k_collide_ms": col, "launch_form": lat.variants[lat.variant],
                 "collide_hbm_frac": alg / (col * 1e-3) / 1e9 / peak,
                 "algorithmic_bytes_per_cell": alg / cells,
+                "traffic": traffic_for(f"k_collide:{args.workload}-lag:{lat.variants[lat.variant]}",
+                                       cells),
                 "autotune_ms_per_collide": tuning},
         "note": "LAG takes A and D from the previous step's corrected alpha and gamma (the paper "
                 "is silent on the time level); both are first order",
@@ -912,21 +935,25 @@ def main():
         hf = torch.from_numpy(fields.copy()).pin_memory()
         hout = torch.empty((16, cells), dtype=torch.float64).pin_memory()
         k = args.steps
-        barrier()
-        t0 = time.perf_counter()
-        lat.init(hf)
-        lat.step(k)
-        try:
-            lat.moments(hout)
-        except lbnr.NonFiniteError:
-            pass
-        barrier()
-        el = time.perf_counter() - t0
-        el, u_e2e = over_ranks(el, cells * 16 * k, world, dev)
+
+        def once():
+            barrier()
+            t0 = time.perf_counter()
+            lat.init(hf)
+            lat.step(k)
+            try:
+                lat.moments(hout)
+            except lbnr.NonFiniteError:
+                pass
+            barrier()
+            return time.perf_counter() - t0
+
+        el, u_e2e = over_ranks(median_of(once), cells * 16 * k, world, dev)
         line["e2e"] = {"value": u_e2e / el / 1e6, "unit": "Mcell*var/s",
                        "h2d_bytes_per_step": hf.numel() * 8 / k,
                        "d2h_bytes_per_step": hout.numel() * 8 / k,
-                       "steps_per_transfer": k}
+                       "steps_per_transfer": k, "repeats": E2E_REPEATS,
+                       "statistic": "median wall time"}
 
     if not args.no_modes and not beta and len(WORKLOADS[args.workload]) <= 8:
         lat.close()

@@ -41,6 +41,8 @@ def main(argv=None):
                    help="the 37-field scheme (A_k and D_kij evolved); f64 or f32 storage")
     p.add_argument("--shift-field", type=float, default=0.0,
                    help="amplitude of a static shear shift field")
+    p.add_argument("--deriv", default="sync", choices=["sync", "lag"],
+                   help="time level of A and D (lag: one kernel per step)")
     a = p.parse_args(argv)
     if a.batch:
         return batch_main(a)
@@ -48,7 +50,8 @@ def main(argv=None):
         return ad_main(a)
     n = a.n
     shape = (n, n, n) if a.vset == 3 else ((n, n, 1) if a.vset == 2 else (n, 1, 1))
-    lat = lbnr.Lattice(a.vset, shape, a.tau, 1 / n, storage=a.storage, streaming=a.streaming)
+    lat = lbnr.Lattice(a.vset, shape, a.tau, 1 / n, storage=a.storage, streaming=a.streaming,
+                       deriv_mode=a.deriv)
     v = lat.variants.index(a.variant) if a.variant in lat.variants else (
         int(a.variant) if a.variant.isdigit() else -1)
     if not 0 <= v < len(lat.variants):
@@ -66,7 +69,7 @@ def main(argv=None):
     ms = lat.step_timed(4)
     form = ("P1-reread-shiftfield" if a.shift_field else
             "P1-reread-shift" if beta else lat.variants[v])
-    print(f"{a.storage} n={n} vset={a.vset} {form}: "
+    print(f"{a.storage} n={n} vset={a.vset} {form} ({a.deriv}): "
           f"ms per step aux {ms[0] / 4:.4f} collide {ms[1] / 4:.4f}")
     return 0
 
@@ -93,7 +96,8 @@ def batch_main(a):
     shape = (n, n, 1) if a.vset == 2 else (n, 1, 1)
     runs = [dict(vset=a.vset, shape=shape, tau=2.0, dx=1 / n, steps=a.steps)
             for _ in range(a.batch)]
-    b = lbnr.Batch(runs, storage=a.storage, block=a.block, ctas_per_sm=a.per_sm)
+    b = lbnr.Batch(runs, storage=a.storage, block=a.block, ctas_per_sm=a.per_sm,
+                   deriv_mode=a.deriv)
     f = W.gauge_wave(shape, 1 / n, 0.01)
     for i in range(a.batch):
         b.init(i, f)
@@ -109,7 +113,7 @@ def batch_main(a):
             times.append(e0.elapsed_time(e1))
     b.check()
     p = b.plan()
-    print(f"batch {a.batch} x {shape} {a.storage}: grid {p['grid']} x {p['block']}, "
+    print(f"batch {a.batch} x {shape} {a.storage} ({a.deriv}): grid {p['grid']} x {p['block']}, "
           f"ms per launch of {a.steps} steps: " + " ".join(f"{t:.3f}" for t in times))
     return 0
 
