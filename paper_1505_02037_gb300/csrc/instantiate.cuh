@@ -117,20 +117,31 @@ struct Impl {
     return cudaGetLastError();
   }
 
-  // Registers of the shift forms: sized for 2 blocks of 128 threads per SM
-  // in FP32 arithmetic (255 registers, next to no spill: 9.6 against 10.7 ms
-  // for 3 blocks with 180 B spilled, 256^3 FP32 on GB300) and 3 in FP64
-  // (the FP64 step is bound by its arithmetic; 8.9 against 9.3 ms at 128^3).
+  // Registers of the shift forms. FP64 (value by value): 3 blocks of 128
+  // threads per SM (the FP64 step is bound by its arithmetic; 8.9 against
+  // 9.3 ms at 128^3). FP32 and 16-bit storage (word by word): 3 blocks with
+  // a constant shift, which fits 168 registers without spills in ping-pong,
+  // and 2 with a shift field (255 registers; 3 would spill).
   template <int LAYOUT, int SHIFT>
   static cudaError_t launch_shifted(const LaunchCtx& L, const StepArgs<S, C>& a) {
     constexpr int MINB = sizeof(C) == 8 ? 3 : 2;
+    constexpr int WMINB = SHIFT == 1 ? 3 : 2;
     const int block = 128;
-    if (a.aux_out)
-      k_collide<Q, S, C, REP, LAYOUT, 1, false, SHIFT, MINB, true>
-          <<<grid_for(L.cells, block), block, 0, L.st>>>(a);
-    else
-      k_collide<Q, S, C, REP, LAYOUT, 1, false, SHIFT, MINB>
-          <<<grid_for(L.cells, block), block, 0, L.st>>>(a);
+    if constexpr (Codec<S>::kV > 1) {
+      if (a.aux_out)
+        k_collide_w<Q, S, C, REP, LAYOUT, false, WMINB, true, SHIFT>
+            <<<grid_for(L.cells, block), block, 0, L.st>>>(a);
+      else
+        k_collide_w<Q, S, C, REP, LAYOUT, false, WMINB, false, SHIFT>
+            <<<grid_for(L.cells, block), block, 0, L.st>>>(a);
+    } else {
+      if (a.aux_out)
+        k_collide<Q, S, C, REP, LAYOUT, 1, false, SHIFT, MINB, true>
+            <<<grid_for(L.cells, block), block, 0, L.st>>>(a);
+      else
+        k_collide<Q, S, C, REP, LAYOUT, 1, false, SHIFT, MINB>
+            <<<grid_for(L.cells, block), block, 0, L.st>>>(a);
+    }
     return cudaGetLastError();
   }
 

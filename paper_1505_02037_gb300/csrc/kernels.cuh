@@ -657,15 +657,25 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : MINB) k_collide(const StepArgs
 
 // From one cell's zeroth moments rt and stencil derivatives A, D: the
 // sources S at rt, the corrected moments rho = rt + dt/2 S (the moment rule
-// of the forced scheme) and the fluxes at rho.
-template <int Q, class S, class C, int REP>
-__device__ __forceinline__ void cell_terms(const StepArgs<S, C>& a, const C rt[kNF], const C A[3],
-                                           const C D[3][6], C rho[kNF], C Sr[kNF], C Fl[6][3]) {
+// of the forced scheme) and the fluxes at rho. SHIFT = 1 adds the terms of a
+// constant shift a.beta, SHIFT = 2 those of the static shift field (with its
+// B_k^i) and the V fluxes -beta^k V_i it gives (Fv).
+template <int Q, class S, class C, int REP, int SHIFT = 0>
+__device__ __forceinline__ void cell_terms(const StepArgs<S, C>& a, const Nbr& n, const C rt[kNF],
+                                           const C A[3], const C D[3][6], C rho[kNF], C Sr[kNF],
+                                           C Fl[6][3], C Fv[3][3]) {
   constexpr int dim = Lattice<Q>::kDim;
   C alpha, gm[6], K[6], V[3];
   unpack<REP, C>(rt, alpha, gm, K, V);
   bm_sources<C>(alpha, gm, K, V, A, D, a.slicing, Sr);
   add_fluid(a, alpha, gm, Sr);
+  C sb[3], sB[3][3];  // shift and B_k^i at this cell (SHIFT = 2)
+  if (SHIFT == 1) shift_sources<C>(a.beta, alpha, A, D, Sr);
+  if (SHIFT == 2) {
+    shift_field_at<Q, C>(n, a.G.cells, a.beta_field, a.beta, (double)a.inv4dx, sb, sB);
+    shift_sources<C>(sb, alpha, A, D, Sr);
+    shift_field_sources<C>(gm, K, V, D, sB, Sr);
+  }
   if (!a.sources_on) {
 #pragma unroll
     for (int F = 0; F < kNF; ++F) Sr[F] = C(0);
@@ -675,16 +685,24 @@ __device__ __forceinline__ void cell_terms(const StepArgs<S, C>& a, const C rt[k
   C alpha2, g2[6], K2[6], V2[3];
   unpack<REP, C>(rho, alpha2, g2, K2, V2);
   bm_flux<C, dim>(alpha2, g2, V2, A, D, Fl);
+  if (SHIFT == 1) shift_flux_k<C, dim>(a.beta, K2, Fl);
+  if (SHIFT == 2) {
+    shift_flux_k<C, dim>(sb, K2, Fl);
+    shift_field_vflux<C, dim>(g2, V2, sb, sB, Fv);
+  }
 }
 
 // ---------------------------------------------------------------------------
 // k_collide_w: one thread per cell for 16-bit storage, word by word
 // ---------------------------------------------------------------------------
-// The step of k_collide (P = 1, no shift) with every load and store moving a
-// whole 32-bit word, fields 2m and 2m + 1 of one (cell, velocity): half the
-// memory instructions of value-by-value access. HOLD keeps the 8 Q words of
-// a cell in registers between the passes.
-template <int Q, class S, class C, int REP, int LAYOUT, bool HOLD, int MINB = 3, bool LAGW = false>
+// The step of k_collide with P = 1 and every load and store moving a whole
+// word of kV consecutive fields of one (cell, velocity): a kV-th of the
+// memory instructions of value-by-value access. HOLD keeps the words of a
+// cell in registers between the passes. SHIFT as in k_collide: 1 a constant
+// shift, 2 a static shift field; under a shift the V fields take the flux
+// -beta^k V_i at the corrected moments.
+template <int Q, class S, class C, int REP, int LAYOUT, bool HOLD, int MINB = 3, bool LAGW = false,
+          int SHIFT = 0>
 __global__ void __launch_bounds__(128, HOLD ? 1 : MINB) k_collide_w(const StepArgs<S, C> a) {
   using L = Lattice<Q>;
   using IO = WordIO<S>;
@@ -729,8 +747,8 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : MINB) k_collide_w(const StepAr
 
   C A[3], D[3][6];
   derivatives<Q, C>(n, cells, a.aux, a.inv2dx, a.inv4dx, A, D);
-  C rho[kNF], Sr[kNF], Fl[6][3];
-  cell_terms<Q, S, C, REP>(a, rt, A, D, rho, Sr, Fl);
+  C rho[kNF], Sr[kNF], Fl[6][3], Fv[3][3];
+  cell_terms<Q, S, C, REP, SHIFT>(a, n, rt, A, D, rho, Sr, Fl, Fv);
   if (LAGW && valid) write_lagged<REP, C>(a.aux_out, cells, n.c, rho);
   const C three_omega = C(3) * a.omega;
 
@@ -751,7 +769,12 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : MINB) k_collide_w(const StepAr
       const int F = V * m + i;
       cf[i] = a.omega * rho[F] + a.sigma * Sr[F];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) b[i][k] = has_flux(F) ? three_omega * Fl[F - kK][k] : C(0);
+      for (int k = 0; k < 3; ++k) {
+        C bk = has_flux(F) ? three_omega * Fl[F - kK][k] : C(0);
+        if (SHIFT == 1 && is_v(F)) bk = -three_omega * rho[F] * a.beta[k];
+        if (SHIFT == 2 && is_v(F)) bk = three_omega * Fv[SHIFT == 2 && is_v(F) ? F - kV : 0][k];
+        b[i][k] = bk;
+      }
     }
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
@@ -760,7 +783,7 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : MINB) k_collide_w(const StepAr
 #pragma unroll
       for (int i = 0; i < V; ++i) {
         C t = cf[i];
-        if (has_flux(V * m + i)) {
+        if (has_flux(V * m + i) || (SHIFT && is_v(V * m + i))) {
 #pragma unroll
           for (int k = 0; k < L::kDim; ++k) {
             if (L::c(l, k) > 0) t += b[i][k];
