@@ -100,12 +100,15 @@ struct Impl {
     const int block = 128;
     const int64_t threads = P == 2 ? ((L.cells + 15) / 16) * 32 : L.cells;
     if constexpr (P == 1 && Codec<S>::kV > 1) {
-      // one thread per cell, word by word (3 blocks per SM with or without
-      // the lagged-field writes)
+      // one thread per cell, word by word: 3 blocks per SM with or without
+      // the lagged-field writes; 2 at the odd AA step, which holds a field
+      // group's Q words and reads and writes at neighbours
+      constexpr int WMINB = LAYOUT == kAAOdd ? 2 : 3;
       if (a.aux_out)
-        k_collide_w<Q, S, C, REP, LAYOUT, H, 3, true><<<grid_for(threads, block), block, 0, L.st>>>(a);
+        k_collide_w<Q, S, C, REP, LAYOUT, H, WMINB, true>
+            <<<grid_for(threads, block), block, 0, L.st>>>(a);
       else
-        k_collide_w<Q, S, C, REP, LAYOUT, H><<<grid_for(threads, block), block, 0, L.st>>>(a);
+        k_collide_w<Q, S, C, REP, LAYOUT, H, WMINB><<<grid_for(threads, block), block, 0, L.st>>>(a);
     } else {
       // the lagged-field writes cost registers: sized for 2 blocks per SM
       if (a.aux_out)
@@ -120,12 +123,12 @@ struct Impl {
   // Registers of the shift forms. FP64 (value by value): 3 blocks of 128
   // threads per SM (the FP64 step is bound by its arithmetic; 8.9 against
   // 9.3 ms at 128^3). FP32 and 16-bit storage (word by word): 3 blocks with
-  // a constant shift, which fits 168 registers without spills in ping-pong,
-  // and 2 with a shift field (255 registers; 3 would spill).
+  // a constant shift, which fits 168 registers without spills outside the
+  // odd AA step, else 2 (255 registers; 3 would spill).
   template <int LAYOUT, int SHIFT>
   static cudaError_t launch_shifted(const LaunchCtx& L, const StepArgs<S, C>& a) {
     constexpr int MINB = sizeof(C) == 8 ? 3 : 2;
-    constexpr int WMINB = SHIFT == 1 ? 3 : 2;
+    constexpr int WMINB = SHIFT == 1 && LAYOUT != kAAOdd ? 3 : 2;
     const int block = 128;
     if constexpr (Codec<S>::kV > 1) {
       if (a.aux_out)
