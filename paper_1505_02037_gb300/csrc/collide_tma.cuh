@@ -4,16 +4,15 @@
 //
 // One persistent CTA per SM. Warp NC (the producer) streams tiles of 32
 // consecutive cells into a ring of NS shared-memory stages: in the
-// tile-blocked layout a tile's 16 Q rows of 32 values are one contiguous
+// tile-blocked layout a tile's 16 Q rows of 32 words are one contiguous
 // block, and the whole stage arrives through one bulk copy (cp.async.bulk)
-// that signals a "full" mbarrier. Consumer warps
-// 0..NC-1 each take whole tiles: two lanes per cell, each lane owning 8 of
-// the 16 fields. A consumer sums its moments from shared memory, swaps them
-// with its partner lane, evaluates the Bona-Masso sources and fluxes, then
-// relaxes and streams every value of the tile straight from shared memory to
-// the destination buffer and releases the stage through an "empty" mbarrier.
-// Registers only carry the physics, so occupancy no longer depends on the
-// 304 distributions of a D3Q19 cell.
+// that signals a "full" mbarrier. Consumer warps 0..NC-1 each take whole
+// tiles, one lane per cell: a lane sums its cell's 16 moments from shared
+// memory (one word of kV fields per read), evaluates the Bona-Masso sources
+// and fluxes, then relaxes and streams every value of the cell straight from
+// shared memory to the destination buffer; the warp then releases the stage
+// through an "empty" mbarrier. Registers only carry the physics, so
+// occupancy does not depend on the 16 Q distributions of a cell.
 //
 // Reads must be local (ping-pong, or AA at an even step): the stage holds
 // the planes of the tile's own cells. Every wait is bounded: after ~2 s the
@@ -93,33 +92,22 @@ __host__ __device__ constexpr uint32_t tma_smem_bytes(uint32_t stage_bytes, int 
   return 1024u + stage_bytes * (uint32_t)NS;
 }
 
-// TC = 32 cells per tile; P lanes per cell (P = 2: each lane owns 8
-// fields and partner lanes swap moments; P = 1: one lane per cell, all 16
-// fields). A tile is consumed by WPT = TC / (32/P) warps together (a group);
-// there are NP = NC/WPT groups, and each group owns K
-// consecutive stages of the ring (NS = NP*K). Tile j of this CTA goes to
-// group j % NP as its m-th tile (m = j / NP) and lands in the group's stage
-// m % K, round m / K. Every stage is therefore filled and consumed in round
-// order by one group, so a parity wait can never mistake an older phase for
-// the awaited one.
-template <int Q, class S, class C, int REP, int LAYOUT, int NC, int K, int TC, int P>
+// NC consumer warps, each owning K consecutive stages of the ring (NS =
+// NC K); TC = 32 cells per tile. Tile j of this CTA goes to warp j % NC as
+// its m-th tile (m = j / NC) and lands in the warp's stage m % K, round
+// m / K. Every stage is therefore filled and consumed in round order by one
+// warp, so a parity wait can never mistake an older phase for the awaited
+// one.
+template <int Q, class S, class C, int REP, int LAYOUT, int NC, int K, int TC>
 __global__ void __launch_bounds__(32 * (NC + 1), 1)
     k_collide_tma(const StepArgs<S, C> a, int64_t ntiles) {
   static_assert(LAYOUT == kPingPong || LAYOUT == kAAEven, "reads must be local");
-  static_assert(P == 1 || P == 2, "one or two lanes per cell");
-  constexpr int CPW = 32 / P;    // cells per consumer warp
-  constexpr int NJ = kNF / P;    // fields per lane
-  constexpr int WPT = TC / CPW;  // warps per tile
-  constexpr int NP = NC / WPT;
-  constexpr int NS = NP * K;
   static_assert(TC == kTileCells, "a stage is one tile of the tile-blocked layout");
-  static_assert(TC % CPW == 0, "a tile holds whole warps of cells");
-  static_assert(NC % WPT == 0 && K >= 1, "whole warp groups per tile");
+  static_assert(K >= 1, "at least one stage per consumer warp");
+  constexpr int NS = NC * K;
   using L = Lattice<Q>;
   using TS = TmaShape<Q>;
-  // one lane per cell: whole words (kV fields) at a time
   constexpr int VW = Codec<S>::kV;  // fields per word
-  constexpr bool WORDS = P == 1 && VW > 1;
   using W = typename Codec<S>::W;
   constexpr int T = TC;
   constexpr int dim = L::kDim;
@@ -136,7 +124,7 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) {
       mbar_init(smem_u32(&bars[s]), 1);
-      mbar_init(smem_u32(&bars[NS + s]), WPT);
+      mbar_init(smem_u32(&bars[NS + s]), 1);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -150,8 +138,8 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
     if (lane == 0) {
       int64_t issued = 0;
       for (int64_t j = 0; j < my; ++j) {
-        const int64_t m = j / NP;
-        const int s = (int)(j % NP) * K + (int)(m % K);
+        const int64_t m = j / NC;
+        const int s = (int)(j % NC) * K + (int)(m % K);
         const int64_t r = m / K;
         if (r >= 1 && !mbar_wait(smem_u32(&bars[NS + s]), (uint32_t)((r - 1) & 1), kLimitNs)) {
           atomicOr(a.flag, 2);
@@ -171,8 +159,8 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
       // Leave only when every copy this warp started has landed: the last
       // fill of each stage is among the last NS tiles issued.
       for (int64_t j = issued > NS ? issued - NS : 0; j < issued; ++j) {
-        const int64_t m = j / NP;
-        const int s = (int)(j % NP) * K + (int)(m % K);
+        const int64_t m = j / NC;
+        const int s = (int)(j % NC) * K + (int)(m % K);
         if (!mbar_wait(smem_u32(&bars[s]), (uint32_t)((m / K) & 1), kLimitNs)) {
           atomicOr(a.flag, 2);
           break;
@@ -182,19 +170,15 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
     return;
   }
 
-  // ---------------- consumers ----------------
-  const int g = P == 2 ? (lane >> 4) : 0;
-  const int grp = warp / WPT;
-  const int half = warp % WPT;
-  const int ci = half * CPW + (P == 2 ? (lane & 15) : lane);
+  // ---------------- consumers: one lane per cell ----------------
   const int64_t cells = a.G.cells;
   for (int64_t m = 0;; ++m) {
-    const int64_t j = grp + m * NP;
+    const int64_t j = warp + m * NC;
     if (j >= my) break;
-    const int s = grp * K + (int)(m % K);
+    const int s = warp * K + (int)(m % K);
     const uint32_t ph = (uint32_t)((m / K) & 1);
     const int64_t tile = blockIdx.x + j * G;
-    const int64_t cell = tile * T + ci;
+    const int64_t cell = tile * T + lane;
     const bool valid = cell < cells;
     const int64_t c = valid ? cell : cells - 1;
     const Nbr n = make_nbr(a.G, c);
@@ -207,133 +191,59 @@ __global__ void __launch_bounds__(32 * (NC + 1), 1)
     }
     const S* st = reinterpret_cast<const S*>(stages + (size_t)s * STAGEB);
 
-    // moments of this lane's fields
-    C mine[NJ];
-    if constexpr (WORDS) {
-      // one word, kV fields, per shared-memory read
-#pragma unroll
-      for (int m = 0; m < NJ / VW; ++m) {
-        C sum[VW];
-#pragma unroll
-        for (int i = 0; i < VW; ++i) sum[i] = C(0);
-#pragma unroll
-        for (int l = 0; l < Q; ++l) {
-          C v[VW];
-          Codec<S>::unpack(*reinterpret_cast<const W*>(st + fidx<Q, S>((uint32_t)ci, VW * m, l)), v);
-#pragma unroll
-          for (int i = 0; i < VW; ++i) sum[i] += REP == kDEV ? C(L::w(l)) * v[i] : v[i];
-        }
-#pragma unroll
-        for (int i = 0; i < VW; ++i) mine[VW * m + i] = sum[i];
-      }
-    } else {
-#pragma unroll
-      for (int jj = 0; jj < NJ; ++jj) {
-        const int F = g ? field_of(P, 1, jj) : field_of(P, 0, jj);
-        C sum = C(0);
-#pragma unroll
-        for (int l = 0; l < Q; ++l) {
-          const C v = (C)st[fidx<Q, S>((uint32_t)ci, F, l)];
-          sum += REP == kDEV ? C(L::w(l)) * v : v;
-        }
-        mine[jj] = sum;
-      }
-    }
+    // zeroth moments, one word (kV fields) per shared-memory read
     C rt[kNF];
 #pragma unroll
-    for (int jj = 0; jj < NJ; ++jj) {
-      if (P == 1) {
-        rt[jj] = mine[jj];
-      } else {
-        const C other = __shfl_xor_sync(0xffffffffu, mine[jj], 16);
-        rt[field_of(P, 0, jj)] = g ? other : mine[jj];
-        rt[field_of(P, 1, jj)] = g ? mine[jj] : other;
+    for (int F = 0; F < kNF; ++F) rt[F] = C(0);
+#pragma unroll
+    for (int mw = 0; mw < kNF / VW; ++mw) {
+#pragma unroll
+      for (int l = 0; l < Q; ++l) {
+        C v[VW];
+        unpack_word<S>(*reinterpret_cast<const W*>(st + fidx<Q, S>((uint32_t)lane, VW * mw, l)), v);
+#pragma unroll
+        for (int i = 0; i < VW; ++i) rt[VW * mw + i] += REP == kDEV ? C(L::w(l)) * v[i] : v[i];
       }
     }
     {
       C chk = C(0);
 #pragma unroll
       for (int F = 0; F < kNF; ++F) chk += rt[F];
-      if (valid && g == 0 && !isfinite(chk)) atomicOr(a.flag, 1);
+      if (valid && !isfinite(chk)) atomicOr(a.flag, 1);
     }
 
-    C alpha, gm[6], Kf[6], V[3];
-    unpack<REP, C>(rt, alpha, gm, Kf, V);
-    C Sr[kNF];
-    bm_sources<C>(alpha, gm, Kf, V, A, D, a.slicing, Sr);
-    add_fluid(a, alpha, gm, Sr);
-    if (!a.sources_on) {
-#pragma unroll
-      for (int F = 0; F < kNF; ++F) Sr[F] = C(0);
-    }
-    C rho[kNF];
-#pragma unroll
-    for (int F = 0; F < kNF; ++F) rho[F] = rt[F] + a.half_dt * Sr[F];
-    if (a.aux_out && valid && g == 0) write_lagged<REP, C>(a.aux_out, cells, n.c, rho);
-    C Fl[6][3];
-    {
-      C alpha2, g2[6], K2[6], V2[3];
-      unpack<REP, C>(rho, alpha2, g2, K2, V2);
-      bm_flux<C, dim>(alpha2, g2, V2, A, D, Fl);
-    }
+    C rho[kNF], Sr[kNF], Fl[6][3], Fv[3][3];
+    cell_terms<Q, S, C, REP>(a, n, rt, A, D, rho, Sr, Fl, Fv);
+    if (a.aux_out && valid) write_lagged<REP, C>(a.aux_out, cells, n.c, rho);
     const C three_omega = C(3) * a.omega;
 
-    if constexpr (WORDS) {
 #pragma unroll
-      for (int m = 0; m < NJ / VW; ++m) {
-        C cf[VW], b[VW][3];
+    for (int mw = 0; mw < kNF / VW; ++mw) {
+      C cf[VW], b[VW][3];
+#pragma unroll
+      for (int i = 0; i < VW; ++i) {
+        const int F = VW * mw + i;
+        cf[i] = a.omega * rho[F] + a.sigma * Sr[F];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) b[i][k] = has_flux(F) ? three_omega * Fl[F - kK][k] : C(0);
+      }
+#pragma unroll
+      for (int l = 0; l < Q; ++l) {
+        C v[VW], out[VW];
+        unpack_word<S>(*reinterpret_cast<const W*>(st + fidx<Q, S>((uint32_t)lane, VW * mw, l)), v);
 #pragma unroll
         for (int i = 0; i < VW; ++i) {
-          const int F = VW * m + i;
-          cf[i] = a.omega * rho[F] + a.sigma * Sr[F];
-#pragma unroll
-          for (int k = 0; k < 3; ++k) b[i][k] = has_flux(F) ? three_omega * Fl[F - kK][k] : C(0);
-        }
-#pragma unroll
-        for (int l = 0; l < Q; ++l) {
-          C v[VW], out[VW];
-          Codec<S>::unpack(*reinterpret_cast<const W*>(st + fidx<Q, S>((uint32_t)ci, VW * m, l)), v);
-#pragma unroll
-          for (int i = 0; i < VW; ++i) {
-            C t = cf[i];
-            if (has_flux(VW * m + i)) {
-#pragma unroll
-              for (int k = 0; k < dim; ++k) {
-                if (L::c(l, k) > 0) t += b[i][k];
-                if (L::c(l, k) < 0) t -= b[i][k];
-              }
-            }
-            out[i] = REP == kDEV ? fma(a.omc, v[i], t) : fma(a.omc, v[i], C(L::w(l)) * t);
-          }
-          WordIO<S>::stw_if(a.fout + write_index<Q, LAYOUT, S>(n, VW * m, l), Codec<S>::pack(out),
-                            valid);
-        }
-      }
-    } else {
-#pragma unroll
-      for (int jj = 0; jj < NJ; ++jj) {
-        const int F0 = field_of(P, 0, jj), F1 = field_of(P, 1, jj);
-        const int F = g ? F1 : F0;
-        const C cf = a.omega * (g ? rho[F1] : rho[F0]) + a.sigma * (g ? Sr[F1] : Sr[F0]);
-        C b[3] = {C(0), C(0), C(0)};
-        if (has_flux(F0)) {
-#pragma unroll
-          for (int k = 0; k < dim; ++k) b[k] = three_omega * (g ? Fl[F1 - kK][k] : Fl[F0 - kK][k]);
-        }
-#pragma unroll
-        for (int l = 0; l < Q; ++l) {
-          const C v = (C)st[fidx<Q, S>((uint32_t)ci, F, l)];
-          C t = cf;
-          if (has_flux(F0)) {
+          C t = cf[i];
+          if (has_flux(VW * mw + i)) {
 #pragma unroll
             for (int k = 0; k < dim; ++k) {
-              if (L::c(l, k) > 0) t += b[k];
-              if (L::c(l, k) < 0) t -= b[k];
+              if (L::c(l, k) > 0) t += b[i][k];
+              if (L::c(l, k) < 0) t -= b[i][k];
             }
           }
-          const C out = REP == kDEV ? fma(a.omc, v, t) : fma(a.omc, v, C(L::w(l)) * t);
-          Codec<S>::store_if(a.fout + write_index<Q, LAYOUT, S>(n, F, l), out, valid);
+          out[i] = REP == kDEV ? fma(a.omc, v[i], t) : fma(a.omc, v[i], C(L::w(l)) * t);
         }
+        store_word_if<S>(a.fout + write_index<Q, LAYOUT, S>(n, VW * mw, l), out, valid);
       }
     }
     __syncwarp();

@@ -9,17 +9,18 @@
 namespace lbnr {
 
 // Launch forms of the collide kernel, per velocity set and storage width.
-// kind 0: one thread block per 128 threads, P threads per cell; HOLD keeps a
-//         thread's distributions in registers between the moment pass and
-//         the update pass (else they are read again, from cache). Any layout.
+// Every form runs one thread (lane) per cell, P = 1 (the P in the names).
+// kind 0: blocks of 128 threads; HOLD keeps a thread's distributions in
+//         registers between the moment pass and the update pass (else they
+//         are read again, from cache). Any layout.
 // kind 1: bulk-copy-fed persistent kernel (collide_tma.cuh) with NC consumer
-//         warps and NS shared-memory stages of one 32-cell tile; local reads
-//         only, so at the odd AA step it hands over to the form named by
-//         `fallback`.
+//         warps and NC K shared-memory stages of one 32-cell tile; local
+//         reads only, so at the odd AA step it hands over to the form named
+//         by `fallback`.
 struct VariantSpec {
   int kind, P;
   bool hold;
-  int nc, k, tc;  // consumer warps, stages per warp group, cells per tile (kind 1)
+  int nc, k, tc;  // consumer warps, stages per warp, cells per tile (kind 1)
 };
 
 template <int Q, int SB>
@@ -36,20 +37,15 @@ struct VariantTable;
 LBNR_VARIANTS(3, 8, 0, {0, 1, true, 0, 0, 0}, {1, 1, false, 8, 1, 32})
 LBNR_VARIANTS(9, 8, 0, {0, 1, false, 0, 0, 0}, {1, 1, false, 4, 1, 32})
 LBNR_VARIANTS(19, 8, 0, {0, 1, false, 0, 0, 0}, {1, 1, false, 2, 1, 32})
-// FP32 storage
-LBNR_VARIANTS(3, 4, 2, {1, 1, false, 8, 4, 32}, {1, 2, false, 8, 4, 32}, {0, 1, true, 0, 0, 0},
-              {0, 1, false, 0, 0, 0})
-LBNR_VARIANTS(9, 4, 2, {1, 1, false, 4, 2, 32}, {1, 2, false, 8, 2, 32}, {0, 1, true, 0, 0, 0},
-              {0, 1, false, 0, 0, 0})
-LBNR_VARIANTS(19, 4, 2, {1, 1, false, 4, 1, 32}, {1, 1, false, 5, 1, 32},
-              {0, 1, false, 0, 0, 0}, {0, 2, false, 0, 0, 0}, {0, 2, true, 0, 0, 0})
-// 16-bit storage
-LBNR_VARIANTS(3, 2, 2, {1, 1, false, 8, 4, 32}, {1, 2, false, 8, 4, 32}, {0, 1, true, 0, 0, 0},
-              {0, 1, false, 0, 0, 0})
-LBNR_VARIANTS(9, 2, 2, {1, 1, false, 8, 2, 32}, {1, 2, false, 8, 3, 32}, {0, 1, true, 0, 0, 0},
-              {0, 1, false, 0, 0, 0})
-LBNR_VARIANTS(19, 2, 2, {1, 2, false, 8, 2, 32}, {1, 1, false, 8, 1, 32},
-              {0, 1, false, 0, 0, 0}, {0, 2, false, 0, 0, 0}, {0, 2, true, 0, 0, 0})
+// FP32 and 16-bit storage: one lane per cell, word by word. (Forms with two
+// lanes per cell split a word's fields between the lanes; on the word
+// layout they ran at half the speed and are not offered.)
+LBNR_VARIANTS(3, 4, 1, {1, 1, false, 8, 4, 32}, {0, 1, true, 0, 0, 0}, {0, 1, false, 0, 0, 0})
+LBNR_VARIANTS(9, 4, 1, {1, 1, false, 4, 2, 32}, {0, 1, true, 0, 0, 0}, {0, 1, false, 0, 0, 0})
+LBNR_VARIANTS(19, 4, 2, {1, 1, false, 4, 1, 32}, {1, 1, false, 5, 1, 32}, {0, 1, false, 0, 0, 0})
+LBNR_VARIANTS(3, 2, 1, {1, 1, false, 8, 4, 32}, {0, 1, true, 0, 0, 0}, {0, 1, false, 0, 0, 0})
+LBNR_VARIANTS(9, 2, 1, {1, 1, false, 8, 2, 32}, {0, 1, true, 0, 0, 0}, {0, 1, false, 0, 0, 0})
+LBNR_VARIANTS(19, 2, 1, {1, 1, false, 8, 1, 32}, {0, 1, false, 0, 0, 0})
 #undef LBNR_VARIANTS
 
 inline int sm_count() {
@@ -95,11 +91,11 @@ struct Impl {
   template <int LAYOUT, int VI>
   static cudaError_t launch_generic(const LaunchCtx& L, const StepArgs<S, C>& a) {
     constexpr VariantSpec x = VT::v[VI];
-    constexpr int P = x.P;
+    static_assert(x.P == 1, "one thread per cell");
     constexpr bool H = x.hold;
     const int block = 128;
-    const int64_t threads = P == 2 ? ((L.cells + 15) / 16) * 32 : L.cells;
-    if constexpr (P == 1 && Codec<S>::kV > 1) {
+    const int64_t threads = L.cells;
+    if constexpr (Codec<S>::kV > 1) {
       // one thread per cell, word by word: 3 blocks per SM with or without
       // the lagged-field writes; 2 at the odd AA step, which holds a field
       // group's Q words and reads and writes at neighbours
@@ -112,10 +108,10 @@ struct Impl {
     } else {
       // the lagged-field writes cost registers: sized for 2 blocks per SM
       if (a.aux_out)
-        k_collide<Q, S, C, REP, LAYOUT, P, H, 0, 2, true>
+        k_collide<Q, S, C, REP, LAYOUT, H, 0, 2, true>
             <<<grid_for(threads, block), block, 0, L.st>>>(a);
       else
-        k_collide<Q, S, C, REP, LAYOUT, P, H><<<grid_for(threads, block), block, 0, L.st>>>(a);
+        k_collide<Q, S, C, REP, LAYOUT, H><<<grid_for(threads, block), block, 0, L.st>>>(a);
     }
     return cudaGetLastError();
   }
@@ -139,10 +135,10 @@ struct Impl {
             <<<grid_for(L.cells, block), block, 0, L.st>>>(a);
     } else {
       if (a.aux_out)
-        k_collide<Q, S, C, REP, LAYOUT, 1, false, SHIFT, MINB, true>
+        k_collide<Q, S, C, REP, LAYOUT, false, SHIFT, MINB, true>
             <<<grid_for(L.cells, block), block, 0, L.st>>>(a);
       else
-        k_collide<Q, S, C, REP, LAYOUT, 1, false, SHIFT, MINB>
+        k_collide<Q, S, C, REP, LAYOUT, false, SHIFT, MINB>
             <<<grid_for(L.cells, block), block, 0, L.st>>>(a);
     }
     return cudaGetLastError();
@@ -153,12 +149,12 @@ struct Impl {
     constexpr VariantSpec x = VT::v[VI];
     constexpr int NC = x.nc > 0 ? x.nc : 1;
     constexpr int K = x.k > 0 ? x.k : 1;
+    static_assert(x.P == 1, "one lane per cell");
     constexpr int TC = x.tc > 0 ? x.tc : kTileCells;
-    constexpr int P = x.P;
-    constexpr int NS = NC / (TC / (32 / P)) * K;
+    constexpr int NS = NC * K;
     constexpr uint32_t smem = tma_smem_bytes(tma_stage_bytes<S>(Q, TC), NS);
     static_assert(smem <= 232448, "shared memory per block");
-    auto kern = k_collide_tma<Q, S, C, REP, LAYOUT, NC, K, TC, P>;
+    auto kern = k_collide_tma<Q, S, C, REP, LAYOUT, NC, K, TC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t ntiles = L.pstride / TC;

@@ -177,6 +177,23 @@ struct WordIO {
   }
 };
 
+// One word's kV values, and a store of kV values as one word under a
+// predicate, for every storage type (a word of FP64 storage is one value).
+template <class S, class C>
+__device__ __forceinline__ void unpack_word(typename Codec<S>::W w, C* v) {
+  if constexpr (Codec<S>::kV == 1)
+    v[0] = w;
+  else
+    Codec<S>::unpack(w, v);
+}
+template <class S, class C>
+__device__ __forceinline__ void store_word_if(S* p, const C* v, bool q) {
+  if constexpr (Codec<S>::kV == 1)
+    Codec<S>::store_if(p, v[0], q);
+  else
+    WordIO<S>::stw_if(p, Codec<S>::pack(v), q);
+}
+
 // Flat-space value of field F (alpha = 1, gamma = delta, K = V = 0).
 __host__ __device__ constexpr double flat_value(int F) {
   return (F == 0 || F == 1 || F == 4 || F == 6) ? 1.0 : 0.0;
@@ -265,13 +282,6 @@ __device__ __forceinline__ Nbr make_nbr(const Grid& G, int64_t c64) {
 // the 600-odd tiles in flight on the GPU touch 16 Q separate DRAM regions
 // each, and the step ran 11 % slower (256^3 D3Q19 FP32 on GB300).
 constexpr int kTileCells = 32;
-// Hides the values from the optimiser (they may have changed), so that what
-// is computed from them is not hoisted out of the enclosing loop.
-template <int N>
-__device__ __forceinline__ void opaque(uint32_t (&v)[N]) {
-#pragma unroll
-  for (int i = 0; i < N; ++i) asm volatile("" : "+r"(v[i]));
-}
 template <int Q, class S>
 __host__ __device__ __forceinline__ size_t fidx(uint32_t c, int F, int l) {
   constexpr int V = Codec<S>::kV;
@@ -308,23 +318,6 @@ __device__ __forceinline__ size_t write_index(const Nbr& n, int F, int l) {
   return fidx<Q, S>(write_cell<Q, LAYOUT>(n, l), F, write_slot<LAYOUT>(l));
 }
 
-// ---------------------------------------------------------------------------
-// Field split between the P threads that share one cell
-// ---------------------------------------------------------------------------
-// With two threads per cell, thread g takes 8 fields; both lists put the
-// flux-free fields first and three K components last, so the j-th field of
-// either thread has the same kind and all indexing stays compile-time.
-__host__ __device__ constexpr int field_of(int P, int g, int j) {
-  // pairs (j-th field of thread 0, of thread 1): (0,1) (2,3) (4,5) (6,13)
-  // (14,15) (7,10) (8,11) (9,12); each pair differs by an odd number of
-  // fields, so with Q odd the two half-warps read shared-memory rows that
-  // start in different banks.
-  return P == 1 ? j
-                : (g == 0 ? (j == 0 ? 0 : j == 1 ? 2 : j == 2 ? 4 : j == 3 ? 6 : j == 4 ? 14
-                                                     : j == 5 ? 7 : j == 6 ? 8 : 9)
-                          : (j == 0 ? 1 : j == 1 ? 3 : j == 2 ? 5 : j == 3 ? 13 : j == 4 ? 15
-                                                     : j == 5 ? 10 : j == 6 ? 11 : 12));
-}
 
 // ---------------------------------------------------------------------------
 // Step arguments
@@ -468,33 +461,27 @@ __device__ __forceinline__ void unpack(const C m[kNF], C& alpha, C g[6], C K[6],
 }
 
 // ---------------------------------------------------------------------------
-// k_collide: the fused step
+// k_collide: the fused step, one thread per cell, value by value (FP64)
 // ---------------------------------------------------------------------------
-// SHIFT: the shift terms are compiled in: 1 a constant shift (a.beta),
-// 2 a static field on top of it (a.beta_field, with its B terms). The
-// zero-shift forms (0) keep none of their code or registers. MINB: blocks
-// per SM the registers are sized for (without HOLD). LAGW: the form writes
-// the lagged fields of reading R17 to a.aux_out (compiled in only where
-// asked, so the other forms keep their registers).
-template <int Q, class S, class C, int REP, int LAYOUT, int P, bool HOLD, int SHIFT = 0, int MINB = 3,
+// Storage with one value per distribution word: FP64 (FP32 and 16-bit
+// storage take k_collide_w below). SHIFT: the shift terms are compiled in: 1
+// a constant shift (a.beta), 2 a static field on top of it (a.beta_field,
+// with its B terms). The zero-shift forms (0) keep none of their code or
+// registers. MINB: blocks per SM the registers are sized for (without HOLD).
+// LAGW: the form writes the lagged fields of reading R17 to a.aux_out
+// (compiled in only where asked, so the other forms keep their registers).
+template <int Q, class S, class C, int REP, int LAYOUT, bool HOLD, int SHIFT = 0, int MINB = 3,
           bool LAGW = false>
 __global__ void __launch_bounds__(128, HOLD ? 1 : MINB) k_collide(const StepArgs<S, C> a) {
   using L = Lattice<Q>;
-  constexpr int NJ = kNF / P;
   constexpr int dim = L::kDim;
-  const int lane = threadIdx.x & 31;
-  const int g = P == 2 ? (lane >> 4) : 0;
-  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t cell = P == 2 ? ((gtid >> 5) << 4) + (lane & 15) : gtid;
+  const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = cell < a.G.cells;
   const int64_t c = valid ? cell : a.G.cells - 1;
   const int64_t cells = a.G.cells;
   const Nbr n = make_nbr(a.G, c);
 
-  // Source and destination cell of each velocity (32-bit). With two threads
-  // per cell the field is a runtime value, and the 64-bit addresses are
-  // formed again for every field rather than kept live across the field
-  // loop (2 Q of them would not fit the register budget).
+  // source and destination cell of each velocity
   uint32_t rc[Q], wc[Q];
 #pragma unroll
   for (int l = 0; l < Q; ++l) {
@@ -502,13 +489,11 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : MINB) k_collide(const StepArgs
     wc[l] = write_cell<Q, LAYOUT>(n, l);
   }
 
-  // Pass 1: zeroth moments of this thread's fields (ascending l).
-  C fv[HOLD ? NJ : 1][HOLD ? Q : 1];
-  C mine[NJ];
+  // Pass 1: zeroth moments (ascending l).
+  C fv[HOLD ? kNF : 1][HOLD ? Q : 1];
+  C rt[kNF];
 #pragma unroll
-  for (int j = 0; j < NJ; ++j) {
-    const int F = g ? field_of(P, 1, j) : field_of(P, 0, j);
-    if (P == 2) opaque(rc);
+  for (int F = 0; F < kNF; ++F) {
     C s = C(0);
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
@@ -517,27 +502,16 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : MINB) k_collide(const StepArgs
       const S* src = a.fin + fidx<Q, S>(rc[l], F, read_slot<LAYOUT>(l));
       const C v = HOLD ? Codec<S>::load(src)
                   : LAYOUT == kPingPong ? Codec<S>::load_keep(src) : Codec<S>::load_coh(src);
-      if (HOLD) fv[HOLD ? j : 0][HOLD ? l : 0] = v;
+      if (HOLD) fv[HOLD ? F : 0][HOLD ? l : 0] = v;
       s += REP == kDEV ? C(L::w(l)) * v : v;
     }
-    mine[j] = s;
-  }
-  C rt[kNF];
-#pragma unroll
-  for (int j = 0; j < NJ; ++j) {
-    if (P == 1) {
-      rt[j] = mine[j];
-    } else {
-      const C other = __shfl_xor_sync(0xffffffffu, mine[j], 16);
-      rt[field_of(P, 0, j)] = g ? other : mine[j];
-      rt[field_of(P, 1, j)] = g ? mine[j] : other;
-    }
+    rt[F] = s;
   }
   {
     C chk = C(0);
 #pragma unroll
     for (int F = 0; F < kNF; ++F) chk += rt[F];
-    if (valid && g == 0 && !isfinite(chk)) atomicOr(a.flag, 1);
+    if (valid && !isfinite(chk)) atomicOr(a.flag, 1);
   }
 
   // Derivatives, sources at rho~, corrected rho, flux at rho.
@@ -562,7 +536,7 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : MINB) k_collide(const StepArgs
   C rho[kNF];  // ABS: rho; DEV: rho - rho_flat
 #pragma unroll
   for (int F = 0; F < kNF; ++F) rho[F] = rt[F] + a.half_dt * Sr[F];
-  if (LAGW && valid && g == 0) write_lagged<REP, C>(a.aux_out, cells, n.c, rho);
+  if (LAGW && valid) write_lagged<REP, C>(a.aux_out, cells, n.c, rho);
   C Fl[6][3];
   C Fv[SHIFT == 2 ? 3 : 1][3];  // V fluxes under a shift field
   {
@@ -583,38 +557,28 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : MINB) k_collide(const StepArgs
 
   // Pass 2: relax, add the source, stream.
 #pragma unroll
-  for (int j = 0; j < NJ; ++j) {
-    const int F0 = field_of(P, 0, j), F1 = field_of(P, 1, j);
-    const int F = g ? F1 : F0;
-    const C cf = g ? coef[F1] : coef[F0];
+  for (int F = 0; F < kNF; ++F) {
+    const C cf = coef[F];
     C b[3] = {C(0), C(0), C(0)};
-    if (has_flux(F0)) {
+    if (has_flux(F)) {
 #pragma unroll
-      for (int k = 0; k < dim; ++k)
-        b[k] = three_omega * (g ? Fl[F1 - kK][k] : Fl[F0 - kK][k]);
+      for (int k = 0; k < dim; ++k) b[k] = three_omega * Fl[F - kK][k];
     }
-    // Under a shift the V fields (and, with two threads per cell, the field
-    // paired with V_x) take the flux -beta^k V_i; b stays zero for the other.
-    const bool vflux = SHIFT && (is_v(F0) || is_v(F1));
+    // under a shift the V fields take the flux -beta^k V_i
+    const bool vflux = SHIFT && is_v(F);
     // All Q values of this field are read before any is written: in place
     // (AA) the field's reads and writes touch the same Q locations.
-    if (P == 2) {
-      opaque(rc);
-      opaque(wc);
-    }
     C v_[Q];
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
       const S* src = a.fin + fidx<Q, S>(rc[l], F, read_slot<LAYOUT>(l));
       // the second read is the last use: streaming (evict-first) load
-      v_[l] = HOLD ? fv[HOLD ? j : 0][HOLD ? l : 0]
+      v_[l] = HOLD ? fv[HOLD ? F : 0][HOLD ? l : 0]
               : LAYOUT == kPingPong ? Codec<S>::load(src) : Codec<S>::load_coh(src);
     }
     if (vflux && SHIFT == 2) {
-      if (is_v(F)) {
 #pragma unroll
-        for (int k = 0; k < dim; ++k) b[k] = three_omega * Fv[SHIFT == 2 ? F - kV : 0][k];
-      }
+      for (int k = 0; k < dim; ++k) b[k] = three_omega * Fv[SHIFT == 2 ? F - kV : 0][k];
     } else if (vflux) {
       // V_i at the corrected moments, recovered from this field's own values
       // rather than kept live since pass 1: coef = omega rho~ + dt S (as
@@ -622,7 +586,7 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : MINB) k_collide(const StepArgs
       C s = C(0);
 #pragma unroll
       for (int l = 0; l < Q; ++l) s += REP == kDEV ? C(L::w(l)) * v_[l] : v_[l];
-      const C mv = is_v(F) ? -three_omega * (s + C(0.5) * (cf - a.omega * s)) : C(0);
+      const C mv = -three_omega * (s + C(0.5) * (cf - a.omega * s));
 #pragma unroll
       for (int k = 0; k < dim; ++k) b[k] = mv * a.beta[k];
     }
@@ -634,7 +598,7 @@ __global__ void __launch_bounds__(128, HOLD ? 1 : MINB) k_collide(const StepArgs
     for (int l = 0; l < Q; ++l) {
       const C v = v_[l];
       C t = kLeanRelax ? C(L::w(l)) * cf : cf;
-      if (has_flux(F0) || vflux) {
+      if (has_flux(F) || vflux) {
 #pragma unroll
         for (int k = 0; k < dim; ++k) {
           const C bk = kLeanRelax ? C(L::w(l)) * b[k] : b[k];
