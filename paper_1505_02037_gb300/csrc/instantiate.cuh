@@ -21,6 +21,8 @@ struct VariantSpec {
   int kind, P;
   bool hold;
   int nc, k, tc;  // consumer warps, stages per warp, cells per tile (kind 1)
+  int tpb, minb;  // kind 0, word forms: threads per block and the blocks per SM the
+                  // registers are sized for (0: 128 and 3)
 };
 
 template <int Q, int SB>
@@ -39,13 +41,22 @@ LBNR_VARIANTS(9, 8, 0, {0, 1, false, 0, 0, 0}, {1, 1, false, 4, 1, 32})
 LBNR_VARIANTS(19, 8, 0, {0, 1, false, 0, 0, 0}, {1, 1, false, 2, 1, 32})
 // FP32 and 16-bit storage: one lane per cell, word by word. (Forms with two
 // lanes per cell split a word's fields between the lanes; on the word
-// layout they ran at half the speed and are not offered.)
-LBNR_VARIANTS(3, 4, 1, {1, 1, false, 8, 4, 32}, {0, 1, true, 0, 0, 0}, {0, 1, false, 0, 0, 0})
-LBNR_VARIANTS(9, 4, 1, {1, 1, false, 4, 2, 32}, {0, 1, true, 0, 0, 0}, {0, 1, false, 0, 0, 0})
-LBNR_VARIANTS(19, 4, 2, {1, 1, false, 4, 1, 32}, {1, 1, false, 5, 1, 32}, {0, 1, false, 0, 0, 0})
-LBNR_VARIANTS(3, 2, 1, {1, 1, false, 8, 4, 32}, {0, 1, true, 0, 0, 0}, {0, 1, false, 0, 0, 0})
-LBNR_VARIANTS(9, 2, 1, {1, 1, false, 8, 2, 32}, {0, 1, true, 0, 0, 0}, {0, 1, false, 0, 0, 0})
-LBNR_VARIANTS(19, 2, 1, {1, 1, false, 8, 1, 32}, {0, 1, false, 0, 0, 0})
+// layout they ran at half the speed and are not offered.) The re-read forms
+// come in three block shapes: 128 threads x 3 blocks per SM (168 registers),
+// 64 x 4 and 128 x 2 (255 registers, 8 warps per SM: fewer cells resident,
+// so more of the update pass's re-read stays in L2).
+LBNR_VARIANTS(3, 4, 1, {1, 1, false, 8, 4, 32}, {0, 1, true, 0, 0, 0}, {0, 1, false, 0, 0, 0},
+              {0, 1, false, 0, 0, 0, 64, 4})
+LBNR_VARIANTS(9, 4, 1, {1, 1, false, 4, 2, 32}, {0, 1, true, 0, 0, 0}, {0, 1, false, 0, 0, 0},
+              {0, 1, false, 0, 0, 0, 64, 4})
+LBNR_VARIANTS(19, 4, 2, {1, 1, false, 4, 1, 32}, {1, 1, false, 5, 1, 32}, {0, 1, false, 0, 0, 0},
+              {0, 1, false, 0, 0, 0, 64, 4}, {0, 1, false, 0, 0, 0, 128, 2})
+LBNR_VARIANTS(3, 2, 1, {1, 1, false, 8, 4, 32}, {0, 1, true, 0, 0, 0}, {0, 1, false, 0, 0, 0},
+              {0, 1, false, 0, 0, 0, 64, 4})
+LBNR_VARIANTS(9, 2, 1, {1, 1, false, 8, 2, 32}, {0, 1, true, 0, 0, 0}, {0, 1, false, 0, 0, 0},
+              {0, 1, false, 0, 0, 0, 64, 4})
+LBNR_VARIANTS(19, 2, 1, {1, 1, false, 8, 1, 32}, {0, 1, false, 0, 0, 0},
+              {0, 1, false, 0, 0, 0, 64, 4}, {0, 1, false, 0, 0, 0, 128, 2})
 #undef LBNR_VARIANTS
 
 inline int sm_count() {
@@ -81,7 +92,10 @@ struct Impl {
     static char buf[8][48];
     if (v < 0 || v >= VT::n || v >= 8) return "?";
     const VariantSpec& x = VT::v[v];
-    if (x.kind == 0)
+    if (x.kind == 0 && x.tpb > 0)
+      snprintf(buf[v], sizeof(buf[v]), "P%d%s-%dx%d", x.P, x.hold ? "-hold" : "-reread", x.tpb,
+               x.minb);
+    else if (x.kind == 0)
       snprintf(buf[v], sizeof(buf[v]), "P%d%s", x.P, x.hold ? "-hold" : "-reread");
     else
       snprintf(buf[v], sizeof(buf[v]), "tma-p%d-nc%d-k%d-t%d", x.P, x.nc, x.k, x.tc);
@@ -96,15 +110,18 @@ struct Impl {
     const int block = 128;
     const int64_t threads = L.cells;
     if constexpr (Codec<S>::kV > 1) {
-      // one thread per cell, word by word: 3 blocks per SM with or without
-      // the lagged-field writes; 2 at the odd AA step, which holds a field
-      // group's Q words and reads and writes at neighbours
-      constexpr int WMINB = LAYOUT == kAAOdd ? 2 : 3;
+      // one thread per cell, word by word. The default shape, 128 threads
+      // sized for 3 blocks per SM with or without the lagged-field writes,
+      // takes 2 at the odd AA step, which holds a field group's Q words and
+      // reads and writes at neighbours.
+      constexpr int TPB = x.tpb > 0 ? x.tpb : 128;
+      constexpr int WMINB = x.minb > 0 ? x.minb : (LAYOUT == kAAOdd ? 2 : 3);
       if (a.aux_out)
-        k_collide_w<Q, S, C, REP, LAYOUT, H, WMINB, true>
-            <<<grid_for(threads, block), block, 0, L.st>>>(a);
+        k_collide_w<Q, S, C, REP, LAYOUT, H, WMINB, true, 0, TPB>
+            <<<grid_for(threads, TPB), TPB, 0, L.st>>>(a);
       else
-        k_collide_w<Q, S, C, REP, LAYOUT, H, WMINB><<<grid_for(threads, block), block, 0, L.st>>>(a);
+        k_collide_w<Q, S, C, REP, LAYOUT, H, WMINB, false, 0, TPB>
+            <<<grid_for(threads, TPB), TPB, 0, L.st>>>(a);
     } else {
       // the lagged-field writes cost registers: sized for 2 blocks per SM
       if (a.aux_out)

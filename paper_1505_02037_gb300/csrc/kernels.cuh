@@ -664,10 +664,10 @@ __device__ __forceinline__ void cell_terms(const StepArgs<S, C>& a, const Nbr& n
 // memory instructions of value-by-value access. HOLD keeps the words of a
 // cell in registers between the passes. SHIFT as in k_collide: 1 a constant
 // shift, 2 a static shift field; under a shift the V fields take the flux
-// -beta^k V_i at the corrected moments.
+// -beta^k V_i at the corrected moments. TPB: threads per block.
 template <int Q, class S, class C, int REP, int LAYOUT, bool HOLD, int MINB = 3, bool LAGW = false,
-          int SHIFT = 0>
-__global__ void __launch_bounds__(128, HOLD ? 1 : MINB) k_collide_w(const StepArgs<S, C> a) {
+          int SHIFT = 0, int TPB = 128>
+__global__ void __launch_bounds__(TPB, HOLD ? 1 : MINB) k_collide_w(const StepArgs<S, C> a) {
   using L = Lattice<Q>;
   using IO = WordIO<S>;
   using W = typename IO::W;
