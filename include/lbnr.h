@@ -59,8 +59,8 @@ enum { LBNR_STREAM_AUTO = 0, LBNR_STREAM_PINGPONG = 1, LBNR_STREAM_AA = 2 };
 /* Time level of A_k and D_kij, on which the paper is silent (Sec. "Lattice
  * Boltzmann Model", moment rule; Sec. "Bona-Masso evolution equations",
  * first-order derivatives). SYNC: central differences of this step's zeroth
- * moments of alpha and gamma (a moment pass over their 7 Q planes, then the
- * collide kernel). LAG: central differences of the previous step's
+ * moments of alpha and gamma (a moment pass over their distributions, then
+ * the collide kernel). LAG: central differences of the previous step's
  * corrected alpha and gamma (the initial fields at the first step), which
  * the collide kernel itself writes for the next step: one kernel per step.
  * Both are first order in dt; they differ by O(dt) per step. */
@@ -141,7 +141,9 @@ int lbnr_moments(lbnr_ctx* ctx, double* out);
 int lbnr_constraints(lbnr_ctx* ctx, double* out);
 
 /* Stored distributions decoded to FP64, host out[16][Q][cells] (standard
- * layout whatever the streaming pattern). For checks and checkpoints. */
+ * layout whatever the device layout and streaming pattern: on the device the
+ * 16 Q values of each 32-cell tile form one block of words of several fields
+ * each). For checks and checkpoints. */
 int lbnr_get_distributions(lbnr_ctx* ctx, double* out);
 
 /* Stored distributions of n selected cells, decoded to FP64, into host
@@ -214,14 +216,16 @@ int lbnr_set_shift(lbnr_ctx* ctx, double bx, double by, double bz);
  * allocated. */
 int lbnr_set_shift_field(lbnr_ctx* ctx, const double* beta);
 
-/* Thread-to-cell layouts of the collide kernel available for this context's
- * set and storage (all give the same results): their number, a short name,
- * and the selection (default 0). Used by the autotuner. Names: "P<n>-hold" /
- * "P<n>-reread" (n threads per cell; distributions held in registers or read
- * again), "tma-p<n>-nc<c>-k<k>-t<t>" (persistent, tensor-copy fed, c
- * consumer warps). The forms fed by tensor copies read each tile's own cells
- * only; at the odd step of the in-place pattern a register form runs in
- * their place. */
+/* Launch forms of the collide kernel available for this context's set and
+ * storage (all give the same results within rounding; every form runs one
+ * thread per cell): their number, a short name, and the selection (default
+ * 0). Used by the autotuner. Names: "P1-hold" / "P1-reread" (distributions
+ * held in registers between the moment and update passes, or read again),
+ * with a suffix "-<t>x<b>" for blocks of t threads sized for b blocks per SM
+ * (no suffix: 128 x 3); "tma-p1-nc<c>-k<k>-t32" (persistent, fed by bulk
+ * copies of whole 32-cell tiles, c consumer warps with k stages each). The
+ * bulk-copy-fed forms read each tile's own cells only; at the odd step of the
+ * in-place pattern a register form runs in their place. */
 int lbnr_num_variants(const lbnr_ctx* ctx);
 const char* lbnr_variant_name(const lbnr_ctx* ctx, int variant);
 int lbnr_set_variant(lbnr_ctx* ctx, int variant);

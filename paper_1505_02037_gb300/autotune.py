@@ -1,11 +1,11 @@
 """Autotuner for the collide kernel's launch form.
 
-Each context offers a few launch forms (threads per cell, register-held or
-shared-memory-staged distributions, consumer warps and pipeline depth of the
-TMA-fed kernel). All give the same results; the tuner runs a few real steps
-with each (best of a few timed runs, CUDA events per kernel) and keeps the
-fastest. Results
-are cached per (set, storage, streaming, lattice shape) for the process.
+Each context offers a few launch forms (block shape of the one-thread-per-cell
+kernel, register-held or re-read distributions, consumer warps and pipeline
+depth of the bulk-copy-fed kernel). All give the same results within
+rounding; the tuner runs a few real steps with each (best of a few timed
+runs, CUDA events per kernel) and keeps the fastest. Results are cached per
+(set, storage, streaming, derivative mode, lattice shape) for the process.
 """
 from __future__ import annotations
 

@@ -1,5 +1,5 @@
-// TMA-fed, warp-specialised form of the fused collide-and-stream step
-// (same arithmetic as k_collide in kernels.cuh: Eq. numlb with the
+// Bulk-copy-fed, warp-specialised form of the fused collide-and-stream step
+// (same arithmetic as k_collide_w in kernels.cuh: Eq. numlb with the
 // equilibria and sources of Eqs. alfa-ekstsor and rho = sum f + dt S/2).
 //
 // One persistent CTA per SM. Warp NC (the producer) streams tiles of 32
