@@ -680,7 +680,7 @@ __global__ void __launch_bounds__(TPB, HOLD ? 1 : MINB) k_collide_w(const StepAr
   const int64_t cells = a.G.cells;
   const Nbr n = make_nbr(a.G, c);
 
-  // Pass 1: zeroth moments, two fields per load (ascending l).
+  // Pass 1: zeroth moments, kV fields per load (ascending l).
   W hw[HOLD ? NW : 1][HOLD ? Q : 1];
   C rt[kNF];
 #pragma unroll
@@ -702,18 +702,22 @@ __global__ void __launch_bounds__(TPB, HOLD ? 1 : MINB) k_collide_w(const StepAr
 #pragma unroll
     for (int i = 0; i < V; ++i) rt[V * m + i] = sum[i];
   }
+  // Non-finite moments are reported, and the lagged fields written, only
+  // after the update pass: a global write here (the flag or aux_out may
+  // alias the input as far as the compiler knows) would keep the update
+  // pass's loads from being issued ahead of the physics.
+  bool bad;
   {
     C chk = C(0);
 #pragma unroll
     for (int F = 0; F < kNF; ++F) chk += rt[F];
-    if (valid && !isfinite(chk)) atomicOr(a.flag, 1);
+    bad = valid && !isfinite(chk);
   }
 
   C A[3], D[3][6];
   derivatives<Q, C>(n, cells, a.aux, a.inv2dx, a.inv4dx, A, D);
   C rho[kNF], Sr[kNF], Fl[6][3], Fv[3][3];
   cell_terms<Q, S, C, REP, SHIFT>(a, n, rt, A, D, rho, Sr, Fl, Fv);
-  if (LAGW && valid) write_lagged<REP, C>(a.aux_out, cells, n.c, rho);
   const C three_omega = C(3) * a.omega;
 
   // Pass 2: relax, add the source, stream; all Q words of a field pair are
@@ -763,6 +767,8 @@ __global__ void __launch_bounds__(TPB, HOLD ? 1 : MINB) k_collide_w(const StepAr
         IO::stw_if(dst, Codec<S>::pack(out), valid);
     }
   }
+  if (LAGW && valid) write_lagged<REP, C>(a.aux_out, cells, n.c, rho);
+  if (bad) atomicOr(a.flag, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -870,11 +876,14 @@ __device__ __forceinline__ void collide_cell(const StepArgs<S, C>& a, int64_t c)
       for (int i = 0; i < VW; ++i) rt[VW * m + i] += REP == kDEV ? C(L::w(l)) * v[i] : v[i];
     }
   }
+  // reported at the end: a global write here would hold back the second
+  // pass's loads (see k_collide_w)
+  bool bad;
   {
     C chk = C(0);
 #pragma unroll
     for (int F = 0; F < kNF; ++F) chk += rt[F];
-    if (!isfinite(chk)) atomicOr(a.flag, 1);
+    bad = !isfinite(chk);
   }
   C A[3], D[3][6];
   derivatives_coh<Q, C>(n, cells, a.aux, a.inv2dx, a.inv4dx, A, D);
@@ -890,7 +899,6 @@ __device__ __forceinline__ void collide_cell(const StepArgs<S, C>& a, int64_t c)
   C rho[kNF];
 #pragma unroll
   for (int F = 0; F < kNF; ++F) rho[F] = rt[F] + a.half_dt * Sr[F];
-  if (LAGW) write_lagged<REP, C>(a.aux_out, cells, n.c, rho);
   C Fl[6][3];
   {
     C alpha2, g2[6], K2[6], V2[3];
@@ -970,6 +978,8 @@ __device__ __forceinline__ void collide_cell(const StepArgs<S, C>& a, int64_t c)
       }
     }
   }
+  if (LAGW) write_lagged<REP, C>(a.aux_out, cells, n.c, rho);
+  if (bad) atomicOr(a.flag, 1);
 }
 
 // ---------------------------------------------------------------------------

@@ -43,6 +43,8 @@ def main(argv=None):
                    help="amplitude of a static shear shift field")
     p.add_argument("--deriv", default="sync", choices=["sync", "lag"],
                    help="time level of A and D (lag: one kernel per step)")
+    p.add_argument("--amplitude", type=float, default=0.1,
+                   help="gauge-wave amplitude A (0: flat space)")
     a = p.parse_args(argv)
     if a.batch:
         return batch_main(a)
@@ -63,7 +65,7 @@ def main(argv=None):
         lat.set_shift(beta)
     if a.shift_field:
         lat.set_shift_field(W.shear_shift3(shape, 1 / n, a.shift_field))
-    lat.init(W.gauge_wave(shape, 1 / n, 0.1, beta=beta))
+    lat.init(W.gauge_wave(shape, 1 / n, a.amplitude, beta=beta))
     lat.step(a.steps)
     lat.status()
     ms = lat.step_timed(4)
