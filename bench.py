@@ -312,6 +312,13 @@ def run_reference(args):
 ENSEMBLE_SEED = 150502037
 
 
+# FP64 flops per cell of the D3Q19 FP64 collide (dadd + dmul + 2 dfma thread
+# instructions per cell, counted by ncu on the 64^3 gauge wave); used when
+# the traffic table holds no count taken on the current sources
+FP64_FLOPS_PER_CELL = 2948.0
+FP64_FLOPS_SOURCE = ("ncu counts of the FP64 collide (64^3 gauge wave), last taken on the "
+                     "tile-blocked layout; the traffic table holds none for these sources")
+
 E2E_REPEATS = 3
 
 
@@ -769,13 +776,16 @@ def precision_records(args, N, device_index):
             # flops (ncu count per cell) against the rate measured here
             flops = profile_entry(f"k_collide:gauge3d-{N}-f64:{rec['launch_form']}",
                                   "fp64_flops_per_cell")
+            source = "ncu counts on the current sources (profiles/traffic.json)"
+            if flops is None:
+                flops, source = FP64_FLOPS_PER_CELL, FP64_FLOPS_SOURCE
             _, col = lat.step_timed(4)
             peak = lbnr.lbnr_fp64_fma_rate(lat.stream)
             rec["collide_ms"] = col / 4
             rec["fp64_peak_tflops_measured"] = peak
-            if flops is not None:
-                ach = flops * cells / (col / 4 * 1e-3) / 1e12
-                rec["alu"] = {"flops_per_cell": flops, "achieved_tflops": ach, "frac": ach / peak}
+            ach = flops * cells / (col / 4 * 1e-3) / 1e12
+            rec["alu"] = {"flops_per_cell": flops, "flops_source": source, "achieved_tflops": ach,
+                          "frac": ach / peak}
         if finite:
             rec["err_vs_analytic"] = float(np.abs(m - exact).max() / A)
             if ref is None:
@@ -894,6 +904,9 @@ def main():
                     "avg_launch_ms": col_ms, "traffic": traffic}
     roofline = hbm_roofline
     flops = profile_entry(tkey, "fp64_flops_per_cell") if storage == "f64" else None
+    flops_source = "ncu counts on the current sources (profiles/traffic.json)"
+    if storage == "f64" and flops is None:
+        flops, flops_source = FP64_FLOPS_PER_CELL, FP64_FLOPS_SOURCE
     if flops is not None:
         # FP64 is bound by the FP64 pipe: its peak is the rate a register
         # FMA-chain kernel sustains on this GPU, measured here
@@ -903,8 +916,8 @@ def main():
                     "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
                     "peak_source": "measured in this run: FP64 FMA chains at full occupancy "
                                    "(lbnr_fp64_fma_rate)",
-                    "flops_per_cell": flops, "avg_launch_ms": col_ms, "traffic": traffic,
-                    "hbm": hbm_roofline}
+                    "flops_per_cell": flops, "flops_source": flops_source,
+                    "avg_launch_ms": col_ms, "traffic": traffic, "hbm": hbm_roofline}
 
     value = units_all / (ms_max * 1e-3) / 1e6
     line = {
