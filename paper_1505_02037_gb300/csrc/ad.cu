@@ -110,7 +110,9 @@ int lbnr_ad_create(const lbnr_grid* grid, int vset, double tau, double dx, doubl
     c->ops = Q == 3 ? ad::table_q3_f64() : Q == 9 ? ad::table_q9_f64() : ad::table_q19_f64();
   else
     c->ops = Q == 3 ? ad::table_q3_f32() : Q == 9 ? ad::table_q9_f32() : ad::table_q19_f32();
-  const size_t fbytes = (size_t)ad::kNFA * Q * ps * (storage == LBNR_F64 ? 8 : 4);
+  // the 37 fields padded to whole words (FP32: 40 slots, FP64: 37)
+  const size_t fbytes = storage == LBNR_F64 ? (size_t)ad::kSlots<double> * Q * ps * 8
+                                            : (size_t)ad::kSlots<float> * Q * ps * 4;
   cudaError_t e = cudaSuccess;
   if (cuda_stream) {
     c->st = static_cast<cudaStream_t>(cuda_stream);

@@ -16,7 +16,6 @@
 #include <type_traits>
 
 #include "../../include/lbnr.h"
-#include <cudaTypedefs.h>
 
 #include "collide_tma.cuh"
 #include "dispatch.h"
@@ -49,34 +48,122 @@ struct Args {
   int slicing;
 };
 
+// Distribution layout: the tile-blocked words of the 16-field scheme, with
+// the 37 fields padded to whole words. A word holds kV consecutive fields of
+// one cell and velocity (four for FP32: 10 words per velocity, slots 37-39
+// held at zero; one for FP64: 37 words). The values of the 32 cells of a tile
+// form one contiguous block, ordered by velocity, then word, then cell.
+template <class S>
+constexpr int kWords = (kNFA + Codec<S>::kV - 1) / Codec<S>::kV;
+template <class S>
+constexpr int kSlots = kWords<S> * Codec<S>::kV;
+
+template <int Q, class S>
+__host__ __device__ __forceinline__ size_t ad_fidx(uint32_t c, int F, int l) {
+  constexpr int V = Codec<S>::kV;
+  constexpr int NW = kWords<S>;
+  return (((size_t)(c >> 5) * (size_t)(NW * Q) + (size_t)(l * NW + F / V)) * lbnr::kTileCells +
+          (c & 31u)) * V + (size_t)(F % V);
+}
+
+// Whole words: read-only path, streaming (last use) load, streaming store.
+template <class S>
+__device__ __forceinline__ typename Codec<S>::W ld_word_keep(const S* p) {
+  if constexpr (Codec<S>::kV == 1)
+    return Codec<S>::load_keep(p);
+  else
+    return WordIO<S>::ldw_keep(p);
+}
+template <class S>
+__device__ __forceinline__ typename Codec<S>::W ld_word_last(const S* p) {
+  if constexpr (Codec<S>::kV == 1)
+    return Codec<S>::load(p);
+  else
+    return WordIO<S>::ldw(p);
+}
+template <class S, class C>
+__device__ __forceinline__ void store_word(S* p, const C* v) {
+  if constexpr (Codec<S>::kV == 1)
+    Codec<S>::store(p, v[0]);
+  else
+    WordIO<S>::stw(p, Codec<S>::pack(v));
+}
+
+// Relaxation coefficient and flux of field F (compile-time F after
+// unrolling): coef = omega rho + sigma S for the 16 fields, omega rho~ for A
+// and D (no source); b[k] = 3 omega times the flux along k.
+template <int dim, class C>
+__device__ __forceinline__ void ad_field_terms(int F, const C rt[kNFA], const C rho[kNF],
+                                               const C Sr[kNF], const C Fl[6][3], C aQ,
+                                               const C aK[6], C omega, C sigma, C& cf, C b[3]) {
+  const C three_omega = C(3) * omega;
+  b[0] = b[1] = b[2] = C(0);
+  if (F < kNF) {
+    cf = omega * rho[F] + sigma * Sr[F];
+    if (has_flux(F)) {
+#pragma unroll
+      for (int k = 0; k < dim; ++k) b[k] = three_omega * Fl[F - kK][k];
+    }
+  } else {
+    cf = omega * rt[F];
+    const int k = F < kD ? F - kA : (F - kD) / 6;
+    const C fk = F < kD ? aQ : aK[(F - kD) % 6];
+#pragma unroll
+    for (int kk = 0; kk < dim; ++kk)
+      if (kk == k) b[kk] = three_omega * fk;
+  }
+}
+// The same for a word's slot F: zero for the padding slots (F >= 37).
+template <int dim, class S, class C>
+__device__ __forceinline__ void ad_word_terms(int F, const C rt[kNFA], const C rho[kNF],
+                                              const C Sr[kNF], const C Fl[6][3], C aQ,
+                                              const C aK[6], const Args<S, C>& a, C& cf, C b[3]) {
+  if (F < kNFA) {
+    ad_field_terms<dim, C>(F, rt, rho, Sr, Fl, aQ, aK, a.omega, a.sigma, cf, b);
+  } else {
+    cf = C(0);
+    b[0] = b[1] = b[2] = C(0);
+  }
+}
+
 // One step: moments, sources (A and D from the cell's own moments), the
-// corrected moments, fluxes at them, relax, stream to x + c_l. MINB: thread
-// blocks of 128 per SM the registers are sized for (the launch forms trade
-// occupancy against spills).
+// corrected moments, fluxes at them, relax, stream to x + c_l, one word
+// (kV fields) per load and store. MINB: thread blocks of 128 per SM the
+// registers are sized for (the launch forms trade occupancy against spills).
 template <int Q, class S, class C, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_ad_collide(const Args<S, C> a) {
   using L = Lattice<Q>;
+  using W = typename Codec<S>::W;
   constexpr int dim = L::kDim;
+  constexpr int V = Codec<S>::kV;
+  constexpr int NW = kWords<S>;
   const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = cell < a.G.cells;
   const int64_t c = valid ? cell : a.G.cells - 1;
-  const uint32_t ps = (uint32_t)a.G.pstride;
   const Nbr n = make_nbr(a.G, c);
 
   C rt[kNFA];
 #pragma unroll
-  for (int F = 0; F < kNFA; ++F) {
-    const S* fb = a.fin + (size_t)F * Q * ps + n.c;
-    C s = C(0);
+  for (int F = 0; F < kNFA; ++F) rt[F] = C(0);
 #pragma unroll
-    for (int l = 0; l < Q; ++l) s += (C)Codec<S>::load_keep(fb + (size_t)l * ps);
-    rt[F] = s;
+  for (int m = 0; m < NW; ++m) {
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+      C v[V];
+      unpack_word<S>(ld_word_keep<S>(a.fin + ad_fidx<Q, S>(n.c, V * m, l)), v);
+#pragma unroll
+      for (int i = 0; i < V; ++i)
+        if (V * m + i < kNFA) rt[V * m + i] += v[i];
+    }
   }
+  // reported after the update pass, so that no global write stands between
+  // the two passes' loads
+  bool bad;
   {
     C chk = C(0);
 #pragma unroll
     for (int F = 0; F < kNFA; ++F) chk += rt[F];
-    if (valid && !isfinite(chk)) atomicOr(a.flag, 1);
+    bad = valid && !isfinite(chk);
   }
   C A[3], D[3][6];
 #pragma unroll
@@ -85,10 +172,10 @@ __global__ void __launch_bounds__(128, MINB) k_ad_collide(const Args<S, C> a) {
 #pragma unroll
     for (int q = 0; q < 6; ++q) D[k][q] = rt[kD + 6 * k + q];
   }
-  C alpha, gm[6], K[6], V[3];
-  unpack<kABS, C>(rt, alpha, gm, K, V);
+  C alpha, gm[6], K[6], Vv[3];
+  unpack<kABS, C>(rt, alpha, gm, K, Vv);
   C Sr[kNF];
-  bm_sources<C>(alpha, gm, K, V, A, D, a.slicing, Sr);
+  bm_sources<C>(alpha, gm, K, Vv, A, D, a.slicing, Sr);
   C rho[kNF];
 #pragma unroll
   for (int F = 0; F < kNF; ++F) rho[F] = rt[F] + a.half_dt * Sr[F];
@@ -101,51 +188,34 @@ __global__ void __launch_bounds__(128, MINB) k_ad_collide(const Args<S, C> a) {
 #pragma unroll
     for (int q = 0; q < 6; ++q) aK[q] = alpha2 * K2[q];
   }
-  C coef[kNF];
-#pragma unroll
-  for (int F = 0; F < kNF; ++F) coef[F] = a.omega * rho[F] + a.sigma * Sr[F];
-  const C three_omega = C(3) * a.omega;
 
 #pragma unroll
-  for (int F = 0; F < kNFA; ++F) {
-    const S* fb = a.fin + (size_t)F * Q * ps + n.c;
-    S* ob = a.fout + (size_t)F * Q * ps;
-    C v_[Q];
+  for (int m = 0; m < NW; ++m) {
+    W vw[Q];
 #pragma unroll
-    for (int l = 0; l < Q; ++l) v_[l] = (C)Codec<S>::load(fb + (size_t)l * ps);
-    C cf;
-    C b[3] = {C(0), C(0), C(0)};
-    if (F < kNF) {
-      cf = coef[F];
-      if (has_flux(F)) {
+    for (int l = 0; l < Q; ++l) vw[l] = ld_word_last<S>(a.fin + ad_fidx<Q, S>(n.c, V * m, l));
+    C cf[V], b[V][3];
 #pragma unroll
-        for (int k = 0; k < dim; ++k) b[k] = three_omega * Fl[F - kK][k];
-      }
-    } else {
-      // A and D have no source: coef = omega rho~, the sum of this field's
-      // own values, in the order of the moment pass.
-      C s = C(0);
-#pragma unroll
-      for (int l = 0; l < Q; ++l) s += v_[l];
-      cf = a.omega * s;
-      const int k = F < kD ? F - kA : (F - kD) / 6;
-      const C fk = F < kD ? aQ : aK[(F - kD) % 6];
-#pragma unroll
-      for (int kk = 0; kk < dim; ++kk)
-        if (kk == k) b[kk] = three_omega * fk;
-    }
+    for (int i = 0; i < V; ++i) ad_word_terms<dim>(V * m + i, rt, rho, Sr, Fl, aQ, aK, a, cf[i], b[i]);
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
-      C t = cf;
+      C v[V], out[V];
+      unpack_word<S>(vw[l], v);
 #pragma unroll
-      for (int k = 0; k < dim; ++k) {
-        if (L::c(l, k) > 0) t += b[k];
-        if (L::c(l, k) < 0) t -= b[k];
+      for (int i = 0; i < V; ++i) {
+        C t = cf[i];
+#pragma unroll
+        for (int k = 0; k < dim; ++k) {
+          if (L::c(l, k) > 0) t += b[i][k];
+          if (L::c(l, k) < 0) t -= b[i][k];
+        }
+        // padding slots stay zero
+        out[i] = V * m + i < kNFA ? fma(a.omc, v[i], C(L::w(l)) * t) : C(0);
       }
-      const C out = fma(a.omc, v_[l], C(L::w(l)) * t);
-      Codec<S>::store(ob + (size_t)l * ps + n.at(L::c(l, 0), L::c(l, 1), L::c(l, 2)), out);
+      store_word<S>(a.fout + ad_fidx<Q, S>(n.at(L::c(l, 0), L::c(l, 1), L::c(l, 2)), V * m, l), out);
     }
   }
+  if (bad) atomicOr(a.flag, 1);
 }
 
 // Initial distributions f = f_eq(v) - (dt/2) w S(v) from nf = 16 fields
@@ -216,9 +286,14 @@ __global__ void __launch_bounds__(128) k_ad_init(const double* __restrict__ fiel
       const double s = F < kNF ? Sr[F] : 0.0;
       const double val = L::w(l) * (v[F] + 3.0 * cf) - half_dt * L::w(l) * s;
       bad |= !isfinite(val);
-      Codec<S>::store(f + (size_t)(F * Q + l) * G.pstride + c, (decltype(Codec<S>::load(f)))val);
+      Codec<S>::store(f + ad_fidx<Q, S>((uint32_t)c, F, l), (decltype(Codec<S>::load(f)))val);
     }
   }
+  // padding slots of the last word
+#pragma unroll
+  for (int F = kNFA; F < kSlots<S>; ++F)
+#pragma unroll
+    for (int l = 0; l < Q; ++l) Codec<S>::store(f + ad_fidx<Q, S>((uint32_t)c, F, l), 0.0f);
   if (bad) atomicOr(flag, 1);
 }
 
@@ -235,7 +310,7 @@ __global__ void __launch_bounds__(128) k_ad_moments(const S* __restrict__ f,
   for (int F = 0; F < kNFA; ++F) {
     double s = 0;
 #pragma unroll
-    for (int l = 0; l < Q; ++l) s += (double)Codec<S>::load_keep(f + (size_t)(F * Q + l) * G.pstride + c);
+    for (int l = 0; l < Q; ++l) s += (double)Codec<S>::load_keep(f + ad_fidx<Q, S>((uint32_t)c, F, l));
     rt[F] = s;
   }
   double A[3], D[3][6];
@@ -259,31 +334,20 @@ inline unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b
 // ---------------------------------------------------------------------------
 // Shared-memory staged form: every distribution is read from HBM once
 // ---------------------------------------------------------------------------
-// One persistent CTA per SM. Warp NC (the producer) streams tiles of 32
-// consecutive cells, all 37*Q planes of each, into NS shared-memory stages
-// through 2D tensor copies of 37 planes each. Each stage belongs to a group
-// of P consumer warps, which takes the CTA's tiles s, s + NS, ... With P = 2
-// two lanes share a cell: each sums half of the 37 moments from shared
-// memory and the partner lanes swap them, both evaluate the cell's sources
-// and fluxes, and each relaxes and stores its half of the fields. The group
-// then frees the stage. Every wait is bounded (~2 s, then bit 1 of the flag).
+// One persistent CTA per SM. Warp NC (the producer) copies each tile of 32
+// consecutive cells, the contiguous block of its words, into one of NS
+// shared-memory stages with one bulk copy (cp.async.bulk). Each stage belongs
+// to a group of P consumer warps, which takes the CTA's tiles s, s + NS, ...
+// With P = 2 two lanes share a cell: each sums the fields of half of the
+// words from shared memory and the partner lanes swap them, both evaluate the
+// cell's sources and fluxes, and each relaxes and stores its half of the
+// words. The group then frees the stage. Every wait is bounded (~2 s, then
+// bit 1 of the flag).
 constexpr int kTileCells = 32;
-constexpr int kPlanesPerBox = kNFA;  // 37*Q planes = Q boxes of 37
-
-// 2D tensor copy of one box (x = cell, y = plane) into shared memory,
-// completing on the mbarrier.
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int32_t x,
-                                            int32_t y, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
 
 template <class S>
 __host__ __device__ constexpr uint32_t tma_stage(int Q) {
-  return (uint32_t)(kNFA * Q * kTileCells * sizeof(S));
+  return (uint32_t)(kSlots<S> * Q * kTileCells * sizeof(S));
 }
 // Stages that fit the 227 KB of shared memory (at most 4).
 template <class S>
@@ -292,45 +356,20 @@ __host__ __device__ constexpr int tma_stages(int Q) {
                                                        : (int)((232448u - 1024u) / tma_stage<S>(Q));
 }
 
-// Relaxation coefficient and flux of field F (compile-time F after
-// unrolling): coef = omega rho + sigma S for the 16 fields, omega rho~ for A
-// and D (no source); b[k] = 3 omega times the flux along k.
-template <int dim, class C>
-__device__ __forceinline__ void ad_field_terms(int F, const C rt[kNFA], const C rho[kNF],
-                                               const C Sr[kNF], const C Fl[6][3], C aQ,
-                                               const C aK[6], C omega, C sigma, C& cf, C b[3]) {
-  const C three_omega = C(3) * omega;
-  b[0] = b[1] = b[2] = C(0);
-  if (F < kNF) {
-    cf = omega * rho[F] + sigma * Sr[F];
-    if (has_flux(F)) {
-#pragma unroll
-      for (int k = 0; k < dim; ++k) b[k] = three_omega * Fl[F - kK][k];
-    }
-  } else {
-    cf = omega * rt[F];
-    const int k = F < kD ? F - kA : (F - kD) / 6;
-    const C fk = F < kD ? aQ : aK[(F - kD) % 6];
-#pragma unroll
-    for (int kk = 0; kk < dim; ++kk)
-      if (kk == k) b[kk] = three_omega * fk;
-  }
-}
-
 template <int Q, class S, class C, int NS, int P>
 __global__ void __launch_bounds__(32 * (NS * P + 1), 1)
-    k_ad_collide_tma(const Args<S, C> a, const __grid_constant__ CUtensorMap tmap, int64_t ntiles) {
+    k_ad_collide_tma(const Args<S, C> a, int64_t ntiles) {
   static_assert(P == 1 || P == 2, "one or two lanes per cell");
   using L = Lattice<Q>;
+  using W = typename Codec<S>::W;
   constexpr int dim = L::kDim;
   constexpr int T = kTileCells;
+  constexpr int V = Codec<S>::kV;
+  constexpr int NW = kWords<S>;
   constexpr int NC = NS * P;  // consumer warps
-  constexpr int kBoxes = Q;
-  constexpr uint32_t ROWB = T * sizeof(S);
-  constexpr uint32_t BOXB = kPlanesPerBox * ROWB;
   constexpr uint32_t STAGEB = tma_stage<S>(Q);
   constexpr uint64_t kLimitNs = 2000000000ull;
-  static_assert(BOXB % 128 == 0 && STAGEB % 128 == 0, "tensor copies land on 128-byte rows");
+  static_assert(STAGEB % 16 == 0, "bulk copies move multiples of 16 bytes");
 
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);  // [0,NS) full, [NS,2NS) empty
@@ -365,10 +404,8 @@ __global__ void __launch_bounds__(32 * (NS * P + 1), 1)
         }
         const uint32_t fb = smem_u32(&bars[s]);
         mbar_expect_tx(fb, STAGEB);
-        const uint32_t dst = smem_u32(stages + (size_t)s * STAGEB);
-#pragma unroll 1
-        for (int b = 0; b < kBoxes; ++b)
-          tma_load_2d(dst + b * BOXB, &tmap, (int32_t)(tile * T), b * kPlanesPerBox, fb);
+        bulk_load(smem_u32(stages + (size_t)s * STAGEB),
+                  a.fin + (size_t)tile * (size_t)(kSlots<S> * Q * T), STAGEB, fb);
         issued = j + 1;
       }
       // leave only when every copy started here has landed
@@ -384,10 +421,9 @@ __global__ void __launch_bounds__(32 * (NS * P + 1), 1)
 
   // ---------------- consumers ----------------
   const int s = warp / P;
-  const int g = P == 2 ? (lane >> 4) : 0;  // which half of the fields this lane owns
+  const int g = P == 2 ? (lane >> 4) : 0;  // which half of the words this lane owns
   const int ci = P == 2 ? (warp % P) * 16 + (lane & 15) : lane;
   const int64_t cells = a.G.cells;
-  const uint32_t ps = (uint32_t)a.G.pstride;
   for (int64_t m = 0;; ++m) {
     const int64_t j = s + m * NS;
     if (j >= my) break;
@@ -401,42 +437,71 @@ __global__ void __launch_bounds__(32 * (NS * P + 1), 1)
       break;
     }
     const S* st = reinterpret_cast<const S*>(stages + (size_t)s * STAGEB);
+    auto word = [&](int w, int l) -> W {
+      return *reinterpret_cast<const W*>(st + ad_fidx<Q, S>((uint32_t)ci, V * w, l));
+    };
     C rt[kNFA];
     if constexpr (P == 1) {
 #pragma unroll
-      for (int F = 0; F < kNFA; ++F) {
-        const S* row = st + (F * Q) * T + ci;
-        C sum = C(0);
+      for (int w = 0; w < NW; ++w) {
+        C sum[V];
 #pragma unroll
-        for (int l = 0; l < Q; ++l) sum += (C)row[l * T];
-        rt[F] = sum;
+        for (int i = 0; i < V; ++i) sum[i] = C(0);
+#pragma unroll
+        for (int l = 0; l < Q; ++l) {
+          C v[V];
+          unpack_word<S>(word(w, l), v);
+#pragma unroll
+          for (int i = 0; i < V; ++i) sum[i] += v[i];
+        }
+#pragma unroll
+        for (int i = 0; i < V; ++i)
+          if (V * w + i < kNFA) rt[V * w + i] = sum[i];
       }
     } else {
-      // fields 2jj (lanes g = 0) and 2jj + 1 (g = 1), swapped between
-      // partner lanes; both lanes sum field 36
+      // words 2jj (lanes g = 0) and 2jj + 1 (g = 1), swapped between partner
+      // lanes; with an odd word count both lanes sum the last word
 #pragma unroll
-      for (int jj = 0; jj < kNFA / 2; ++jj) {
-        const S* row = st + ((2 * jj + g) * Q) * T + ci;
-        C sum = C(0);
+      for (int jj = 0; jj < NW / 2; ++jj) {
+        C sum[V];
 #pragma unroll
-        for (int l = 0; l < Q; ++l) sum += (C)row[l * T];
-        const C other = __shfl_xor_sync(0xffffffffu, sum, 16);
-        rt[2 * jj] = g ? other : sum;
-        rt[2 * jj + 1] = g ? sum : other;
+        for (int i = 0; i < V; ++i) sum[i] = C(0);
+#pragma unroll
+        for (int l = 0; l < Q; ++l) {
+          C v[V];
+          unpack_word<S>(word(2 * jj + g, l), v);
+#pragma unroll
+          for (int i = 0; i < V; ++i) sum[i] += v[i];
+        }
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+          const C other = __shfl_xor_sync(0xffffffffu, sum[i], 16);
+          if (V * (2 * jj) + i < kNFA) rt[V * (2 * jj) + i] = g ? other : sum[i];
+          if (V * (2 * jj + 1) + i < kNFA) rt[V * (2 * jj + 1) + i] = g ? sum[i] : other;
+        }
       }
-      {
-        const S* row = st + ((kNFA - 1) * Q) * T + ci;
-        C sum = C(0);
+      if constexpr (NW % 2 == 1) {
+        C sum[V];
 #pragma unroll
-        for (int l = 0; l < Q; ++l) sum += (C)row[l * T];
-        rt[kNFA - 1] = sum;
+        for (int i = 0; i < V; ++i) sum[i] = C(0);
+#pragma unroll
+        for (int l = 0; l < Q; ++l) {
+          C v[V];
+          unpack_word<S>(word(NW - 1, l), v);
+#pragma unroll
+          for (int i = 0; i < V; ++i) sum[i] += v[i];
+        }
+#pragma unroll
+        for (int i = 0; i < V; ++i)
+          if (V * (NW - 1) + i < kNFA) rt[V * (NW - 1) + i] = sum[i];
       }
     }
+    bool bad;
     {
       C chk = C(0);
 #pragma unroll
       for (int F = 0; F < kNFA; ++F) chk += rt[F];
-      if (valid && g == 0 && !isfinite(chk)) atomicOr(a.flag, 1);
+      bad = valid && g == 0 && !isfinite(chk);
     }
     C A[3], D[3][6];
 #pragma unroll
@@ -445,10 +510,10 @@ __global__ void __launch_bounds__(32 * (NS * P + 1), 1)
 #pragma unroll
       for (int q = 0; q < 6; ++q) D[k][q] = rt[kD + 6 * k + q];
     }
-    C alpha, gm[6], K[6], V[3];
-    unpack<kABS, C>(rt, alpha, gm, K, V);
+    C alpha, gm[6], K[6], Vv[3];
+    unpack<kABS, C>(rt, alpha, gm, K, Vv);
     C Sr[kNF];
-    bm_sources<C>(alpha, gm, K, V, A, D, a.slicing, Sr);
+    bm_sources<C>(alpha, gm, K, Vv, A, D, a.slicing, Sr);
     C rho[kNF];
 #pragma unroll
     for (int F = 0; F < kNF; ++F) rho[F] = rt[F] + a.half_dt * Sr[F];
@@ -461,96 +526,76 @@ __global__ void __launch_bounds__(32 * (NS * P + 1), 1)
 #pragma unroll
       for (int q = 0; q < 6; ++q) aK[q] = alpha2 * K2[q];
     }
-    uint32_t woff[Q];
-#pragma unroll
-    for (int l = 0; l < Q; ++l) woff[l] = (uint32_t)l * ps + n.at(L::c(l, 0), L::c(l, 1), L::c(l, 2));
 
-    // relax and store: field F of this lane, coefficients cf and b
-    auto relax = [&](int F, C cf, const C b[3], bool store) {
-      const S* row = st + (F * Q) * T + ci;
-      S* ob = a.fout + (size_t)F * Q * ps;
+    // relax and store word w of this cell with coefficients cf and b
+    auto relax = [&](int w, const C cf[V], const C b[V][3], bool store) {
 #pragma unroll
       for (int l = 0; l < Q; ++l) {
-        C t = cf;
+        C v[V], out[V];
+        unpack_word<S>(word(w, l), v);
 #pragma unroll
-        for (int k = 0; k < dim; ++k) {
-          if (L::c(l, k) > 0) t += b[k];
-          if (L::c(l, k) < 0) t -= b[k];
+        for (int i = 0; i < V; ++i) {
+          C t = cf[i];
+#pragma unroll
+          for (int k = 0; k < dim; ++k) {
+            if (L::c(l, k) > 0) t += b[i][k];
+            if (L::c(l, k) < 0) t -= b[i][k];
+          }
+          out[i] = fma(a.omc, v[i], C(L::w(l)) * t);
         }
-        const C out = fma(a.omc, (C)row[l * T], C(L::w(l)) * t);
-        Codec<S>::store_if(ob + woff[l], out, store);
+        store_word_if<S>(a.fout + ad_fidx<Q, S>(n.at(L::c(l, 0), L::c(l, 1), L::c(l, 2)), V * w, l),
+                         out, store);
       }
     };
     if constexpr (P == 1) {
 #pragma unroll
-      for (int F = 0; F < kNFA; ++F) {
-        C cf, b[3];
-        ad_field_terms<dim, C>(F, rt, rho, Sr, Fl, aQ, aK, a.omega, a.sigma, cf, b);
-        relax(F, cf, b, valid);
+      for (int w = 0; w < NW; ++w) {
+        C cf[V], b[V][3];
+#pragma unroll
+        for (int i = 0; i < V; ++i) ad_word_terms<dim>(V * w + i, rt, rho, Sr, Fl, aQ, aK, a, cf[i], b[i]);
+        relax(w, cf, b, valid);
       }
     } else {
 #pragma unroll
-      for (int jj = 0; jj < kNFA / 2; ++jj) {
-        C cf0, b0[3], cf1, b1[3];
-        ad_field_terms<dim, C>(2 * jj, rt, rho, Sr, Fl, aQ, aK, a.omega, a.sigma, cf0, b0);
-        ad_field_terms<dim, C>(2 * jj + 1, rt, rho, Sr, Fl, aQ, aK, a.omega, a.sigma, cf1, b1);
-        const C b[3] = {g ? b1[0] : b0[0], g ? b1[1] : b0[1], g ? b1[2] : b0[2]};
-        relax(2 * jj + g, g ? cf1 : cf0, b, valid);
+      for (int jj = 0; jj < NW / 2; ++jj) {
+        C cf0[V], b0[V][3], cf1[V], b1[V][3], cf[V], b[V][3];
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+          ad_word_terms<dim>(V * (2 * jj) + i, rt, rho, Sr, Fl, aQ, aK, a, cf0[i], b0[i]);
+          ad_word_terms<dim>(V * (2 * jj + 1) + i, rt, rho, Sr, Fl, aQ, aK, a, cf1[i], b1[i]);
+          cf[i] = g ? cf1[i] : cf0[i];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) b[i][k] = g ? b1[i][k] : b0[i][k];
+        }
+        relax(2 * jj + g, cf, b, valid);
       }
-      C cf, b[3];
-      ad_field_terms<dim, C>(kNFA - 1, rt, rho, Sr, Fl, aQ, aK, a.omega, a.sigma, cf, b);
-      relax(kNFA - 1, cf, b, valid && g == 0);
+      if constexpr (NW % 2 == 1) {
+        C cf[V], b[V][3];
+#pragma unroll
+        for (int i = 0; i < V; ++i) ad_word_terms<dim>(V * (NW - 1) + i, rt, rho, Sr, Fl, aQ, aK, a, cf[i], b[i]);
+        relax(NW - 1, cf, b, valid && g == 0);
+      }
     }
+    if (bad) atomicOr(a.flag, 1);
     __syncwarp();
     if (lane == 0) mbar_arrive(smem_u32(&bars[NS + s]));
   }
 }
 
-// One distribution plane of the 37-field state (plane layout: all cells of
-// one (F, l) contiguous) to FP64 and back.
-template <class S>
-__global__ void k_ad_get_plane(const S* __restrict__ plane, double* __restrict__ out, int64_t cells) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < cells) out[c] = (double)Codec<S>::load_keep(plane + c);
-}
-template <class S>
-__global__ void k_ad_set_plane(S* __restrict__ plane, const double* __restrict__ in, int64_t cells) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < cells) Codec<S>::store(plane + c, (decltype(Codec<S>::load(plane)))in[c]);
-}
-
-// cuTensorMapEncodeTiled through the runtime's driver entry point.
-inline PFN_cuTensorMapEncodeTiled_v12000 ad_tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
-// 2D view of a 37-field buffer: x = cell (stride 1), y = plane (37*Q planes,
-// stride pstride); boxes of 32 cells x 37 planes.
+// One (F, l) of every cell of the 37-field state to FP64 and back.
 template <int Q, class S>
-cudaError_t encode_ad_planes(const void* base, int64_t pstride, CUtensorMap* map) {
-  auto fn = ad_tensor_map_encoder();
-  if (!fn) return cudaErrorNotSupported;
-  const cuuint64_t dims[2] = {(cuuint64_t)pstride, (cuuint64_t)(kNFA * Q)};
-  const cuuint64_t strides[1] = {(cuuint64_t)pstride * sizeof(S)};
-  const cuuint32_t box[2] = {(cuuint32_t)kTileCells, (cuuint32_t)kPlanesPerBox};
-  const cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, sizeof(S) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                  2, const_cast<void*>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                  CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+__global__ void k_ad_get_plane(const S* __restrict__ f, double* __restrict__ out, int64_t cells,
+                               int F, int l) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < cells) out[c] = (double)Codec<S>::load_keep(f + ad_fidx<Q, S>((uint32_t)c, F, l));
+}
+template <int Q, class S>
+__global__ void k_ad_set_plane(S* __restrict__ f, const double* __restrict__ in, int64_t cells,
+                               int F, int l) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < cells) Codec<S>::store(f + ad_fidx<Q, S>((uint32_t)c, F, l), (decltype(Codec<S>::load(f)))in[c]);
 }
 
-// Per-(Q, storage) launchers.
 template <int Q, class S>
 struct Ops {
   using C = typename std::conditional<sizeof(S) == 8, double, float>::type;
@@ -589,15 +634,12 @@ struct Ops {
     auto kern = k_ad_collide_tma<Q, S, C, NS, P>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    CUtensorMap map;
-    e = encode_ad_planes<Q, S>(fin, G.pstride, &map);
-    if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t ntiles = G.pstride / kTileCells;
     const int64_t grid = ntiles < sms ? ntiles : (sms > 0 ? sms : 1);
-    kern<<<(unsigned)grid, 32 * (NS * P + 1), smem, st>>>(a, map, ntiles);
+    kern<<<(unsigned)grid, 32 * (NS * P + 1), smem, st>>>(a, ntiles);
     return cudaGetLastError();
   }
   static cudaError_t init(const Grid& G, const double* fields, int nf, void* f, int* flag,
@@ -615,14 +657,14 @@ struct Ops {
   }
   static cudaError_t get_plane(const Grid& G, const void* f, int F, int l, double* out,
                                cudaStream_t st) {
-    k_ad_get_plane<S><<<blocks_for(G.cells, 256), 256, 0, st>>>(
-        static_cast<const S*>(f) + (size_t)(F * Q + l) * G.pstride, out, G.cells);
+    k_ad_get_plane<Q, S><<<blocks_for(G.cells, 256), 256, 0, st>>>(static_cast<const S*>(f), out,
+                                                                   G.cells, F, l);
     return cudaGetLastError();
   }
   static cudaError_t set_plane(const Grid& G, void* f, int F, int l, const double* in,
                                cudaStream_t st) {
-    k_ad_set_plane<S><<<blocks_for(G.cells, 256), 256, 0, st>>>(
-        static_cast<S*>(f) + (size_t)(F * Q + l) * G.pstride, in, G.cells);
+    k_ad_set_plane<Q, S><<<blocks_for(G.cells, 256), 256, 0, st>>>(static_cast<S*>(f), in,
+                                                                   G.cells, F, l);
     return cudaGetLastError();
   }
 };
