@@ -434,13 +434,13 @@ int64_t lbnr_ad_steps_done(const lbnr_ad_ctx* ctx);
  * registers sized for lbnr_ad_form_blocks(form) blocks per SM (2 to 5: more
  * warps in flight against more spilled values), and two shared-memory
  * staged forms (lbnr_ad_form_blocks 0: one lane per cell, -1: two lanes per
- * cell, each owning half the fields): one persistent block per SM whose
- * producer warp streams tiles of 32 cells, all 37*Q planes, into shared
- * memory with tensor copies, so every distribution is read from HBM once;
- * their waits are bounded and a timeout sets LBNR_ETIMEOUT in
+ * cell, each owning half the words): one persistent block per SM whose
+ * producer warp copies each tile of 32 cells, its contiguous block of words,
+ * into shared memory with one bulk copy, so every distribution is read from
+ * HBM once; their waits are bounded and a timeout sets LBNR_ETIMEOUT in
  * lbnr_ad_status. All forms compute the same values. lbnr_ad_form_blocks
  * returns -100 for an unknown form, lbnr_ad_set_form LBNR_EINVAL. Defaults:
- * 2 blocks per SM with FP64 storage, the two-lane staged form with FP32. */
+ * 2 blocks per SM with FP64 storage, the one-lane staged form with FP32. */
 int lbnr_ad_num_forms(void);
 int lbnr_ad_form_blocks(int form);
 int lbnr_ad_set_form(lbnr_ad_ctx* ctx, int form);

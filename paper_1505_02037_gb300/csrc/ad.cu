@@ -104,8 +104,8 @@ int lbnr_ad_create(const lbnr_grid* grid, int vset, double tau, double dx, doubl
   c->dt = dt;
   c->G = make_grid(grid->nx, grid->ny, grid->nz, (int64_t)cells, (int64_t)ps);
   // the fastest forms on GB300: registers for 2 blocks per SM (FP64), the
-  // staged form with two lanes per cell (FP32)
-  c->form = storage == LBNR_F64 ? 0 : 5;
+  // staged form with one lane per cell (FP32)
+  c->form = storage == LBNR_F64 ? 0 : 4;
   if (storage == LBNR_F64)
     c->ops = Q == 3 ? ad::table_q3_f64() : Q == 9 ? ad::table_q9_f64() : ad::table_q19_f64();
   else
