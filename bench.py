@@ -108,6 +108,9 @@ def parse():
     p.add_argument("--profile-steps", type=int, default=20)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--launches-per-crossing", type=int, default=8,
+                   help="batched workload: launches per crossing time (each run advances N / this "
+                        "many steps per launch, and the blocks are re-planned between launches)")
     p.add_argument("--deriv", default="sync", choices=["sync", "lag"],
                    help="time level of A and D for the batched workload (lag: one pass and "
                         "one team barrier per step)")
@@ -328,7 +331,7 @@ def median_of(fn, repeats=E2E_REPEATS):
     return statistics.median(fn() for _ in range(repeats))
 
 
-def batched_config(world_rank_seed_note=""):
+def batched_config(world_rank_seed_note="", sub=8):
     return {
         "workload": "ensemble of 512 independent gauge-wave runs (seed 150502037): 1D D1Q3 "
                     "N~U{64..4096} or 2D D2Q9 NxN, N~U{64..512} (x-aligned for even run id, "
@@ -336,8 +339,8 @@ def batched_config(world_rank_seed_note=""):
                     "times (10 N steps) per run, FP32 deviation storage, one persistent "
                     "cooperative launch per step (graph-captured)" + world_rank_seed_note,
         "workload_key": "batched", "runs": 512, "fields": 16,
-        "step": "every run advances one crossing time: 4 launches of ceil(N/4) steps each, "
-                "the work re-planned over the live runs before each launch; 10 steps = the "
+        "step": f"every run advances one crossing time: {sub} launches of ceil(N/{sub}) steps "
+                "each, the work re-planned over the live runs before each launch; 10 steps = the "
                 "whole configuration from t = 0",
         "tau_note": "every tau in [0.51, 2] is linearly unstable for this scheme; a run whose "
                     "moments turn non-finite stops at that step and only the steps actually "
@@ -576,7 +579,7 @@ def main_batched(args):
 
     # each rank its own ensemble (independent problems; rank 0 = the seed above)
     specs = W.ensemble(seed=ENSEMBLE_SEED + rank)
-    sub = 4  # launches per crossing time
+    sub = args.launches_per_crossing  # launches per crossing time
     for r in specs:
         r["steps_total"] = r["steps"]
         r["steps"] = -(-r["N"] // sub)
@@ -638,7 +641,7 @@ def main_batched(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 (f32 deviation storage)", "data": "synthetic",
-        "config": dict(batched_config(), l2="inputs larger than L2 (%.1f GB of distributions)"
+        "config": dict(batched_config(sub=sub), l2="inputs larger than L2 (%.1f GB of distributions)"
                        % (sum(c * 16 * q * 4 * 2 for c, q in zip(cells, qs)) / 1e9),
                        parallelism="one ensemble per GPU" if world > 1 else "single GPU",
                        cell_steps_taken=int(taken @ np.array(cells)),
