@@ -15,7 +15,7 @@
 // occupancy does not depend on the 16 Q distributions of a cell.
 //
 // Reads must be local (ping-pong, or AA at an even step): the stage holds
-// the planes of the tile's own cells. Every wait is bounded: after ~2 s the
+// the words of the tile's own cells. Every wait is bounded: after ~2 s the
 // kernel sets bit 1 of the flag word and leaves.
 #pragma once
 
@@ -79,6 +79,8 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
       : "memory");
 }
 
+// Values per cell: 16 fields times Q velocities (a tile's block holds 32
+// cells of them).
 template <int Q>
 struct TmaShape {
   static constexpr int kPlanes = kNF * Q;

@@ -4,12 +4,16 @@
 // rho = sum_l f_l + dt S / 2 (Sec. "Lattice Boltzmann Model").
 //
 // One step = k_aux (zeroth moments of alpha and gamma -> 7 planes used by the
-// derivative stencil) + k_collide (moments of all 16 fields, A and D by
-// central differences, sources at rho~, corrected rho, flux at rho,
-// equilibria, BGK relaxation plus source, streaming).
+// derivative stencil) + the collide kernel (k_collide_w, word by word, for
+// FP32 and 16-bit storage; k_collide, value by value, for FP64; or the
+// bulk-copy-fed k_collide_tma): moments of all 16 fields, A and D by central
+// differences, sources at rho~, corrected rho, flux at rho, equilibria, BGK
+// relaxation plus source, streaming. Under LAG (reading R17) the collide
+// kernel writes the next step's stencil planes itself and k_aux goes.
 //
-// Memory: SoA planes. Plane p = F*Q + l holds f_{F,l} for every cell,
-// x fastest, so each warp touches 32 consecutive cells of one plane.
+// Memory: tile-blocked words (fidx below). The 16 Q values of 32 consecutive
+// cells (x fastest) form one block; a word holds kV fields of one cell and
+// velocity, and a warp's 32 cells of one (word, l) are one aligned row.
 //
 // Streaming layouts (the state after n steps):
 //   ping-pong: f_l(x) at (l, x) of the current buffer; a step writes f*_l(x)
@@ -151,7 +155,7 @@ struct Codec<__half> {
   }
 };
 
-// Whole distribution words (two values): ldw streams (evict-first),
+// Whole distribution words (four values): ldw streams (evict-first),
 // ldw_keep takes the read-only path, ldw_coh reads coherently through L2;
 // stw streams a word out, stw_if under a predicate.
 template <class S>
@@ -270,17 +274,19 @@ __device__ __forceinline__ Nbr make_nbr(const Grid& G, int64_t c64) {
   return n;
 }
 
-// Distribution layout in HBM: tile-blocked. The 16 Q values of the 32
+// Distribution layout in HBM: tile-blocked words. The 16 Q values of the 32
 // consecutive cells of a tile form one contiguous block, ordered by velocity,
 // then field word, then cell. A word holds kV consecutive fields of one
-// (cell, velocity): kV = 2 for 16-bit storage (fields 2m, 2m+1 side by side in
-// 32 bits), else 1. With W = 16 / kV words per velocity, f_{F,l}(c) sits at
+// (cell, velocity): kV = 4 for FP32 (a 16-byte float4) and for 16-bit storage
+// (8 bytes), 1 for FP64. With W = 16 / kV words per velocity, f_{F,l}(c) sits at
 //   (((c / 32) W Q + l W + F / kV) 32 + c % 32) kV + F % kV.
 // A warp's 32 cells of one (word, l) are one aligned row of 32 words, the
 // fields of one velocity are W consecutive rows, and a tile's whole state is
-// one block. With one plane per (F, l) instead (all cells of a plane contiguous),
-// the 600-odd tiles in flight on the GPU touch 16 Q separate DRAM regions
-// each, and the step ran 11 % slower (256^3 D3Q19 FP32 on GB300).
+// one block. With one plane per (F, l) instead (all cells of a plane
+// contiguous, one value per access), the 600-odd tiles in flight on the GPU
+// touched 16 Q separate DRAM regions each and every thread issued 16 Q loads
+// per pass: the FP32 collide ran at 0.65 of the copy bandwidth, against 0.72
+// with tile blocks and 0.99 with tile-blocked words (256^3 D3Q19, GB300).
 constexpr int kTileCells = 32;
 template <int Q, class S>
 __host__ __device__ __forceinline__ size_t fidx(uint32_t c, int F, int l) {
@@ -657,11 +663,11 @@ __device__ __forceinline__ void cell_terms(const StepArgs<S, C>& a, const Nbr& n
 }
 
 // ---------------------------------------------------------------------------
-// k_collide_w: one thread per cell for 16-bit storage, word by word
+// k_collide_w: one thread per cell for FP32 and 16-bit storage, word by word
 // ---------------------------------------------------------------------------
-// The step of k_collide with P = 1 and every load and store moving a whole
-// word of kV consecutive fields of one (cell, velocity): a kV-th of the
-// memory instructions of value-by-value access. HOLD keeps the words of a
+// The step of k_collide with every load and store moving a whole word of kV
+// consecutive fields of one (cell, velocity): a kV-th of the memory
+// instructions of value-by-value access. HOLD keeps the words of a
 // cell in registers between the passes. SHIFT as in k_collide: 1 a constant
 // shift, 2 a static shift field; under a shift the V fields take the flux
 // -beta^k V_i at the corrected moments. TPB: threads per block.
@@ -720,7 +726,7 @@ __global__ void __launch_bounds__(TPB, HOLD ? 1 : MINB) k_collide_w(const StepAr
   cell_terms<Q, S, C, REP, SHIFT>(a, n, rt, A, D, rho, Sr, Fl, Fv);
   const C three_omega = C(3) * a.omega;
 
-  // Pass 2: relax, add the source, stream; all Q words of a field pair are
+  // Pass 2: relax, add the source, stream; all Q words of a field group are
   // read before any is written (in place they share the Q locations).
 #pragma unroll
   for (int m = 0; m < NW; ++m) {
