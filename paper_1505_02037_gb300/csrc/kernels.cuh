@@ -785,18 +785,30 @@ __global__ void __launch_bounds__(256) k_aux(const S* __restrict__ f, C* __restr
   using L = Lattice<Q>;
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= G.cells) return;
+  constexpr int V = Codec<S>::kV;
+  constexpr int NW = (7 + V - 1) / V;  // the words holding fields 0..6
   const Nbr n = make_nbr(G, c);
+  C s[NW * V];
 #pragma unroll
-  for (int F = 0; F < 7; ++F) {
-    C s = C(0);
+  for (int F = 0; F < NW * V; ++F) s[F] = C(0);
+#pragma unroll
+  for (int m = 0; m < NW; ++m) {
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
-      const C v = Codec<S>::load_keep(f + read_index<Q, LAYOUT, S>(n, F, l));
-      s += REP == kDEV ? C(L::w(l)) * v : v;
+      const S* src = f + read_index<Q, LAYOUT, S>(n, V * m, l);
+      C v[V];
+      if constexpr (V > 1)
+        Codec<S>::unpack(WordIO<S>::ldw_keep(src), v);
+      else
+        v[0] = Codec<S>::load_keep(src);
+#pragma unroll
+      for (int i = 0; i < V; ++i)
+        if (V * m + i < 7) s[V * m + i] += REP == kDEV ? C(L::w(l)) * v[i] : v[i];
     }
-    if (F == 0) s = REP == kDEV ? log1p(s) : log(s);
-    aux[(int64_t)F * G.cells + c] = s;
   }
+  s[0] = REP == kDEV ? log1p(s[0]) : log(s[0]);
+#pragma unroll
+  for (int F = 0; F < 7; ++F) aux[(int64_t)F * G.cells + c] = s[F];
 }
 
 // ---------------------------------------------------------------------------
